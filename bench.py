@@ -1,0 +1,367 @@
+"""Benchmark: gridded + degridded visibilities per second at support 16.
+
+One step = the whole hot path over the 32,256,000-visibility workload
+(64 antennas, 2016 baselines x 1000 dumps x 16 channels, 4096^2 grid, support
+16, oversampling 16, 128 w-planes): zero the grid, locate + bin (plan), grid
+every visibility, degrid every visibility from the resulting grid.  value =
+2 * nvis / step time (whole job over all ranks).  Inputs (1.16 GB per step)
+are larger than L2 (129 MB), so no separate L2 flush is done.
+
+Also reported: the plain FP32 form (global atomics, no binning) on the same
+data, the roofline of the dominant kernel (FP32 FMA pipe: the scatter form is
+ALU-bound at S = 16; the HBM fraction is given beside it), an end-to-end
+figure through the C ABI with host buffers, and the FP64 oracle timed on the
+host cores on a bounded sample.
+
+--impl reference times the FP64 CPU oracle (the baseline arm) instead.
+Multi-GPU (torchrun): every rank runs an independent replica of the
+workload (the path is not sharded in this build), time = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "visibilities/s gridded+degridded at support 16 vs plain FP32 GPU form; % roofline"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        return json.load(open(PEAKS_FILE)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}",
+                                       f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.p is None:
+            return out
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower() == "active"})
+        out.update(sm_mhz=statistics.median(sm) if sm else None,
+                   sm_max_mhz=max(mx) if mx else None, reasons=reasons, samples=len(rows))
+        return out
+
+
+def _kernel_source_tag():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("sepw_tiled.cu", "sepw_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1511_07152_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None if the kernel source changed since the counters were taken."""
+    try:
+        t = json.load(open(TRAFFIC_FILE))
+    except Exception:
+        return None
+    e = t.get(kernel)
+    if not e or e.get("source_tag") != _kernel_source_tag():
+        return None
+    return e.get("dram_bytes_per_launch_full")
+
+
+def cpu_oracle_sample(wl, nsample: int):
+    """Time the FP64 oracle (locate + separable grid + degrid) on a seeded
+    sample of the workload, single-threaded.  Returns (vis/s, seconds)."""
+    import oracle as O
+    sub = wl.subsample(nsample, seed=7)
+    p = O.params_from(sub.params())
+    T = O.taps(p)  # table build is off the timed path, as on the GPU
+    t0 = time.perf_counter()
+    loc = O.locate(p, sub.u, sub.v, sub.w)
+    g = O.grid_separable(p, loc, sub.vis, sub.weight, T)
+    O.degrid_separable(p, loc, g, sub.weight, T)
+    dt = time.perf_counter() - t0
+    return 2 * sub.nvis / dt, dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import synth
+    wl = synth.meerkat_like()
+    ns = args.ref_sample
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(wl, min(ns, 20000))
+    t_all = 0.0
+    for _ in range(args.steps):
+        v, dt = cpu_oracle_sample(wl, ns)
+        vals.append(v)
+        t_all += dt
+    value = 2 * ns * args.steps / t_all
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "vis/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "nvis": wl.nvis, "sample": ns},
+        "cpu_baseline": {"value": value, "unit": "vis/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{ns} seeded visibilities of the workload per step "
+                                   "(locate + FP64 grid + FP64 degrid)"},
+        "e2e": {"value": value, "unit": "vis/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_1511_07152_gb300.sepw as S
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    wl = synth.meerkat_like()
+    N = wl.grid_size
+    nvis = wl.nvis
+    dev = {k: torch.from_numpy(getattr(wl, k)).cuda() for k in ("u", "v", "w", "vis", "weight")}
+    ctx = S.sepw_create(S.make_params(**wl.params(), tile=args.tile, form=S.FORM_TILED))
+    taps = S.sepw_make_taps(ctx)
+    grid = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+    out = torch.empty(nvis, dtype=torch.complex64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    S.sepw_plan(ctx, dev["u"], dev["v"], dev["w"])
+    ndrop = S.sepw_plan_dropped(ctx)
+    nkept = nvis - ndrop
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        grid.zero_()
+        S.sepw_plan(ctx, dev["u"], dev["v"], dev["w"])
+        if ev:
+            ev[1].record(stream)
+        S.sepw_grid_planned(ctx, taps, dev["vis"], dev["weight"], grid)
+        if ev:
+            ev[2].record(stream)
+        S.sepw_degrid_planned(ctx, taps, grid, dev["weight"], out)
+        if ev:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    plan_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    grid_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    degrid_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    value = 2.0 * nvis * ws / (ms * 1e-3)
+
+    # ---- plain FP32 form on the same data (the comparator) ----
+    plain = None
+    if not args.skip_plain:
+        ctxp = S.sepw_create(S.make_params(**wl.params(), form=S.FORM_PLAIN))
+        gp = torch.zeros_like(grid)
+        op = torch.empty_like(out)
+
+        def pstep():
+            gp.zero_()
+            S.sepw_plan(ctxp, dev["u"], dev["v"], dev["w"])
+            S.sepw_grid_planned(ctxp, taps, dev["vis"], dev["weight"], gp)
+            S.sepw_degrid_planned(ctxp, taps, gp, dev["weight"], op)
+        pstep()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        npl = max(1, min(3, args.steps))
+        a.record(stream)
+        for _ in range(npl):
+            pstep()
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b) / npl
+        plain = {"value": 2.0 * nvis * ws / (pms * 1e-3), "unit": "vis/s",
+                 "ms_per_step": pms, "steps": npl,
+                 "speedup_of_tiled": pms / ms}
+        ctxp.close()
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.skip_e2e:
+        host = {k: torch.from_numpy(getattr(wl, k)).pin_memory()
+                for k in ("u", "v", "w", "vis", "weight")}
+        hout = torch.empty(nvis, dtype=torch.complex64).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+        d2h = hout.numel() * hout.element_size()
+
+        def estep():
+            for k, t in host.items():
+                dev[k].copy_(t, non_blocking=True)
+            step()
+            hout.copy_(out, non_blocking=True)
+        estep()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        ne = max(1, min(5, args.steps))
+        a.record(stream)
+        for _ in range(ne):
+            estep()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ems = a.elapsed_time(b) / ne
+        e2e = {"value": 2.0 * nvis * ws / (ems * 1e-3), "unit": "vis/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": ems}
+
+    # ---- roofline of the dominant kernel ----
+    peaks, peak_src = _peaks()
+    Ssup = wl.support
+    flops_per_vis = 8 * Ssup * Ssup + 8 * Ssup
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    dom, dom_ms = ("grid_tiled_kernel", grid_ms) if grid_ms >= degrid_ms else \
+        ("degrid_tiled_kernel", degrid_ms)
+    achieved = flops_per_vis * nkept / (dom_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "traffic": _traffic(dom), "kernel": dom,
+                "peak_note": (f"FP32 FMA pipe: {sm_count} SMs x {FP32_LANES_PER_SM} lanes x 2 "
+                              f"flop x {sm_max:.0f} MHz max clock (derived)"),
+                "algorithmic": f"{flops_per_vis} flop/vis (8 S^2 + 8 S), {nkept} vis/launch"}
+    hbm_bytes = 36 * nkept  # uvw + V + W per visibility
+    roofline_hbm = {"bound": "hbm", "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                    "achieved": hbm_bytes / (dom_ms * 1e-3) / 1e9,
+                    "note": "36 B/vis algorithmic (uvw f64 + V + W) over the dominant kernel"}
+    roofline_hbm["frac"] = roofline_hbm["achieved"] / roofline_hbm["peak"]
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        v, dt = cpu_oracle_sample(wl, args.cpu_sample)
+        cpu = {"value": v, "unit": "vis/s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_sample} seeded visibilities of the workload "
+                         f"(locate + FP64 grid + FP64 degrid, {dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "vis/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp32", "data": "synthetic",
+            "config": {"workload": wl.name, "nvis": nvis, "kept": nkept, "grid": N,
+                       "support": wl.support, "oversample": wl.oversample,
+                       "wplanes": wl.n_wplanes, "form": "tiled", "tile": args.tile or 32,
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (1.16 GB per step), no flush"},
+            "phases_ms": {"plan": plan_ms, "grid": grid_ms, "degrid": degrid_ms},
+            "grid_updates_per_s": nkept * Ssup * Ssup * 2 * ws / (ms * 1e-3),
+            "plain_fp32": plain,
+            "roofline": roofline, "roofline_hbm": roofline_hbm, "peak_source": peak_src,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": 7 * args.steps,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--cpu-sample", type=int, default=4_000_000,
+                    help="visibilities in the oracle's timed sample (about 10-15 s)")
+    ap.add_argument("--ref-sample", type=int, default=1_000_000,
+                    help="visibilities per step of the reference (oracle) arm")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

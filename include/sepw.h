@@ -1,0 +1,202 @@
+/*
+ * sepw.h -- C ABI of the separable W-projection gridding library (libsepw.so)
+ * for NVIDIA GB300 (sm_103a).
+ *
+ * The method (B. Merry, "Approximating W projection as a separable kernel",
+ * MNRAS 2015): the W-projection gridding convolution function F_w (Sec. 2) is
+ * replaced by the separable F~_w(u, v) = F1_w(u) F1_w(v) (Eq. gt, Sec. 5), so
+ * that a visibility at (u_i, v_i, w_i) updates grid cell (u, v) by
+ * W_i V_i F1_{w_i}(u - u_i) F1_{w_i}(v - v_i).  The 1-D kernel F1 is tabulated
+ * per w-plane and per oversampled fractional offset.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Coordinates u, v, w are in wavelengths (Sec. 2), as float64 arrays of
+ *    length nvis (structure of arrays).
+ *  - Complex data are interleaved float32 pairs (re, im) ("complex64").
+ *  - The grid is grid_size x grid_size complex64, row-major [v][u]; the cell
+ *    size is du = 1/fov, and u = 0 lies at column grid_size/2.  The image
+ *    has the same shape, [m][l], with l_a = (a - N/2) fov / N.
+ *  - Visibility i is located at x = u*fov + N/2 (cells), rounded to the
+ *    nearest 1/oversample (ties up): cell c, oversample index o.  Its
+ *    footprint is the S x S block of cells c - S/2 + 1 .. c + S/2 per axis.
+ *    Its w-plane is round-half-up(|w| (P-1)/w_max) and w < 0 uses the complex
+ *    conjugate of the |w| kernel.  A visibility whose footprint leaves the
+ *    grid, whose plane exceeds P-1, or whose coordinates are not finite is
+ *    DROPPED (skipped and counted), never clamped or wrapped.  All of this is
+ *    done in IEEE float64 without fused multiply-add, so cell, oversample and
+ *    plane indices are reproducible bit for bit on any IEEE machine.
+ *  - Every data pointer is caller-owned DEVICE memory unless stated.  The
+ *    library never frees caller memory.  The context owns only its workspace
+ *    (binning buffers, FFT plan, small tables).
+ *  - Calls are asynchronous on `stream` (0 = legacy default stream) unless
+ *    stated; errors detected on the host return before anything is enqueued.
+ *  - Return value: SEPW_OK (0) or a negative SEPW_E* code.  No call throws.
+ *    sepw_last_error() gives a message for the most recent failure on a ctx.
+ *  - A ctx is not thread-safe: serialise calls on one ctx.  Calls on one ctx
+ *    with different streams must not overlap in time (they share workspace).
+ */
+#ifndef SEPW_H
+#define SEPW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SEPW_API __attribute__((visibility("default")))
+#else
+#define SEPW_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEPW_VERSION 1
+
+/* status codes */
+#define SEPW_OK 0
+#define SEPW_EINVAL (-1)   /* bad parameter, size, pointer or alignment */
+#define SEPW_ENOMEM (-2)   /* device allocation of workspace failed */
+#define SEPW_ECUDA (-3)    /* a CUDA / cuFFT call failed */
+#define SEPW_ETIMEOUT (-4) /* a bounded device wait gave up */
+#define SEPW_ENOTSUP (-5)  /* form not available for these parameters */
+#define SEPW_ENOPLAN (-6)  /* *_planned call without a current plan */
+
+/* kernel forms (sepw_params.form) */
+#define SEPW_FORM_PLAIN 0  /* plain FP32: one global atomic per cell update */
+#define SEPW_FORM_TILED 1  /* binned tiles, register/shared accumulation, FP32 */
+
+/* image directions (sepw_image) */
+#define SEPW_GRID_TO_IMAGE 0
+#define SEPW_IMAGE_TO_GRID 1
+
+typedef struct CUstream_st *sepw_stream_t; /* same type as cudaStream_t */
+
+typedef struct sepw_params {
+    int32_t grid_size;  /* N: grid and image are N x N; even, 16..65536       */
+    int32_t support;    /* S: taps per axis; even, 2..32, S <= N             */
+    int32_t oversample; /* OS: kernel samples per cell; 1..256               */
+    int32_t n_wplanes;  /* P: planes over |w| in [0, w_max]; 1..32768        */
+    double fov;         /* image extent in direction cosine, 0 < fov < 1.4;
+                           du = 1/fov (Sec. 2)                                */
+    double w_max;       /* |w| of the last plane, wavelengths, > 0           */
+    double gamma;       /* tuning parameter of Eq. gt (5/24 minimax, 1/8
+                           exact on the axes, Sec. 3)                         */
+    double kb_beta;     /* Kaiser-Bessel antialiasing window parameter; the
+                           taper is its transform (Sec. 2 kernel C / c)       */
+    int32_t tile;       /* tiled forms: tile edge T in cells (0 = 32);
+                           even, 8..64, T + S - 1 <= 64                       */
+    int32_t form;       /* SEPW_FORM_*                                        */
+} sepw_params;
+
+typedef struct sepw_ctx sepw_ctx;
+
+/* Library version (SEPW_VERSION).  Host only. */
+SEPW_API int sepw_version(void);
+
+/* Message for a status code.  Host only; static storage. */
+SEPW_API const char *sepw_strerror(int status);
+
+/* Check parameters without touching the GPU.  Returns SEPW_OK or
+ * SEPW_EINVAL / SEPW_ENOTSUP.  Host only. */
+SEPW_API int sepw_check_params(const sepw_params *p);
+
+/* Number of complex taps in the 1-D table: P * OS * S.  Host only; 0 if the
+ * parameters are invalid. */
+SEPW_API size_t sepw_taps_count(const sepw_params *p);
+
+/* Create a context on the current CUDA device.  Allocates the context's
+ * small tables (taper, twiddles) on that device; binning workspace is
+ * allocated on first use and grows as needed.  *out is set to NULL on error.
+ * Sec. 2 (problem statement: image size, cell size, support, oversampling,
+ * number of w planes). */
+SEPW_API int sepw_create(sepw_ctx **out, const sepw_params *p);
+
+/* Free the context and everything it owns (synchronises its device).
+ * NULL is ignored. */
+SEPW_API void sepw_destroy(sepw_ctx *ctx);
+
+/* Message for the most recent failure on ctx (host memory owned by ctx). */
+SEPW_API const char *sepw_last_error(const sepw_ctx *ctx);
+
+/* 1-D GCF tables, Eq. gt and Sec. 2 (the GCF is the transform of the taper
+ * times the screen):
+ *   taps[p][o][j] = F1_{w_p}(d),  d = j - S/2 + 1 - o/OS,  w_p = p w_max/(P-1),
+ *   F1_w(d) = (1/N) sum_{a=0}^{N-1} c1(nu_a) g1_w(l_a) exp(-2 pi i d nu_a),
+ *   g1_w(l) = exp(2 pi i w (-l^2/2 - gamma l^4)),  nu_a = (a - N/2)/N,
+ *   l_a = nu_a fov, c1 = Kaiser-Bessel transform normalised to c1(0) = 1.
+ * Computed in float64 on the GPU.  sepw_make_taps writes complex64
+ * (P*OS*S*2 floats, layout [p][o][j][re,im]); sepw_make_taps_f64 writes the
+ * float64 values (P*OS*S*2 doubles).  Off the hot path. */
+SEPW_API int sepw_make_taps(sepw_ctx *ctx, float *taps, sepw_stream_t stream);
+SEPW_API int sepw_make_taps_f64(sepw_ctx *ctx, double *taps, sepw_stream_t stream);
+
+/* Locate each visibility (the convention above): writes cell indices cu, cv
+ * (int32), oversample indices ou, ov (int32), plane (int32), conj and keep
+ * flags (uint8, 1 = true) for i < nvis.  Dropped visibilities have keep = 0
+ * and zeros elsewhere.  Any output pointer may be NULL.  Sec. 2 (coordinates)
+ * and the oversampled kernel lookup of Sec. 2. */
+SEPW_API int sepw_locate(sepw_ctx *ctx, int64_t nvis, const double *u, const double *v,
+                const double *w, int32_t *cu, int32_t *cv, int32_t *ou,
+                int32_t *ov, int32_t *plane, uint8_t *conj, uint8_t *keep,
+                sepw_stream_t stream);
+
+/* Locate and bin nvis visibilities into the context's plan (tiled forms:
+ * counting sort by tile, then by footprint origin inside each tile).  The
+ * plan is reused by sepw_grid_planned / sepw_degrid_planned until the next
+ * sepw_plan; u, v, w need not stay alive.  Binning is amortisable over the
+ * gridding/degridding calls of a major cycle (Sec. 6).  For the plain form
+ * the plan only records the coordinates' pointers, which must then stay
+ * valid and unchanged until the next sepw_plan. */
+SEPW_API int sepw_plan(sepw_ctx *ctx, int64_t nvis, const double *u, const double *v,
+              const double *w, sepw_stream_t stream);
+
+/* Number of visibilities dropped by the current plan.  Host pointer;
+ * synchronises `stream`. */
+SEPW_API int sepw_plan_dropped(sepw_ctx *ctx, int64_t *n_dropped_host,
+                      sepw_stream_t stream);
+
+/* Gridding, Sec. 5:  grid[c_v - S/2 + 1 + k][c_u - S/2 + 1 + j] +=
+ *   (W_i V_i taps[p][o_u][j]) * taps[p][o_v][k]   (conjugated taps if w_i < 0)
+ * for every kept visibility i.  `grid` is ACCUMULATED into (+=).  vis:
+ * complex64 [nvis]; weight: float32 [nvis] or NULL (= 1); taps: the table of
+ * sepw_make_taps.  FP32 arithmetic.  The planned variant uses the plan's
+ * visibilities (vis and weight indexed as in the call to sepw_plan).
+ * n_dropped (device int64, may be NULL) receives the number dropped. */
+SEPW_API int sepw_grid(sepw_ctx *ctx, const float *taps, int64_t nvis, const double *u,
+              const double *v, const double *w, const float *vis,
+              const float *weight, float *grid, int64_t *n_dropped,
+              sepw_stream_t stream);
+SEPW_API int sepw_grid_planned(sepw_ctx *ctx, const float *taps, const float *vis,
+                      const float *weight, float *grid, sepw_stream_t stream);
+
+/* Degridding (prediction, Sec. 2; used for prediction in Cotton-Schwab major
+ * cycles, Sec. 6), the exact adjoint of sepw_grid:
+ *   vis_out[i] = W_i sum_k conj(tv[k]) sum_j conj(tu[j]) grid[y_k][x_j]
+ * with tu, tv the (conjugated if w_i < 0) taps used by sepw_grid.  vis_out
+ * (complex64 [nvis]) is OVERWRITTEN; dropped visibilities get 0. */
+SEPW_API int sepw_degrid(sepw_ctx *ctx, const float *taps, int64_t nvis, const double *u,
+                const double *v, const double *w, const float *grid,
+                const float *weight, float *vis_out, int64_t *n_dropped,
+                sepw_stream_t stream);
+SEPW_API int sepw_degrid_planned(sepw_ctx *ctx, const float *taps, const float *grid,
+                        const float *weight, float *vis_out,
+                        sepw_stream_t stream);
+
+/* Image step with grid correction, Sec. 2 (I_D / n = F^-1[grid] / c), in
+ * place on an N x N complex64 buffer:
+ *   SEPW_GRID_TO_IMAGE:  I[b][a] = n_ab / (c1(nu_a) c1(nu_b)) *
+ *       sum_{cu,cv} grid[cv][cu] exp(2 pi i ((cu-N/2) nu_a + (cv-N/2) nu_b))
+ *   SEPW_IMAGE_TO_GRID (prediction direction):  grid[cv][cu] =
+ *       sum_{a,b} exp(-2 pi i ((cu-N/2) nu_a + (cv-N/2) nu_b)) I[b][a] /
+ *       (n_ab c1(nu_a) c1(nu_b))
+ * with n_ab = sqrt(1 - l_a^2 - m_b^2).  Uses cuFFT (FP32 C2C); the plan is
+ * created on first use. */
+SEPW_API int sepw_image(sepw_ctx *ctx, int direction, float *buf, sepw_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEPW_H */

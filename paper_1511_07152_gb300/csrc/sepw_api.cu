@@ -1,0 +1,505 @@
+// C ABI of libsepw: parameter checks, context and workspace management, and
+// the launch sequence of each entry point.  See include/sepw.h for the
+// contract of every function.
+#include <cufft.h>
+#include <math.h>
+#include <new>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "sepw_internal.cuh"
+
+using namespace sepw;
+
+struct sepw_ctx {
+    sepw_params p;
+    DevParams dp;
+    int device = 0;
+    int num_sms = 0;
+    double *d_taper64 = nullptr;
+    float *d_taper32 = nullptr;
+    double2 *d_tw = nullptr;
+    Plan plan;
+    cufftHandle fft = 0;
+    bool fft_ready = false;
+    char err[512] = {0};
+};
+
+namespace {
+
+int fail(sepw_ctx *ctx, int code, const char *fmt, ...)
+{
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_fail(sepw_ctx *ctx, cudaError_t e, const char *where)
+{
+    return fail(ctx, SEPW_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define SEPW_CUDA(ctx, call)                                  \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess)                                \
+            return cuda_fail((ctx), e_, #call);               \
+    } while (0)
+
+int effective_tile(const sepw_params *p) { return p->tile == 0 ? 32 : p->tile; }
+
+DevParams make_dev(const sepw_params *p)
+{
+    DevParams d;
+    d.N = p->grid_size;
+    d.S = p->support;
+    d.OS = p->oversample;
+    d.P = p->n_wplanes;
+    d.T = effective_tile(p);
+    d.ntx = (d.N - d.S) / d.T + 1;
+    d.fov = p->fov;
+    d.half = (double)(d.N / 2);
+    d.os_d = (double)d.OS;
+    d.plane_r = d.P > 1 ? (double)(d.P - 1) / p->w_max : 0.0;
+    d.w_max = p->w_max;
+    d.gamma = p->gamma;
+    d.beta = p->kb_beta;
+    return d;
+}
+
+template <typename T>
+int grow(sepw_ctx *ctx, T **ptr, size_t count)
+{
+    if (*ptr)
+        cudaFree(*ptr);
+    *ptr = nullptr;
+    if (count == 0)
+        count = 1;
+    cudaError_t e = cudaMalloc((void **)ptr, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return fail(ctx, SEPW_ENOMEM, "cudaMalloc of %zu bytes: %s", count * sizeof(T),
+                    cudaGetErrorString(e));
+    }
+    return SEPW_OK;
+}
+
+void free_plan(Plan &pl)
+{
+    cudaFree(pl.d_tile);
+    cudaFree(pl.d_rec0);
+    cudaFree(pl.d_rec);
+    cudaFree(pl.d_perm);
+    cudaFree(pl.d_drop_list);
+    cudaFree(pl.d_tile_count);
+    cudaFree(pl.d_tile_cursor);
+    cudaFree(pl.d_items);
+    cudaFree(pl.d_nitems);
+    cudaFree(pl.d_item_counter);
+    cudaFree(pl.d_dropped);
+    pl = Plan();
+}
+
+bool is_device_ptr(const void *ptr)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int check_dev(sepw_ctx *ctx, const void *ptr, const char *name, bool allow_null)
+{
+    if (!ptr)
+        return allow_null ? SEPW_OK : fail(ctx, SEPW_EINVAL, "%s is NULL", name);
+    if (!is_device_ptr(ptr))
+        return fail(ctx, SEPW_EINVAL, "%s is not device memory", name);
+    if (((uintptr_t)ptr) & 7)
+        return fail(ctx, SEPW_EINVAL, "%s is not 8-byte aligned", name);
+    return SEPW_OK;
+}
+
+int ensure_plan_capacity(sepw_ctx *ctx, int64_t nvis)
+{
+    Plan &pl = ctx->plan;
+    int rc;
+    const int ntiles = ctx->dp.ntx * ctx->dp.ntx;
+    if (!pl.d_nitems) {
+        if ((rc = grow(ctx, &pl.d_nitems, 1)) || (rc = grow(ctx, &pl.d_item_counter, 2)) ||
+            (rc = grow(ctx, &pl.d_dropped, 1)))
+            return rc;
+    }
+    if (pl.tiles_capacity < ntiles) {
+        if ((rc = grow(ctx, &pl.d_tile_count, ntiles)) ||
+            (rc = grow(ctx, &pl.d_tile_cursor, ntiles)))
+            return rc;
+        pl.tiles_capacity = ntiles;
+    }
+    pl.ntiles = ntiles;
+    if (ctx->p.form == SEPW_FORM_PLAIN)
+        return SEPW_OK;  // the plain form keeps no per-visibility state
+    if (pl.capacity < nvis) {
+        int64_t cap = nvis;
+        if ((rc = grow(ctx, &pl.d_tile, cap)) || (rc = grow(ctx, &pl.d_rec0, cap)) ||
+            (rc = grow(ctx, &pl.d_rec, cap)) || (rc = grow(ctx, &pl.d_perm, cap)) ||
+            (rc = grow(ctx, &pl.d_drop_list, cap)))
+            return rc;
+        pl.capacity = cap;
+    }
+    int64_t items = (int64_t)ntiles + nvis / kChunk + 1;
+    if (items > INT32_MAX)
+        return fail(ctx, SEPW_EINVAL, "too many work items");
+    if (pl.items_capacity < items) {
+        if ((rc = grow(ctx, &pl.d_items, (size_t)items)))
+            return rc;
+        pl.items_capacity = (int32_t)items;
+    }
+    return SEPW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sepw_version(void) { return SEPW_VERSION; }
+
+const char *sepw_strerror(int status)
+{
+    switch (status) {
+    case SEPW_OK: return "ok";
+    case SEPW_EINVAL: return "invalid argument";
+    case SEPW_ENOMEM: return "out of device memory";
+    case SEPW_ECUDA: return "CUDA error";
+    case SEPW_ETIMEOUT: return "device wait timed out";
+    case SEPW_ENOTSUP: return "not supported for these parameters";
+    case SEPW_ENOPLAN: return "no current plan";
+    default: return "unknown status";
+    }
+}
+
+int sepw_check_params(const sepw_params *p)
+{
+    if (!p)
+        return SEPW_EINVAL;
+    const int N = p->grid_size, S = p->support, OS = p->oversample, P = p->n_wplanes;
+    if (N < 16 || N > 65536 || (N & 1))
+        return SEPW_EINVAL;
+    if (S < 2 || S > 32 || (S & 1) || S > N)
+        return SEPW_EINVAL;
+    if (OS < 1 || OS > 256)
+        return SEPW_EINVAL;
+    if (P < 1 || P > 32768)
+        return SEPW_EINVAL;
+    if (!(p->fov > 0.0) || !(p->fov < 1.4) || !isfinite(p->fov))
+        return SEPW_EINVAL;
+    if (!(p->w_max > 0.0) || !isfinite(p->w_max))
+        return SEPW_EINVAL;
+    if (!isfinite(p->gamma))
+        return SEPW_EINVAL;
+    if (!(p->kb_beta > 0.0) || !(p->kb_beta < 1e4))
+        return SEPW_EINVAL;
+    const int T = effective_tile(p);
+    if (T < 8 || T > 64 || (T & 1) || T + S - 1 > kMaxWindow)
+        return SEPW_EINVAL;
+    if (p->form != SEPW_FORM_PLAIN && p->form != SEPW_FORM_TILED)
+        return SEPW_ENOTSUP;
+    return SEPW_OK;
+}
+
+size_t sepw_taps_count(const sepw_params *p)
+{
+    if (sepw_check_params(p) != SEPW_OK)
+        return 0;
+    return (size_t)p->n_wplanes * p->oversample * p->support;
+}
+
+int sepw_create(sepw_ctx **out, const sepw_params *p)
+{
+    if (!out)
+        return SEPW_EINVAL;
+    *out = nullptr;
+    int rc = sepw_check_params(p);
+    if (rc != SEPW_OK)
+        return rc;
+    sepw_ctx *ctx = new (std::nothrow) sepw_ctx();
+    if (!ctx)
+        return SEPW_ENOMEM;
+    ctx->p = *p;
+    ctx->dp = make_dev(p);
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount,
+                                   ctx->device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return SEPW_ECUDA;
+    }
+    const int N = p->grid_size;
+    if ((rc = grow(ctx, &ctx->d_taper64, N)) || (rc = grow(ctx, &ctx->d_taper32, N)) ||
+        (rc = grow(ctx, &ctx->d_tw, (size_t)N * p->oversample))) {
+        sepw_destroy(ctx);
+        return rc;
+    }
+    e = launch_taper(ctx->dp, ctx->d_taper64, ctx->d_taper32, 0);
+    if (e == cudaSuccess)
+        e = launch_twiddles(ctx->dp, ctx->d_tw, 0);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        sepw_destroy(ctx);
+        return SEPW_ECUDA;
+    }
+    *out = ctx;
+    return SEPW_OK;
+}
+
+void sepw_destroy(sepw_ctx *ctx)
+{
+    if (!ctx)
+        return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->fft_ready)
+        cufftDestroy(ctx->fft);
+    cudaFree(ctx->d_taper64);
+    cudaFree(ctx->d_taper32);
+    cudaFree(ctx->d_tw);
+    free_plan(ctx->plan);
+    cudaSetDevice(cur);
+    delete ctx;
+}
+
+const char *sepw_last_error(const sepw_ctx *ctx) { return ctx ? ctx->err : "no context"; }
+
+int sepw_make_taps(sepw_ctx *ctx, float *taps, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    int rc = check_dev(ctx, taps, "taps", false);
+    if (rc)
+        return rc;
+    SEPW_CUDA(ctx, launch_taps(ctx->dp, ctx->d_taper64, ctx->d_tw, nullptr,
+                               (float2 *)taps, (cudaStream_t)stream));
+    return SEPW_OK;
+}
+
+int sepw_make_taps_f64(sepw_ctx *ctx, double *taps, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    int rc = check_dev(ctx, taps, "taps", false);
+    if (rc)
+        return rc;
+    SEPW_CUDA(ctx, launch_taps(ctx->dp, ctx->d_taper64, ctx->d_tw, (double2 *)taps,
+                               nullptr, (cudaStream_t)stream));
+    return SEPW_OK;
+}
+
+int sepw_locate(sepw_ctx *ctx, int64_t nvis, const double *u, const double *v,
+                const double *w, int32_t *cu, int32_t *cv, int32_t *ou, int32_t *ov,
+                int32_t *plane, uint8_t *conj, uint8_t *keep, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    if (nvis < 0)
+        return fail(ctx, SEPW_EINVAL, "nvis < 0");
+    if (nvis == 0)
+        return SEPW_OK;
+    int rc;
+    if ((rc = check_dev(ctx, u, "u", false)) || (rc = check_dev(ctx, v, "v", false)) ||
+        (rc = check_dev(ctx, w, "w", false)))
+        return rc;
+    SEPW_CUDA(ctx, launch_locate(ctx->dp, nvis, u, v, w, cu, cv, ou, ov, plane, conj,
+                                 keep, (cudaStream_t)stream));
+    return SEPW_OK;
+}
+
+int sepw_plan(sepw_ctx *ctx, int64_t nvis, const double *u, const double *v,
+              const double *w, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    ctx->plan.valid = false;
+    if (nvis < 0 || nvis > (int64_t)INT32_MAX - 1)
+        return fail(ctx, SEPW_EINVAL, "nvis out of range [0, 2^31 - 2]");
+    int rc;
+    if (nvis > 0 && ((rc = check_dev(ctx, u, "u", false)) ||
+                     (rc = check_dev(ctx, v, "v", false)) ||
+                     (rc = check_dev(ctx, w, "w", false))))
+        return rc;
+    if ((rc = ensure_plan_capacity(ctx, nvis)))
+        return rc;
+    Plan &pl = ctx->plan;
+    pl.form = ctx->p.form;
+    pl.nvis = nvis;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->p.form == SEPW_FORM_PLAIN) {
+        pl.u = u;
+        pl.v = v;
+        pl.w = w;
+        SEPW_CUDA(ctx, cudaMemsetAsync(pl.d_dropped, 0, sizeof(unsigned long long), s));
+        SEPW_CUDA(ctx, launch_count_dropped(ctx->dp, nvis, u, v, w, pl.d_dropped, s));
+    } else {
+        pl.u = pl.v = pl.w = nullptr;
+        SEPW_CUDA(ctx, launch_plan(ctx->dp, nvis, u, v, w, pl, s));
+    }
+    pl.valid = true;
+    return SEPW_OK;
+}
+
+int sepw_plan_dropped(sepw_ctx *ctx, int64_t *n_dropped_host, sepw_stream_t stream)
+{
+    if (!ctx || !n_dropped_host)
+        return SEPW_EINVAL;
+    if (!ctx->plan.valid)
+        return fail(ctx, SEPW_ENOPLAN, "no plan");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long n = 0;
+    SEPW_CUDA(ctx, cudaMemcpyAsync(&n, ctx->plan.d_dropped, sizeof(n),
+                                   cudaMemcpyDeviceToHost, s));
+    SEPW_CUDA(ctx, cudaStreamSynchronize(s));
+    *n_dropped_host = (int64_t)n;
+    return SEPW_OK;
+}
+
+int sepw_grid_planned(sepw_ctx *ctx, const float *taps, const float *vis,
+                      const float *weight, float *grid, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    if (!ctx->plan.valid)
+        return fail(ctx, SEPW_ENOPLAN, "no plan");
+    int rc;
+    if ((rc = check_dev(ctx, taps, "taps", false)) || (rc = check_dev(ctx, grid, "grid", false)))
+        return rc;
+    const Plan &pl = ctx->plan;
+    if (pl.nvis == 0)
+        return SEPW_OK;
+    if ((rc = check_dev(ctx, vis, "vis", false)) ||
+        (rc = check_dev(ctx, weight, "weight", true)))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (pl.form == SEPW_FORM_PLAIN) {
+        SEPW_CUDA(ctx, launch_grid_plain(ctx->dp, pl.nvis, pl.u, pl.v, pl.w,
+                                         (const float2 *)vis, weight, (const float2 *)taps,
+                                         (float2 *)grid, nullptr, s));
+    } else {
+        SEPW_CUDA(ctx, launch_grid_tiled(ctx->dp, pl, (const float2 *)vis, weight,
+                                         (const float2 *)taps, (float2 *)grid,
+                                         ctx->num_sms, s));
+    }
+    return SEPW_OK;
+}
+
+int sepw_degrid_planned(sepw_ctx *ctx, const float *taps, const float *grid,
+                        const float *weight, float *vis_out, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    if (!ctx->plan.valid)
+        return fail(ctx, SEPW_ENOPLAN, "no plan");
+    int rc;
+    if ((rc = check_dev(ctx, taps, "taps", false)) || (rc = check_dev(ctx, grid, "grid", false)))
+        return rc;
+    const Plan &pl = ctx->plan;
+    if (pl.nvis == 0)
+        return SEPW_OK;
+    if ((rc = check_dev(ctx, vis_out, "vis_out", false)) ||
+        (rc = check_dev(ctx, weight, "weight", true)))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (pl.form == SEPW_FORM_PLAIN) {
+        SEPW_CUDA(ctx, launch_degrid_plain(ctx->dp, pl.nvis, pl.u, pl.v, pl.w,
+                                           (const float2 *)grid, weight,
+                                           (const float2 *)taps, (float2 *)vis_out,
+                                           nullptr, s));
+    } else {
+        SEPW_CUDA(ctx, launch_zero_dropped(pl, (float2 *)vis_out, s));
+        SEPW_CUDA(ctx, launch_degrid_tiled(ctx->dp, pl, (const float2 *)grid, weight,
+                                           (const float2 *)taps, (float2 *)vis_out,
+                                           ctx->num_sms, s));
+    }
+    return SEPW_OK;
+}
+
+static int copy_dropped(sepw_ctx *ctx, int64_t *n_dropped, cudaStream_t s)
+{
+    if (!n_dropped)
+        return SEPW_OK;
+    int rc = check_dev(ctx, n_dropped, "n_dropped", false);
+    if (rc)
+        return rc;
+    SEPW_CUDA(ctx, cudaMemcpyAsync(n_dropped, ctx->plan.d_dropped, sizeof(int64_t),
+                                   cudaMemcpyDeviceToDevice, s));
+    return SEPW_OK;
+}
+
+int sepw_grid(sepw_ctx *ctx, const float *taps, int64_t nvis, const double *u,
+              const double *v, const double *w, const float *vis, const float *weight,
+              float *grid, int64_t *n_dropped, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    int rc = sepw_plan(ctx, nvis, u, v, w, stream);
+    if (rc)
+        return rc;
+    if ((rc = sepw_grid_planned(ctx, taps, vis, weight, grid, stream)))
+        return rc;
+    return copy_dropped(ctx, n_dropped, (cudaStream_t)stream);
+}
+
+int sepw_degrid(sepw_ctx *ctx, const float *taps, int64_t nvis, const double *u,
+                const double *v, const double *w, const float *grid, const float *weight,
+                float *vis_out, int64_t *n_dropped, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    int rc = sepw_plan(ctx, nvis, u, v, w, stream);
+    if (rc)
+        return rc;
+    if ((rc = sepw_degrid_planned(ctx, taps, grid, weight, vis_out, stream)))
+        return rc;
+    return copy_dropped(ctx, n_dropped, (cudaStream_t)stream);
+}
+
+int sepw_image(sepw_ctx *ctx, int direction, float *buf, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    if (direction != SEPW_GRID_TO_IMAGE && direction != SEPW_IMAGE_TO_GRID)
+        return fail(ctx, SEPW_EINVAL, "bad direction %d", direction);
+    int rc = check_dev(ctx, buf, "buf", false);
+    if (rc)
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!ctx->fft_ready) {
+        cufftResult r = cufftPlan2d(&ctx->fft, ctx->p.grid_size, ctx->p.grid_size, CUFFT_C2C);
+        if (r != CUFFT_SUCCESS)
+            return fail(ctx, SEPW_ECUDA, "cufftPlan2d failed (%d)", (int)r);
+        ctx->fft_ready = true;
+    }
+    if (cufftSetStream(ctx->fft, s) != CUFFT_SUCCESS)
+        return fail(ctx, SEPW_ECUDA, "cufftSetStream failed");
+    SEPW_CUDA(ctx, launch_image_pre(ctx->dp, direction, ctx->d_taper32, (float2 *)buf, s));
+    cufftResult r = cufftExecC2C(ctx->fft, (cufftComplex *)buf, (cufftComplex *)buf,
+                                 direction == SEPW_GRID_TO_IMAGE ? CUFFT_INVERSE
+                                                                 : CUFFT_FORWARD);
+    if (r != CUFFT_SUCCESS)
+        return fail(ctx, SEPW_ECUDA, "cufftExecC2C failed (%d)", (int)r);
+    SEPW_CUDA(ctx, launch_image_post(ctx->dp, direction, ctx->d_taper32, (float2 *)buf, s));
+    return SEPW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,266 @@
+// Plan construction for the tiled forms: locate every visibility, bin it by
+// the T x T tile that holds its footprint origin (counting sort with
+// warp-aggregated atomics), cut each tile into work items of at most kChunk
+// visibilities, and sort each item by footprint origin so that consecutive
+// visibilities with the same origin can be accumulated in registers.
+//
+// The update structure this serves is Sec. 5: every visibility adds a
+// separable S x S block at its own offset; visibilities that share a tile
+// share one shared-memory window, and visibilities that share an origin share
+// one register block.
+#include "sepw_internal.cuh"
+
+namespace sepw {
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Pass 1: locate, record, tile histogram, dropped count.
+__global__ void __launch_bounds__(256) locate_bin_kernel(
+    DevParams p, int64_t nvis, const double *__restrict__ u, const double *__restrict__ v,
+    const double *__restrict__ w, int32_t *__restrict__ tile_of,
+    uint64_t *__restrict__ rec0, int32_t *tile_count, unsigned long long *dropped,
+    int32_t *__restrict__ drop_list)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool active = i < nvis;
+    int tile = -1;
+    if (active) {
+        Loc L = locate(u[i], v[i], w[i], p);
+        if (L.keep) {
+            int fx = L.cu - p.S / 2 + 1, fy = L.cv - p.S / 2 + 1;
+            int tx = fx / p.T, ty = fy / p.T;
+            tile = ty * p.ntx + tx;
+            rec0[i] = pack_rec(fx - tx * p.T, fy - ty * p.T, L.ou, L.ov, L.plane, L.conj);
+        }
+        tile_of[i] = tile;
+    }
+    unsigned act = __ballot_sync(0xffffffffu, active && tile >= 0);
+    unsigned drop = __ballot_sync(0xffffffffu, active && tile < 0);
+    int lane = threadIdx.x & 31;
+    if (drop) {
+        // append the dropped indices (degridding writes 0 there)
+        int leader = __ffs(drop) - 1;
+        unsigned long long base = 0;
+        if (lane == leader)
+            base = atomicAdd(dropped, (unsigned long long)__popc(drop));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (active && tile < 0)
+            drop_list[base + __popc(drop & lanemask_lt())] = (int32_t)i;
+    }
+    if (active && tile >= 0) {
+        unsigned peers = __match_any_sync(act, tile);
+        if (lane == __ffs(peers) - 1)
+            atomicAdd(tile_count + tile, __popc(peers));
+    }
+}
+
+// Pass 2 (one block of 1024 threads): exclusive scans of the tile counts
+// (-> slot cursors) and of the per-tile chunk counts (-> work items).
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(
+    int32_t ntiles, const int32_t *__restrict__ tile_count, int32_t *__restrict__ cursor,
+    WorkItem *__restrict__ items, int32_t *nitems)
+{
+    __shared__ int64_t s_cnt[kScanThreads];
+    __shared__ int32_t s_chk[kScanThreads];
+    int t = threadIdx.x;
+    int per = (ntiles + kScanThreads - 1) / kScanThreads;
+    int lo = min(ntiles, t * per), hi = min(ntiles, lo + per);
+    int64_t c = 0;
+    int32_t k = 0;
+    for (int i = lo; i < hi; ++i) {
+        int n = tile_count[i];
+        c += n;
+        k += (n + kChunk - 1) / kChunk;
+    }
+    s_cnt[t] = c;
+    s_chk[t] = k;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over 1024 partials
+    for (int off = 1; off < kScanThreads; off <<= 1) {
+        int64_t a = t >= off ? s_cnt[t - off] : 0;
+        int32_t b = t >= off ? s_chk[t - off] : 0;
+        __syncthreads();
+        s_cnt[t] += a;
+        s_chk[t] += b;
+        __syncthreads();
+    }
+    int64_t off_c = s_cnt[t] - c;
+    int32_t off_k = s_chk[t] - k;
+    for (int i = lo; i < hi; ++i) {
+        int n = tile_count[i];
+        cursor[i] = (int32_t)off_c;
+        int nk = (n + kChunk - 1) / kChunk;
+        for (int q = 0; q < nk; ++q) {
+            WorkItem it;
+            it.tile = i;
+            it.start = (int32_t)(off_c + (int64_t)q * kChunk);
+            it.count = min(kChunk, n - q * kChunk);
+            it.pad = 0;
+            items[off_k + q] = it;
+        }
+        off_c += n;
+        off_k += nk;
+    }
+    if (t == kScanThreads - 1)
+        *nitems = s_chk[t];
+}
+
+// Pass 3: scatter visibility ids and records to their tile's slots.
+__global__ void __launch_bounds__(256) scatter_kernel(
+    int64_t nvis, const int32_t *__restrict__ tile_of, const uint64_t *__restrict__ rec0,
+    int32_t *cursor, int32_t *__restrict__ perm, uint64_t *__restrict__ rec)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int tile = i < nvis ? tile_of[i] : -1;
+    unsigned act = __ballot_sync(0xffffffffu, tile >= 0);
+    if (tile < 0)
+        return;
+    int lane = threadIdx.x & 31;
+    unsigned peers = __match_any_sync(act, tile);
+    int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader)
+        base = atomicAdd(cursor + tile, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    int slot = base + __popc(peers & lanemask_lt());
+    perm[slot] = (int32_t)i;
+    rec[slot] = rec0[i];
+}
+
+// Pass 4: inside each work item, counting sort by footprint origin
+// (ly * 64 + lx).  One block per item; the item's slots are rewritten in
+// place.  Block-local; the order among equal origins is arbitrary.
+constexpr int kSortBins = 64 * 64;
+
+__global__ void __launch_bounds__(512) item_sort_kernel(const WorkItem *__restrict__ items,
+                                                        const int32_t *__restrict__ nitems,
+                                                        int32_t *__restrict__ perm,
+                                                        uint64_t *__restrict__ rec)
+{
+    __shared__ int32_t hist[kSortBins];
+    __shared__ uint64_t s_rec[kChunk];
+    __shared__ int32_t s_perm[kChunk];
+    __shared__ int32_t s_wsum[32];
+    int item = blockIdx.x;
+    if (item >= *nitems)
+        return;
+    WorkItem it = items[item];
+    const int n = it.count;
+    for (int b = threadIdx.x; b < kSortBins; b += blockDim.x)
+        hist[b] = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        uint64_t r = rec[it.start + q];
+        s_rec[q] = r;
+        s_perm[q] = perm[it.start + q];
+        atomicAdd(hist + rec_ly(r) * 64 + rec_lx(r), 1);
+    }
+    __syncthreads();
+    // exclusive scan of hist: each thread owns 8 consecutive bins
+    const int per = kSortBins / 512;
+    int t = threadIdx.x;
+    int local[per];
+    int sum = 0;
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+        local[q] = hist[t * per + q];
+        sum += local[q];
+    }
+    int lane = t & 31, warp = t >> 5;
+    int incl = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off)
+            incl += y;
+    }
+    if (lane == 31)
+        s_wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int x = lane < 16 ? s_wsum[lane] : 0;
+        int y = x;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int z = __shfl_up_sync(0xffffffffu, y, off);
+            if (lane >= off)
+                y += z;
+        }
+        if (lane < 16)
+            s_wsum[lane] = y - x;  // exclusive warp offsets
+    }
+    __syncthreads();
+    int run = s_wsum[warp] + incl - sum;
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+        hist[t * per + q] = run;
+        run += local[q];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        uint64_t r = s_rec[q];
+        int dst = atomicAdd(hist + rec_ly(r) * 64 + rec_lx(r), 1);
+        rec[it.start + dst] = r;
+        perm[it.start + dst] = s_perm[q];
+    }
+}
+
+// Degridding writes 0 for every dropped visibility of the plan.
+__global__ void zero_dropped_kernel(const int32_t *__restrict__ drop_list,
+                                    const unsigned long long *__restrict__ ndrop,
+                                    float2 *__restrict__ vis)
+{
+    const unsigned long long n = *ndrop;
+    for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+         k < n; k += (unsigned long long)gridDim.x * blockDim.x)
+        vis[drop_list[k]] = make_float2(0.f, 0.f);
+}
+
+cudaError_t launch_zero_dropped(const Plan &plan, float2 *vis, cudaStream_t s)
+{
+    zero_dropped_kernel<<<64, 256, 0, s>>>(plan.d_drop_list, plan.d_dropped, vis);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
+                        const double *v, const double *w, Plan &plan, cudaStream_t s)
+{
+    cudaError_t e;
+    e = cudaMemsetAsync(plan.d_tile_count, 0, sizeof(int32_t) * plan.ntiles, s);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaMemsetAsync(plan.d_dropped, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess)
+        return e;
+    if (nvis > 0) {
+        locate_bin_kernel<<<(unsigned)((nvis + 255) / 256), 256, 0, s>>>(
+            p, nvis, u, v, w, plan.d_tile, plan.d_rec0, plan.d_tile_count, plan.d_dropped,
+            plan.d_drop_list);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+    }
+    scan_kernel<<<1, kScanThreads, 0, s>>>(plan.ntiles, plan.d_tile_count,
+                                           plan.d_tile_cursor, plan.d_items, plan.d_nitems);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    if (nvis > 0) {
+        scatter_kernel<<<(unsigned)((nvis + 255) / 256), 256, 0, s>>>(
+            nvis, plan.d_tile, plan.d_rec0, plan.d_tile_cursor, plan.d_perm, plan.d_rec);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+        item_sort_kernel<<<plan.items_capacity, 512, 0, s>>>(plan.d_items, plan.d_nitems,
+                                                             plan.d_perm, plan.d_rec);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace sepw

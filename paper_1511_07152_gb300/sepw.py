@@ -1,0 +1,296 @@
+"""Thin ctypes binding of libsepw (include/sepw.h).
+
+Argument marshalling only: every step of gridding, degridding, tap generation,
+location, binning and the image step runs in the CUDA library.  Tensors are
+torch CUDA tensors (torch provides device memory and streams); their raw
+pointers and the current stream are passed through the C ABI.  If the shared
+library is missing or cannot be loaded, importing this module raises: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+FORM_PLAIN = 0
+FORM_TILED = 1
+GRID_TO_IMAGE = 0
+IMAGE_TO_GRID = 1
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP, ENOPLAN = 0, -1, -2, -3, -4, -5, -6
+
+
+class SepwError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"sepw error {status}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """Mirror of struct sepw_params."""
+    _fields_ = [
+        ("grid_size", ctypes.c_int32),
+        ("support", ctypes.c_int32),
+        ("oversample", ctypes.c_int32),
+        ("n_wplanes", ctypes.c_int32),
+        ("fov", ctypes.c_double),
+        ("w_max", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("kb_beta", ctypes.c_double),
+        ("tile", ctypes.c_int32),
+        ("form", ctypes.c_int32),
+    ]
+
+
+def make_params(grid_size, fov, support, oversample, n_wplanes, w_max,
+                gamma=5.0 / 24.0, kb_beta=None, tile=0, form=FORM_TILED) -> Params:
+    if kb_beta is None:
+        kb_beta = 2.34 * support
+    return Params(int(grid_size), int(support), int(oversample), int(n_wplanes),
+                  float(fov), float(w_max), float(gamma), float(kb_beta), int(tile),
+                  int(form))
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_SIG = {
+    "sepw_version": (ctypes.c_int, []),
+    "sepw_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "sepw_check_params": (ctypes.c_int, [ctypes.POINTER(Params)]),
+    "sepw_taps_count": (ctypes.c_size_t, [ctypes.POINTER(Params)]),
+    "sepw_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(Params)]),
+    "sepw_destroy": (None, [_P]),
+    "sepw_last_error": (ctypes.c_char_p, [_P]),
+    "sepw_make_taps": (ctypes.c_int, [_P, _P, _P]),
+    "sepw_make_taps_f64": (ctypes.c_int, [_P, _P, _P]),
+    "sepw_locate": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "sepw_plan": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P]),
+    "sepw_plan_dropped": (ctypes.c_int, [_P, ctypes.POINTER(_I64), _P]),
+    "sepw_grid": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "sepw_grid_planned": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "sepw_degrid": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "sepw_degrid_planned": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "sepw_image": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+}
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libsepw.so is not built ({path}); run "
+                          "paper_1511_07152_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIG.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+def exported_symbols():
+    return sorted(_SIG)
+
+
+# ---- helpers ---------------------------------------------------------------
+
+
+def _ptr(t, dtype=None, n=None, name="tensor"):
+    """Raw device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Context:
+    """Owns a sepw_ctx (created on the current CUDA device)."""
+
+    def __init__(self, params: Params):
+        self.params = params
+        h = _P()
+        rc = LIB.sepw_create(ctypes.byref(h), ctypes.byref(params))
+        if rc != OK:
+            raise SepwError(rc, LIB.sepw_strerror(rc).decode())
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            LIB.sepw_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc: int):
+        if rc != OK:
+            msg = LIB.sepw_last_error(self.handle).decode()
+            raise SepwError(rc, f"{LIB.sepw_strerror(rc).decode()}: {msg}")
+
+    @property
+    def ntaps(self) -> int:
+        return int(LIB.sepw_taps_count(ctypes.byref(self.params)))
+
+    @property
+    def taps_shape(self):
+        p = self.params
+        return (p.n_wplanes, p.oversample, p.support)
+
+
+# ---- entry points (same names as the C ABI) ---------------------------------
+
+
+def sepw_version() -> int:
+    return LIB.sepw_version()
+
+
+def sepw_check_params(params: Params) -> int:
+    return LIB.sepw_check_params(ctypes.byref(params))
+
+
+def sepw_create(params: Params) -> Context:
+    return Context(params)
+
+
+def sepw_make_taps(ctx: Context, taps=None, stream=None):
+    """complex64 taps [P, OS, S] (Eq. gt), computed in float64 on the GPU."""
+    import torch
+    if taps is None:
+        taps = torch.empty(ctx.taps_shape, dtype=torch.complex64, device="cuda")
+    ctx.check(LIB.sepw_make_taps(ctx.handle, _ptr(taps, torch.complex64, ctx.ntaps, "taps"),
+                                 _stream(stream)))
+    return taps
+
+
+def sepw_make_taps_f64(ctx: Context, taps=None, stream=None):
+    import torch
+    if taps is None:
+        taps = torch.empty(ctx.taps_shape, dtype=torch.complex128, device="cuda")
+    ctx.check(LIB.sepw_make_taps_f64(ctx.handle,
+                                     _ptr(taps, torch.complex128, ctx.ntaps, "taps"),
+                                     _stream(stream)))
+    return taps
+
+
+def sepw_locate(ctx: Context, u, v, w, stream=None):
+    import torch
+    n = u.numel()
+    dev = u.device
+    out = dict(cu=torch.empty(n, dtype=torch.int32, device=dev),
+               cv=torch.empty(n, dtype=torch.int32, device=dev),
+               ou=torch.empty(n, dtype=torch.int32, device=dev),
+               ov=torch.empty(n, dtype=torch.int32, device=dev),
+               plane=torch.empty(n, dtype=torch.int32, device=dev),
+               conj=torch.empty(n, dtype=torch.uint8, device=dev),
+               keep=torch.empty(n, dtype=torch.uint8, device=dev))
+    ctx.check(LIB.sepw_locate(ctx.handle, n, _ptr(u, torch.float64, n, "u"),
+                              _ptr(v, torch.float64, n, "v"), _ptr(w, torch.float64, n, "w"),
+                              *[out[k].data_ptr() for k in
+                                ("cu", "cv", "ou", "ov", "plane", "conj", "keep")],
+                              _stream(stream)))
+    return out
+
+
+def sepw_plan(ctx: Context, u, v, w, stream=None):
+    import torch
+    n = u.numel()
+    ctx.check(LIB.sepw_plan(ctx.handle, n, _ptr(u, torch.float64, n, "u"),
+                            _ptr(v, torch.float64, n, "v"), _ptr(w, torch.float64, n, "w"),
+                            _stream(stream)))
+    ctx.plan_nvis = n
+
+
+def sepw_plan_dropped(ctx: Context, stream=None) -> int:
+    out = _I64(0)
+    ctx.check(LIB.sepw_plan_dropped(ctx.handle, ctypes.byref(out), _stream(stream)))
+    return int(out.value)
+
+
+def sepw_grid(ctx: Context, taps, u, v, w, vis, weight, grid, n_dropped=None, stream=None):
+    import torch
+    n = u.numel()
+    N = ctx.params.grid_size
+    ctx.check(LIB.sepw_grid(ctx.handle, _ptr(taps, torch.complex64, ctx.ntaps, "taps"), n,
+                            _ptr(u, torch.float64, n, "u"), _ptr(v, torch.float64, n, "v"),
+                            _ptr(w, torch.float64, n, "w"),
+                            _ptr(vis, torch.complex64, n, "vis"),
+                            _ptr(weight, torch.float32, n, "weight"),
+                            _ptr(grid, torch.complex64, N * N, "grid"),
+                            _ptr(n_dropped, torch.int64, 1, "n_dropped"), _stream(stream)))
+    ctx.plan_nvis = n
+    return grid
+
+
+def sepw_grid_planned(ctx: Context, taps, vis, weight, grid, stream=None):
+    import torch
+    n = ctx.plan_nvis
+    N = ctx.params.grid_size
+    ctx.check(LIB.sepw_grid_planned(ctx.handle, _ptr(taps, torch.complex64, ctx.ntaps, "taps"),
+                                    _ptr(vis, torch.complex64, n, "vis"),
+                                    _ptr(weight, torch.float32, n, "weight"),
+                                    _ptr(grid, torch.complex64, N * N, "grid"),
+                                    _stream(stream)))
+    return grid
+
+
+def sepw_degrid(ctx: Context, taps, u, v, w, grid, weight, vis_out, n_dropped=None,
+                stream=None):
+    import torch
+    n = u.numel()
+    N = ctx.params.grid_size
+    ctx.check(LIB.sepw_degrid(ctx.handle, _ptr(taps, torch.complex64, ctx.ntaps, "taps"), n,
+                              _ptr(u, torch.float64, n, "u"), _ptr(v, torch.float64, n, "v"),
+                              _ptr(w, torch.float64, n, "w"),
+                              _ptr(grid, torch.complex64, N * N, "grid"),
+                              _ptr(weight, torch.float32, n, "weight"),
+                              _ptr(vis_out, torch.complex64, n, "vis_out"),
+                              _ptr(n_dropped, torch.int64, 1, "n_dropped"), _stream(stream)))
+    ctx.plan_nvis = n
+    return vis_out
+
+
+def sepw_degrid_planned(ctx: Context, taps, grid, weight, vis_out, stream=None):
+    import torch
+    n = ctx.plan_nvis
+    N = ctx.params.grid_size
+    ctx.check(LIB.sepw_degrid_planned(ctx.handle,
+                                      _ptr(taps, torch.complex64, ctx.ntaps, "taps"),
+                                      _ptr(grid, torch.complex64, N * N, "grid"),
+                                      _ptr(weight, torch.float32, n, "weight"),
+                                      _ptr(vis_out, torch.complex64, n, "vis_out"),
+                                      _stream(stream)))
+    return vis_out
+
+
+def sepw_image(ctx: Context, direction: int, buf, stream=None):
+    import torch
+    N = ctx.params.grid_size
+    ctx.check(LIB.sepw_image(ctx.handle, int(direction),
+                             _ptr(buf, torch.complex64, N * N, "buf"), _stream(stream)))
+    return buf
