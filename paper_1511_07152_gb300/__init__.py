@@ -11,8 +11,13 @@ raises if it is missing (there is no CPU fallback).  ``build`` compiles it.
 import importlib
 
 
+_SUBMODULES = ("build", "sepw")
+
+
 def __getattr__(name):
     if name.startswith("__"):
         raise AttributeError(name)
+    if name in _SUBMODULES:
+        return importlib.import_module(f"{__name__}.{name}")
     mod = importlib.import_module(__name__ + ".sepw")
     return getattr(mod, name)
