@@ -177,7 +177,7 @@ def run_ours(args):
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    wl = synth.meerkat_like()
+    wl = synth.meerkat_like(ndumps=args.dumps)
     N = wl.grid_size
     nvis = wl.nvis
     dev = {k: torch.from_numpy(getattr(wl, k)).cuda() for k in ("u", "v", "w", "vis", "weight")}
@@ -349,6 +349,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--dumps", type=int, default=1000,
+                    help="time dumps of the workload (1000 = the 32,256,000-vis bench; "
+                         "smaller values only for profiling captures)")
     ap.add_argument("--cpu-sample", type=int, default=4_000_000,
                     help="visibilities in the oracle's timed sample (about 10-15 s)")
     ap.add_argument("--ref-sample", type=int, default=1_000_000,

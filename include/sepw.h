@@ -62,6 +62,7 @@ extern "C" {
 #define SEPW_ETIMEOUT (-4) /* a bounded device wait gave up */
 #define SEPW_ENOTSUP (-5)  /* form not available for these parameters */
 #define SEPW_ENOPLAN (-6)  /* *_planned call without a current plan */
+#define SEPW_ETOOLARGE (-7) /* sepw_grid_noalloc: beyond its fixed scratch */
 
 /* kernel forms (sepw_params.form) */
 #define SEPW_FORM_PLAIN 0  /* plain FP32: one global atomic per cell update */
@@ -194,6 +195,38 @@ SEPW_API int sepw_degrid_planned(sepw_ctx *ctx, const float *taps, const float *
  * with n_ab = sqrt(1 - l_a^2 - m_b^2).  Uses cuFFT (FP32 C2C); the plan is
  * created on first use. */
 SEPW_API int sepw_image(sepw_ctx *ctx, int direction, float *buf, sepw_stream_t stream);
+
+/* Limits of sepw_grid_noalloc's fixed scratch array. */
+#define SEPW_NOALLOC_MAX_VIS 524288    /* visibilities per call            */
+#define SEPW_NOALLOC_MAX_TILES 65536   /* ((N - S)/T + 1)^2 tiles per grid */
+
+/* Gridding that allocates no device memory.  The paper has no counterpart:
+ * this is a service for callers that cannot let a library allocate, such as
+ * a real-time pipeline that reserves all of its device memory at start-up and
+ * must not block on cudaMalloc (which may synchronise the device) while it
+ * observes, or a plugin inside a framework that owns the device memory pool.
+ *
+ * Same result as sepw_grid with the tiled FP32 form (p->form is ignored), but
+ * no context is needed and nothing is allocated: the binning workspace is one
+ * file-scope device array of about 16 MB compiled into the library, which
+ * every GPU that loads the library keeps until the process exits.  The call
+ * makes no cudaMalloc / cudaFree and no allocating library call.
+ *   - p, taps, u, v, w, vis, weight (NULL = 1), grid (accumulated, +=):
+ *     as for sepw_grid; n_dropped: device int64 or NULL.
+ *   - nvis > SEPW_NOALLOC_MAX_VIS, or a grid/tile combination with more than
+ *     SEPW_NOALLOC_MAX_TILES tiles, returns SEPW_ETOOLARGE before anything is
+ *     enqueued; split the visibilities into several calls instead (gridding
+ *     accumulates).
+ *   - The first call on each device looks up the array's device address
+ *     (with that device current) and caches it; make that first call before
+ *     any stream capture on the device.
+ *   - Every call reuses the same array.  Calls whose GPU work overlaps (two
+ *     streams, two host threads, two devices' calls are fine) race on it and
+ *     give wrong results: serialise them. */
+SEPW_API int sepw_grid_noalloc(const sepw_params *p, const float *taps, int64_t nvis,
+                               const double *u, const double *v, const double *w,
+                               const float *vis, const float *weight, float *grid,
+                               int64_t *n_dropped, sepw_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -181,6 +181,7 @@ const char *sepw_strerror(int status)
     case SEPW_ETIMEOUT: return "device wait timed out";
     case SEPW_ENOTSUP: return "not supported for these parameters";
     case SEPW_ENOPLAN: return "no current plan";
+    case SEPW_ETOOLARGE: return "size exceeds the fixed scratch of sepw_grid_noalloc";
     default: return "unknown status";
     }
 }

@@ -19,7 +19,9 @@ FORM_TILED = 1
 GRID_TO_IMAGE = 0
 IMAGE_TO_GRID = 1
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP, ENOPLAN = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP, ENOPLAN, ETOOLARGE = 0, -1, -2, -3, -4, -5, -6, -7
+NOALLOC_MAX_VIS = 524288
+NOALLOC_MAX_TILES = 65536
 
 
 class SepwError(RuntimeError):
@@ -73,6 +75,8 @@ _SIG = {
     "sepw_degrid": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "sepw_degrid_planned": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "sepw_image": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "sepw_grid_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _P, _I64, _P, _P, _P, _P,
+                                         _P, _P, _P, _P]),
 }
 
 
@@ -294,3 +298,24 @@ def sepw_image(ctx: Context, direction: int, buf, stream=None):
     ctx.check(LIB.sepw_image(ctx.handle, int(direction),
                              _ptr(buf, torch.complex64, N * N, "buf"), _stream(stream)))
     return buf
+
+
+def sepw_grid_noalloc(params: Params, taps, u, v, w, vis, weight, grid, n_dropped=None,
+                      stream=None) -> int:
+    """Gridding without any device allocation (fixed scratch compiled into the
+    library).  Returns the status code instead of raising, so a caller can see
+    SEPW_ETOOLARGE."""
+    import torch
+    n = u.numel()
+    N = params.grid_size
+    ntaps = params.n_wplanes * params.oversample * params.support
+    return int(LIB.sepw_grid_noalloc(ctypes.byref(params),
+                                     _ptr(taps, torch.complex64, ntaps, "taps"), n,
+                                     _ptr(u, torch.float64, n, "u"),
+                                     _ptr(v, torch.float64, n, "v"),
+                                     _ptr(w, torch.float64, n, "w"),
+                                     _ptr(vis, torch.complex64, n, "vis"),
+                                     _ptr(weight, torch.float32, n, "weight"),
+                                     _ptr(grid, torch.complex64, N * N, "grid"),
+                                     _ptr(n_dropped, torch.int64, 1, "n_dropped"),
+                                     _stream(stream)))
