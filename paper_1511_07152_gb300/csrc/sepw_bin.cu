@@ -1,8 +1,9 @@
 // Plan construction for the tiled forms: locate every visibility, bin it by
 // the T x T tile that holds its footprint origin (counting sort with
 // warp-aggregated atomics), cut each tile into work items of at most kChunk
-// visibilities, and sort each item by footprint origin so that consecutive
-// visibilities with the same origin can be accumulated in registers.
+// visibilities, and sort each item by (footprint origin, conj) so that
+// consecutive visibilities with the same origin and kernel conjugation can be
+// accumulated in one register block.
 //
 // The update structure this serves is Sec. 5: every visibility adds a
 // separable S x S block at its own offset; visibilities that share a tile
@@ -134,50 +135,59 @@ __global__ void __launch_bounds__(256) scatter_kernel(
     rec[slot] = rec0[i];
 }
 
-// Pass 4: inside each work item, counting sort by footprint origin
-// (ly * 64 + lx).  One block per item; the item's slots are rewritten in
-// place.  Block-local; the order among equal origins is arbitrary.
-constexpr int kSortBins = 64 * 64;
+// Pass 4: inside each work item, counting sort by (footprint origin, conj):
+// key = ((ly * T + lx) << 1) | conj.  Visibilities that share a key share one
+// register block in the tiled kernels, and the block never mixes conjugated
+// and plain kernels.  One block per item; the item's slots are rewritten in
+// place.  The order among equal keys is arbitrary.
+constexpr int kSortThreads = 512;
+constexpr int kMaxSortBins = 2 * 64 * 64;
+constexpr int kMaxBinsPerThread = kMaxSortBins / kSortThreads;
 
-__global__ void __launch_bounds__(512) item_sort_kernel(const WorkItem *__restrict__ items,
-                                                        const int32_t *__restrict__ nitems,
-                                                        int32_t *__restrict__ perm,
-                                                        uint64_t *__restrict__ rec)
+__device__ __forceinline__ int sort_key(uint64_t r, int T)
 {
-    __shared__ int32_t hist[kSortBins];
+    return ((rec_ly(r) * T + rec_lx(r)) << 1) | (rec_conj(r) ? 1 : 0);
+}
+
+__global__ void __launch_bounds__(kSortThreads) item_sort_kernel(
+    const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems, int T,
+    int32_t *__restrict__ perm, uint64_t *__restrict__ rec)
+{
+    extern __shared__ int32_t hist[];  // per * kSortThreads bins
     __shared__ uint64_t s_rec[kChunk];
     __shared__ int32_t s_perm[kChunk];
     __shared__ int32_t s_wsum[32];
-    int item = blockIdx.x;
+    const int item = blockIdx.x;
     if (item >= *nitems)
         return;
-    WorkItem it = items[item];
+    const WorkItem it = items[item];
     const int n = it.count;
-    for (int b = threadIdx.x; b < kSortBins; b += blockDim.x)
+    const int nb = 2 * T * T;
+    const int per = (nb + kSortThreads - 1) / kSortThreads;
+    for (int b = threadIdx.x; b < per * kSortThreads; b += kSortThreads)
         hist[b] = 0;
     __syncthreads();
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-        uint64_t r = rec[it.start + q];
+    for (int q = threadIdx.x; q < n; q += kSortThreads) {
+        const uint64_t r = rec[it.start + q];
         s_rec[q] = r;
         s_perm[q] = perm[it.start + q];
-        atomicAdd(hist + rec_ly(r) * 64 + rec_lx(r), 1);
+        atomicAdd(hist + sort_key(r, T), 1);
     }
     __syncthreads();
-    // exclusive scan of hist: each thread owns 8 consecutive bins
-    const int per = kSortBins / 512;
-    int t = threadIdx.x;
-    int local[per];
+    // exclusive scan: thread t owns bins [t*per, t*per + per)
+    const int t = threadIdx.x;
+    int local[kMaxBinsPerThread];
     int sum = 0;
 #pragma unroll
-    for (int q = 0; q < per; ++q) {
-        local[q] = hist[t * per + q];
+    for (int q = 0; q < kMaxBinsPerThread; ++q) {
+        local[q] = q < per ? hist[t * per + q] : 0;
         sum += local[q];
     }
-    int lane = t & 31, warp = t >> 5;
+    const int lane = t & 31, warp = t >> 5;
     int incl = sum;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, incl, off);
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
         if (lane >= off)
             incl += y;
     }
@@ -185,28 +195,30 @@ __global__ void __launch_bounds__(512) item_sort_kernel(const WorkItem *__restri
         s_wsum[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        int x = lane < 16 ? s_wsum[lane] : 0;
+        const int nw = kSortThreads / 32;
+        const int x = lane < nw ? s_wsum[lane] : 0;
         int y = x;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            int z = __shfl_up_sync(0xffffffffu, y, off);
+            const int z = __shfl_up_sync(0xffffffffu, y, off);
             if (lane >= off)
                 y += z;
         }
-        if (lane < 16)
+        if (lane < nw)
             s_wsum[lane] = y - x;  // exclusive warp offsets
     }
     __syncthreads();
     int run = s_wsum[warp] + incl - sum;
 #pragma unroll
-    for (int q = 0; q < per; ++q) {
-        hist[t * per + q] = run;
+    for (int q = 0; q < kMaxBinsPerThread; ++q) {
+        if (q < per)
+            hist[t * per + q] = run;
         run += local[q];
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-        uint64_t r = s_rec[q];
-        int dst = atomicAdd(hist + rec_ly(r) * 64 + rec_lx(r), 1);
+    for (int q = threadIdx.x; q < n; q += kSortThreads) {
+        const uint64_t r = s_rec[q];
+        const int dst = atomicAdd(hist + sort_key(r, T), 1);
         rec[it.start + dst] = r;
         perm[it.start + dst] = s_perm[q];
     }
@@ -255,8 +267,15 @@ cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
             nvis, plan.d_tile, plan.d_rec0, plan.d_tile_cursor, plan.d_perm, plan.d_rec);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
-        item_sort_kernel<<<plan.items_capacity, 512, 0, s>>>(plan.d_items, plan.d_nitems,
-                                                             plan.d_perm, plan.d_rec);
+        const int nb = 2 * p.T * p.T;
+        const size_t shm =
+            sizeof(int32_t) * kSortThreads * ((nb + kSortThreads - 1) / kSortThreads);
+        e = cudaFuncSetAttribute(item_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shm);
+        if (e != cudaSuccess)
+            return e;
+        item_sort_kernel<<<plan.items_capacity, kSortThreads, shm, s>>>(
+            plan.d_items, plan.d_nitems, p.T, plan.d_perm, plan.d_rec);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
     }

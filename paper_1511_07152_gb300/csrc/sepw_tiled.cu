@@ -1,24 +1,33 @@
 // Tiled FP32 gridder and degridder (the separable update of Sec. 5, binned).
 //
 // A persistent CTA takes work items (<= kChunk visibilities of one T x T tile,
-// sorted by footprint origin) from an atomic counter.  The tile's window of
-// (T + S - 1)^2 cells lives in shared memory (separate re / im planes, row
-// stride chosen so a warp's accesses are bank-conflict free).
+// sorted by (footprint origin, conj)) from an atomic counter.  The tile's
+// window of (T + S - 1)^2 cells lives in shared memory (separate re / im
+// planes; row stride chosen so the row groups of a warp hit disjoint banks).
 //
-// Gridding: each warp walks a contiguous range of the item's visibilities.
-// Lane (rg, j) owns footprint column j and rows rg*RPL .. rg*RPL+RPL-1.  Per
-// visibility it forms the partial product W V F1(u - u_i) for its column once
-// (Sec. 5: reused down every row) and accumulates RPL complex products with
-// the v-taps in registers.  While consecutive visibilities share a footprint
-// origin the S x S block stays in registers; when the origin changes it is
-// added into the shared window with shared-memory atomics.  At the end of the
-// item the window is added to the HBM grid once with float2 atomics (windows
-// of neighbouring tiles and other chunks of the same tile overlap).
+// Lane (rg, j) of a warp owns footprint column j and rows rg*RPL ..
+// rg*RPL + RPL - 1.  Each warp walks a contiguous slice of the item.  Per
+// block of 32 visibilities the warp first decodes the records once (one per
+// lane: origin/conj key, tap-row offsets, W V) into shared memory; the inner
+// loop then reads them as broadcasts and loads the v-taps of its rows with
+// 128-bit loads.
 //
-// Degridding (the adjoint): the window is loaded from the HBM grid, each lane
-// forms sum_k conj(tv[k]) X[y_k][x_j] for its rows (the block is re-read from
-// shared memory only when the origin changes), multiplies by conj(tu[j]) and
-// the warp sums the 32 lane partials with shuffles.
+// Gridding: per visibility the lane forms the partial product W V F1(u - u_i)
+// for its column once (Sec. 5: reused down every row) and accumulates RPL
+// complex products with the v-taps into a register block.  A block of
+// visibilities with one key shares the register block; for conj visibilities
+// it accumulates conj(W V) F1 F1 and is conjugated when it is flushed, so the
+// inner loop needs no sign handling.  The register block is added into the
+// shared window (shared-memory atomics) when the key changes, and the window
+// is added to the HBM grid once per item (float2 atomics: windows of
+// neighbouring tiles and other items of the same tile overlap).
+//
+// Degridding (the adjoint): the window is loaded from HBM; the lane keeps its
+// RPL window values (conjugated for plain-kernel groups) in registers while
+// the key is unchanged, forms sum_k F1_v(k) X'(k) and multiplies by F1_u(j).
+// Eight visibilities are reduced over the 32 lanes together (reduce-scatter:
+// 9 shuffles per component instead of 40), then conjugated back as needed and
+// scaled by W.
 #include "sepw_internal.cuh"
 
 namespace sepw {
@@ -27,30 +36,64 @@ template <int S>
 struct Layout {
     static constexpr int RG = (32 / S) > 0 ? (32 / S) : 1;  // row groups per warp
     static constexpr int RPL = (S + RG - 1) / RG;            // rows per lane
+    static constexpr bool VEC = (RPL % 2) == 0;              // 16-byte tap loads
 };
-
-__device__ __forceinline__ float2 cmulf(float2 a, float2 b)
-{
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
 
 constexpr int kTiledThreads = 256;
 constexpr int kTiledWarps = kTiledThreads / 32;
+constexpr int kTiledBlocksPerSM = 3;
+
+__device__ __forceinline__ int key_ly(int key) { return (key >> 1) >> 6; }
+__device__ __forceinline__ int key_lx(int key) { return (key >> 1) & 63; }
+
+// Loads the RPL v-taps of this lane's rows (rows >= S give zero).
+template <int S>
+__device__ __forceinline__ void load_vtaps(const float2 *__restrict__ row, int rg,
+                                           float (&tr)[Layout<S>::RPL],
+                                           float (&ti)[Layout<S>::RPL])
+{
+    constexpr int RPL = Layout<S>::RPL;
+    const int k0 = rg * RPL;
+    if constexpr (Layout<S>::VEC) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(row + k0);
+#pragma unroll
+        for (int q = 0; q < RPL / 2; ++q) {
+            float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k0 + 2 * q < S)
+                t = __ldg(r4 + q);
+            tr[2 * q] = t.x;
+            ti[2 * q] = t.y;
+            tr[2 * q + 1] = t.z;
+            ti[2 * q + 1] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            float2 t = make_float2(0.f, 0.f);
+            if (k0 + q < S)
+                t = __ldg(row + k0 + q);
+            tr[q] = t.x;
+            ti[q] = t.y;
+        }
+    }
+}
 
 template <int S>
-__global__ void __launch_bounds__(kTiledThreads, 2) grid_tiled_kernel(
+__global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_kernel(
     DevParams p, int WP, const WorkItem *__restrict__ items,
     const int32_t *__restrict__ nitems, int32_t *counter, const uint64_t *__restrict__ rec,
     const int32_t *__restrict__ perm, const float2 *__restrict__ vis,
     const float *__restrict__ weight, const float2 *__restrict__ taps, float2 *grid)
 {
     constexpr int RG = Layout<S>::RG, RPL = Layout<S>::RPL;
-    extern __shared__ float smem[];
+    extern __shared__ float4 smem4[];
     __shared__ int s_item;
     const int W = p.T + S - 1;
-    float *wre = smem;
-    float *wim = smem + W * WP;
+    float *wre = reinterpret_cast<float *>(smem4);
+    float *wim = wre + W * WP;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int4 *meta = reinterpret_cast<int4 *>(smem4 + ((2 * W * WP + 3) / 4)) + warp * 32;
+    float2 *wvs = reinterpret_cast<float2 *>(meta + (kTiledWarps - warp) * 32) + warp * 32;
     const int rg = lane / S, j = lane % S;
     const bool lane_ok = rg < RG;
     const int n_items = *nitems;
@@ -72,79 +115,71 @@ __global__ void __launch_bounds__(kTiledThreads, 2) grid_tiled_kernel(
         const int b0 = it.start + min(it.count, warp * per);
         const int b1 = it.start + min(it.count, (warp + 1) * per);
 
-        float2 acc[RPL];
+        float ar[RPL], ai[RPL];
 #pragma unroll
         for (int q = 0; q < RPL; ++q)
-            acc[q] = make_float2(0.f, 0.f);
-        int cur_lx = -1, cur_ly = -1;
+            ar[q] = ai[q] = 0.f;
+        int cur = -1;
+
+        auto flush = [&]() {
+            if (cur >= 0 && lane_ok) {
+                const int ly = key_ly(cur), lx = key_lx(cur);
+                const float sg = (cur & 1) ? -1.f : 1.f;
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) {
+                    const int k = rg * RPL + q;
+                    if (k < S) {
+                        const int a = (ly + k) * WP + lx + j;
+                        atomicAdd(wre + a, ar[q]);
+                        atomicAdd(wim + a, sg * ai[q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RPL; ++q)
+                ar[q] = ai[q] = 0.f;
+        };
 
         for (int base = b0; base < b1; base += 32) {
             const int s = base + lane;
-            uint64_t r = 0;
-            float2 wv = make_float2(0.f, 0.f);
             if (s < b1) {
-                r = rec[s];
+                const uint64_t r = rec[s];
                 const int i = perm[s];
                 const float wt = weight ? __ldg(weight + i) : 1.0f;
                 const float2 x = __ldg(vis + i);
-                wv = make_float2(wt * x.x, wt * x.y);
+                const bool cj = rec_conj(r);
+                const int row = rec_plane(r) * p.OS;
+                meta[lane] = make_int4(((rec_ly(r) * 64 + rec_lx(r)) << 1) | (cj ? 1 : 0),
+                                       (row + rec_ou(r)) * S, (row + rec_ov(r)) * S, 0);
+                wvs[lane] = make_float2(wt * x.x, cj ? -wt * x.y : wt * x.y);
             }
+            __syncwarp();
             const int n = min(32, b1 - base);
             for (int q = 0; q < n; ++q) {
-                const uint64_t rq = __shfl_sync(0xffffffffu, r, q);
-                const float2 wq = make_float2(__shfl_sync(0xffffffffu, wv.x, q),
-                                              __shfl_sync(0xffffffffu, wv.y, q));
-                const int lx = rec_lx(rq), ly = rec_ly(rq);
-                if (lx != cur_lx || ly != cur_ly) {
-                    if (cur_lx >= 0 && lane_ok) {
-#pragma unroll
-                        for (int qq = 0; qq < RPL; ++qq) {
-                            const int k = rg * RPL + qq;
-                            if (k < S) {
-                                const int a = (cur_ly + k) * WP + cur_lx + j;
-                                atomicAdd(wre + a, acc[qq].x);
-                                atomicAdd(wim + a, acc[qq].y);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int qq = 0; qq < RPL; ++qq)
-                        acc[qq] = make_float2(0.f, 0.f);
-                    cur_lx = lx;
-                    cur_ly = ly;
+                const int4 m = meta[q];
+                const float2 wq = wvs[q];
+                if (m.x != cur) {
+                    flush();
+                    cur = m.x;
                 }
-                const float sg = rec_conj(rq) ? -1.f : 1.f;
-                const int64_t row = (int64_t)rec_plane(rq) * p.OS;
-                const float2 *tu = taps + (row + rec_ou(rq)) * S;
-                const float2 *tv = taps + (row + rec_ov(rq)) * S;
                 if (lane_ok) {
-                    float2 a = __ldg(tu + j);
-                    a.y *= sg;
-                    const float2 pu = cmulf(wq, a);
+                    const float2 a = __ldg(taps + m.y + j);
+                    const float pr = wq.x * a.x - wq.y * a.y;
+                    const float pi = wq.x * a.y + wq.y * a.x;
+                    float tr[RPL], ti[RPL];
+                    load_vtaps<S>(taps + m.z, rg, tr, ti);
 #pragma unroll
-                    for (int qq = 0; qq < RPL; ++qq) {
-                        const int k = rg * RPL + qq;
-                        if (k < S) {
-                            float2 b = __ldg(tv + k);
-                            b.y *= sg;
-                            acc[qq].x += pu.x * b.x - pu.y * b.y;
-                            acc[qq].y += pu.x * b.y + pu.y * b.x;
-                        }
+                    for (int k = 0; k < RPL; ++k) {
+                        ar[k] = fmaf(pr, tr[k], ar[k]);
+                        ar[k] = fmaf(-pi, ti[k], ar[k]);
+                        ai[k] = fmaf(pr, ti[k], ai[k]);
+                        ai[k] = fmaf(pi, tr[k], ai[k]);
                     }
                 }
             }
+            __syncwarp();
         }
-        if (cur_lx >= 0 && lane_ok) {
-#pragma unroll
-            for (int qq = 0; qq < RPL; ++qq) {
-                const int k = rg * RPL + qq;
-                if (k < S) {
-                    const int a = (cur_ly + k) * WP + cur_lx + j;
-                    atomicAdd(wre + a, acc[qq].x);
-                    atomicAdd(wim + a, acc[qq].y);
-                }
-            }
-        }
+        flush();
         __syncthreads();
         const int ty = it.tile / p.ntx, tx = it.tile - ty * p.ntx;
         const int64_t gy0 = (int64_t)ty * p.T, gx0 = (int64_t)tx * p.T;
@@ -161,8 +196,34 @@ __global__ void __launch_bounds__(kTiledThreads, 2) grid_tiled_kernel(
     }
 }
 
+// Sum of v[e] over the 32 lanes for e = 0..7; on return v[0] holds the sum
+// for e = (lane >> 2) & 7.
+__device__ __forceinline__ void reduce8(float (&v)[8], int lane)
+{
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = b4 ? v[i] : v[i + 4];
+        const float keep = b4 ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b3 ? v[i] : v[i + 2];
+        const float keep = b3 ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+        const float send = b2 ? v[0] : v[1];
+        const float keep = b2 ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 template <int S>
-__global__ void __launch_bounds__(kTiledThreads, 2) degrid_tiled_kernel(
+__global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) degrid_tiled_kernel(
     DevParams p, int WP, const WorkItem *__restrict__ items,
     const int32_t *__restrict__ nitems, int32_t *counter, const uint64_t *__restrict__ rec,
     const int32_t *__restrict__ perm, const float2 *__restrict__ grid,
@@ -170,12 +231,14 @@ __global__ void __launch_bounds__(kTiledThreads, 2) degrid_tiled_kernel(
     float2 *__restrict__ vis_out)
 {
     constexpr int RG = Layout<S>::RG, RPL = Layout<S>::RPL;
-    extern __shared__ float smem[];
+    extern __shared__ float4 smem4[];
     __shared__ int s_item;
     const int W = p.T + S - 1;
-    float *wre = smem;
-    float *wim = smem + W * WP;
+    float *wre = reinterpret_cast<float *>(smem4);
+    float *wim = wre + W * WP;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int4 *meta = reinterpret_cast<int4 *>(smem4 + ((2 * W * WP + 3) / 4)) + warp * 32;
+    float *wts = reinterpret_cast<float *>(meta + (kTiledWarps - warp) * 32) + warp * 32;
     const int rg = lane / S, j = lane % S;
     const bool lane_ok = rg < RG;
     const int n_items = *nitems;
@@ -209,107 +272,76 @@ __global__ void __launch_bounds__(kTiledThreads, 2) degrid_tiled_kernel(
 #pragma unroll
         for (int q = 0; q < RPL; ++q)
             xr[q] = xi[q] = 0.f;
-        int cur_lx = -1, cur_ly = -1;
+        int cur = -1;
 
         for (int base = b0; base < b1; base += 32) {
             const int s = base + lane;
-            uint64_t r = 0;
-            int i = 0;
             if (s < b1) {
-                r = rec[s];
-                i = perm[s];
+                const uint64_t r = rec[s];
+                const int i = perm[s];
+                const int row = rec_plane(r) * p.OS;
+                meta[lane] = make_int4(((rec_ly(r) * 64 + rec_lx(r)) << 1) |
+                                           (rec_conj(r) ? 1 : 0),
+                                       (row + rec_ou(r)) * S, (row + rec_ov(r)) * S, i);
+                wts[lane] = weight ? __ldg(weight + i) : 1.0f;
             }
-            float2 outv = make_float2(0.f, 0.f);
+            __syncwarp();
             const int n = min(32, b1 - base);
-            for (int q = 0; q < n; ++q) {
-                const uint64_t rq = __shfl_sync(0xffffffffu, r, q);
-                const int lx = rec_lx(rq), ly = rec_ly(rq);
-                if (lx != cur_lx || ly != cur_ly) {
-                    cur_lx = lx;
-                    cur_ly = ly;
-                    if (lane_ok) {
+            for (int qb = 0; qb < n; qb += 8) {
+                float vr[8], vi[8];
 #pragma unroll
-                        for (int qq = 0; qq < RPL; ++qq) {
-                            const int k = rg * RPL + qq;
-                            if (k < S) {
-                                const int a = (ly + k) * WP + lx + j;
-                                xr[qq] = wre[a];
-                                xi[qq] = wim[a];
+                for (int e = 0; e < 8; ++e) {
+                    vr[e] = vi[e] = 0.f;
+                    if (qb + e < n) {
+                        const int4 m = meta[qb + e];
+                        if (m.x != cur) {
+                            cur = m.x;
+                            if (lane_ok) {
+                                const int ly = key_ly(cur), lx = key_lx(cur);
+                                // plain-kernel groups work on conj(X)
+                                const float sg = (cur & 1) ? 1.f : -1.f;
+#pragma unroll
+                                for (int q = 0; q < RPL; ++q) {
+                                    const int k = rg * RPL + q;
+                                    if (k < S) {
+                                        const int a = (ly + k) * WP + lx + j;
+                                        xr[q] = wre[a];
+                                        xi[q] = sg * wim[a];
+                                    }
+                                }
                             }
                         }
-                    }
-                }
-                // conjugate of the gridding kernel: conj(tap) for w >= 0
-                const float sg = rec_conj(rq) ? 1.f : -1.f;
-                const int64_t row = (int64_t)rec_plane(rq) * p.OS;
-                const float2 *tu = taps + (row + rec_ou(rq)) * S;
-                const float2 *tv = taps + (row + rec_ov(rq)) * S;
-                float tre = 0.f, tim = 0.f;
-                if (lane_ok) {
-                    float sre = 0.f, sim = 0.f;
+                        if (lane_ok) {
+                            float tr[RPL], ti[RPL];
+                            load_vtaps<S>(taps + m.z, rg, tr, ti);
+                            float sr = 0.f, si = 0.f;
 #pragma unroll
-                    for (int qq = 0; qq < RPL; ++qq) {
-                        const int k = rg * RPL + qq;
-                        if (k < S) {
-                            float2 b = __ldg(tv + k);
-                            b.y *= sg;
-                            sre += b.x * xr[qq] - b.y * xi[qq];
-                            sim += b.x * xi[qq] + b.y * xr[qq];
+                            for (int k = 0; k < RPL; ++k) {
+                                sr = fmaf(tr[k], xr[k], sr);
+                                sr = fmaf(-ti[k], xi[k], sr);
+                                si = fmaf(tr[k], xi[k], si);
+                                si = fmaf(ti[k], xr[k], si);
+                            }
+                            const float2 a = __ldg(taps + m.y + j);
+                            vr[e] = sr * a.x - si * a.y;
+                            vi[e] = sr * a.y + si * a.x;
                         }
                     }
-                    float2 a = __ldg(tu + j);
-                    a.y *= sg;
-                    tre = sre * a.x - sim * a.y;
-                    tim = sre * a.y + sim * a.x;
                 }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    tre += __shfl_xor_sync(0xffffffffu, tre, off);
-                    tim += __shfl_xor_sync(0xffffffffu, tim, off);
+                reduce8(vr, lane);
+                reduce8(vi, lane);
+                const int e = lane >> 2;
+                if ((lane & 3) == 0 && qb + e < n) {
+                    const int4 m = meta[qb + e];
+                    const float wt = wts[qb + e];
+                    // plain-kernel groups computed conj(V / W)
+                    const float im = (m.x & 1) ? vi[0] : -vi[0];
+                    vis_out[m.w] = make_float2(wt * vr[0], wt * im);
                 }
-                if (lane == q)
-                    outv = make_float2(tre, tim);
             }
-            if (s < b1) {
-                const float wt = weight ? __ldg(weight + i) : 1.0f;
-                vis_out[i] = make_float2(wt * outv.x, wt * outv.y);
-            }
+            __syncwarp();
         }
     }
-}
-
-template <int S>
-static cudaError_t launch_grid_S(const DevParams &p, int WP, const Plan &plan,
-                                 const float2 *vis, const float *weight,
-                                 const float2 *taps, float2 *grid, int num_sms,
-                                 cudaStream_t s)
-{
-    const int W = p.T + S - 1;
-    size_t shm = (size_t)2 * W * WP * sizeof(float);
-    cudaError_t e = cudaMemsetAsync(plan.d_item_counter, 0, sizeof(int32_t), s);
-    if (e != cudaSuccess)
-        return e;
-    grid_tiled_kernel<S><<<num_sms * 2, kTiledThreads, shm, s>>>(
-        p, WP, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm,
-        vis, weight, taps, grid);
-    return cudaGetLastError();
-}
-
-template <int S>
-static cudaError_t launch_degrid_S(const DevParams &p, int WP, const Plan &plan,
-                                   const float2 *grid, const float *weight,
-                                   const float2 *taps, float2 *vis, int num_sms,
-                                   cudaStream_t s)
-{
-    const int W = p.T + S - 1;
-    size_t shm = (size_t)2 * W * WP * sizeof(float);
-    cudaError_t e = cudaMemsetAsync(plan.d_item_counter + 1, 0, sizeof(int32_t), s);
-    if (e != cudaSuccess)
-        return e;
-    degrid_tiled_kernel<S><<<num_sms * 2, kTiledThreads, shm, s>>>(
-        p, WP, plan.d_items, plan.d_nitems, plan.d_item_counter + 1, plan.d_rec,
-        plan.d_perm, grid, weight, taps, vis);
-    return cudaGetLastError();
 }
 
 // Row stride of the shared window: the smallest WP >= W for which the row
@@ -323,7 +355,7 @@ static int window_stride(int W, int S)
         bool ok = true;
         for (int g = 0; g < RG && ok; ++g)
             for (int jj = 0; jj < S && ok; ++jj) {
-                unsigned b = 1u << ((g * RPL * wp + jj) & 31);
+                const unsigned b = 1u << ((g * RPL * wp + jj) & 31);
                 if (used & b)
                     ok = false;
                 used |= b;
@@ -334,6 +366,48 @@ static int window_stride(int W, int S)
     return W;
 }
 
+static size_t tiled_smem(int W, int WP)
+{
+    // window (re + im), then per warp 32 int4 of metadata and 32 x 8 bytes
+    return sizeof(float4) * (size_t)((2 * W * WP + 3) / 4) +
+           (size_t)kTiledWarps * 32 * (sizeof(int4) + sizeof(float2));
+}
+
+template <int S>
+static cudaError_t launch_grid_S(const DevParams &p, const Plan &plan, const float2 *vis,
+                                 const float *weight, const float2 *taps, float2 *grid,
+                                 int num_sms, cudaStream_t s)
+{
+    const int W = p.T + S - 1;
+    const int WP = window_stride(W, S);
+    const size_t shm = tiled_smem(W, WP);
+    cudaError_t e = cudaMemsetAsync(plan.d_item_counter, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess)
+        return e;
+    grid_tiled_kernel<S><<<num_sms * kTiledBlocksPerSM, kTiledThreads, shm, s>>>(
+        p, WP, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm,
+        vis, weight, taps, grid);
+    return cudaGetLastError();
+}
+
+template <int S>
+static cudaError_t launch_degrid_S(const DevParams &p, const Plan &plan,
+                                   const float2 *grid, const float *weight,
+                                   const float2 *taps, float2 *vis, int num_sms,
+                                   cudaStream_t s)
+{
+    const int W = p.T + S - 1;
+    const int WP = window_stride(W, S);
+    const size_t shm = tiled_smem(W, WP);
+    cudaError_t e = cudaMemsetAsync(plan.d_item_counter + 1, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess)
+        return e;
+    degrid_tiled_kernel<S><<<num_sms * kTiledBlocksPerSM, kTiledThreads, shm, s>>>(
+        p, WP, plan.d_items, plan.d_nitems, plan.d_item_counter + 1, plan.d_rec,
+        plan.d_perm, grid, weight, taps, vis);
+    return cudaGetLastError();
+}
+
 #define SEPW_FOR_EACH_S(X) \
     X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24) X(26) X(28) X(30) X(32)
 
@@ -341,10 +415,9 @@ cudaError_t launch_grid_tiled(const DevParams &p, const Plan &plan, const float2
                               const float *weight, const float2 *taps, float2 *grid,
                               int num_sms, cudaStream_t s)
 {
-    const int WP = window_stride(p.T + p.S - 1, p.S);
     switch (p.S) {
 #define X(SS) \
-    case SS: return launch_grid_S<SS>(p, WP, plan, vis, weight, taps, grid, num_sms, s);
+    case SS: return launch_grid_S<SS>(p, plan, vis, weight, taps, grid, num_sms, s);
         SEPW_FOR_EACH_S(X)
 #undef X
     default:
@@ -357,10 +430,9 @@ cudaError_t launch_degrid_tiled(const DevParams &p, const Plan &plan,
                                 const float2 *taps, float2 *vis, int num_sms,
                                 cudaStream_t s)
 {
-    const int WP = window_stride(p.T + p.S - 1, p.S);
     switch (p.S) {
 #define X(SS) \
-    case SS: return launch_degrid_S<SS>(p, WP, plan, grid, weight, taps, vis, num_sms, s);
+    case SS: return launch_degrid_S<SS>(p, plan, grid, weight, taps, vis, num_sms, s);
         SEPW_FOR_EACH_S(X)
 #undef X
     default:
