@@ -165,6 +165,63 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _time_form(S, torch, ctx, taps, dev, grid, out, steps, warmup, stream, evs_out=None):
+    """Times `steps` steps (zero grid, plan, grid, degrid) of one form.
+    Returns (ms per step, plan ms, grid ms, degrid ms)."""
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        grid.zero_()
+        S.sepw_plan(ctx, dev["u"], dev["v"], dev["w"])
+        if ev:
+            ev[1].record(stream)
+        S.sepw_grid_planned(ctx, taps, dev["vis"], dev["weight"], grid)
+        if ev:
+            ev[2].record(stream)
+        S.sepw_degrid_planned(ctx, taps, grid, dev["weight"], out)
+        if ev:
+            ev[3].record(stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(steps):
+        step(evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if S.sepw_device_status(ctx) != S.OK:
+        raise RuntimeError("a kernel recorded a device wait timeout")
+    ms = t0.elapsed_time(t1) / steps
+    return (ms, statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
+            statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
+            statistics.mean(e[2].elapsed_time(e[3]) for e in evs))
+
+
+def _form_errors(S, torch, wl, forms):
+    """Relative L2 of each form's grid against the FP64 oracle on a seeded 1%
+    subsample of the workload (gridded on the full 4096^2 grid)."""
+    import oracle as O
+    sub = wl.subsample(wl.nvis // 100)
+    p = O.params_from(sub.params())
+    loc = O.locate(p, sub.u, sub.v, sub.w)
+    want = O.grid_separable(p, loc, sub.vis, sub.weight, O.taps(p))
+    nrm = np.linalg.norm(want)
+    d = {k: torch.from_numpy(getattr(sub, k)).cuda() for k in ("u", "v", "w", "vis", "weight")}
+    errs = {}
+    for name, form in forms.items():
+        ctx = S.sepw_create(S.make_params(**sub.params(), form=form))
+        taps = S.sepw_make_taps(ctx)
+        g = torch.zeros((sub.grid_size, sub.grid_size), dtype=torch.complex64, device="cuda")
+        S.sepw_grid(ctx, taps, d["u"], d["v"], d["w"], d["vis"], d["weight"], g)
+        errs[name] = float(np.linalg.norm(g.cpu().numpy().astype(np.complex128) - want) / nrm)
+        ctx.close()
+    return errs, sub.nvis
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -191,76 +248,69 @@ def run_ours(args):
     ndrop = S.sepw_plan_dropped(ctx)
     nkept = nvis - ndrop
 
-    def step(ev=None):
-        if ev:
-            ev[0].record(stream)
-        grid.zero_()
-        S.sepw_plan(ctx, dev["u"], dev["v"], dev["w"])
-        if ev:
-            ev[1].record(stream)
-        S.sepw_grid_planned(ctx, taps, dev["vis"], dev["weight"], grid)
-        if ev:
-            ev[2].record(stream)
-        S.sepw_degrid_planned(ctx, taps, grid, dev["weight"], out)
-        if ev:
-            ev[3].record(stream)
-
-    for _ in range(args.warmup):
-        step()
+    # ---- headline: tiled FP32 form, whole hot path per step ----
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     clocks = Clocks(local)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    t_start.record(stream)
-    for k in range(args.steps):
-        step(evs[k])
-    t_end.record(stream)
-    torch.cuda.synchronize()
+    t_start = time.perf_counter()
+    ms, plan_ms, grid_ms, degrid_ms = _time_form(S, torch, ctx, taps, dev, grid, out,
+                                                 args.steps, args.warmup, stream)
     clk = clocks.stop()
-    total_ms = t_start.elapsed_time(t_end)
     if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
+        t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms = total_ms / args.steps
-    plan_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
-    grid_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
-    degrid_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+        ms = float(t.item())
     value = 2.0 * nvis * ws / (ms * 1e-3)
+    forms = {"tiled_fp32": {"value": value, "unit": "vis/s", "ms_per_step": ms,
+                            "phases_ms": {"plan": plan_ms, "grid": grid_ms,
+                                          "degrid": degrid_ms}}}
+
+    # ---- tensor-core contraction forms (grid on tcgen05, degrid tiled FP32) ----
+    peaks, peak_src = _peaks()
+    if not args.skip_tc:
+        for name, form in (("tc_bf16", S.FORM_TC_BF16), ("tc_fp16", S.FORM_TC_FP16)):
+            c2 = S.sepw_create(S.make_params(**wl.params(), form=form))
+            fms, fp, fg, fd = _time_form(S, torch, c2, taps, dev, grid, out,
+                                         max(3, args.steps // 2), 2, stream)
+            # executed dense MMA flops: one M128 x N64 x K16 MMA per 8 visibilities
+            # of a stage, K = 2 real components per visibility
+            mma_flops = 2 * 128 * 64 * 2 * nkept
+            forms[name] = {"value": 2.0 * nvis * ws / (fms * 1e-3), "unit": "vis/s",
+                           "ms_per_step": fms,
+                           "phases_ms": {"plan": fp, "grid": fg, "degrid": fd},
+                           "tensor_roofline": {
+                               "bound": "tensor", "unit": "TFLOP/s",
+                               "achieved": mma_flops / (fg * 1e-3) / 1e12,
+                               "peak": float(peaks["bf16_tflops"]),
+                               "frac": mma_flops / (fg * 1e-3) / 1e12 /
+                               float(peaks["bf16_tflops"]),
+                               "note": "dense MMA flops executed (2 x 128 x 64 x 2 per vis) "
+                                       "over the grid kernel; burst bf16 peak (fp16 same)"}}
+            c2.close()
 
     # ---- plain FP32 form on the same data (the comparator) ----
-    plain = None
     if not args.skip_plain:
         ctxp = S.sepw_create(S.make_params(**wl.params(), form=S.FORM_PLAIN))
-        gp = torch.zeros_like(grid)
-        op = torch.empty_like(out)
-
-        def pstep():
-            gp.zero_()
-            S.sepw_plan(ctxp, dev["u"], dev["v"], dev["w"])
-            S.sepw_grid_planned(ctxp, taps, dev["vis"], dev["weight"], gp)
-            S.sepw_degrid_planned(ctxp, taps, gp, dev["weight"], op)
-        pstep()
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        npl = max(1, min(3, args.steps))
-        a.record(stream)
-        for _ in range(npl):
-            pstep()
-        b.record(stream)
-        torch.cuda.synchronize()
-        pms = a.elapsed_time(b) / npl
-        plain = {"value": 2.0 * nvis * ws / (pms * 1e-3), "unit": "vis/s",
-                 "ms_per_step": pms, "steps": npl,
-                 "speedup_of_tiled": pms / ms}
+        pms, pp, pg, pd = _time_form(S, torch, ctxp, taps, dev, grid, out,
+                                     max(1, min(3, args.steps)), 1, stream)
+        forms["plain_fp32"] = {"value": 2.0 * nvis * ws / (pms * 1e-3), "unit": "vis/s",
+                               "ms_per_step": pms,
+                               "phases_ms": {"plan": pp, "grid": pg, "degrid": pd}}
         ctxp.close()
 
-    # ---- end to end through the C ABI with host buffers ----
+    # ---- grid error of each form on a 1% subsample (FP64 oracle) ----
+    if rank == 0 and not args.skip_errors:
+        fm = {"tiled_fp32": S.FORM_TILED, "plain_fp32": S.FORM_PLAIN}
+        if not args.skip_tc:
+            fm.update(tc_bf16=S.FORM_TC_BF16, tc_fp16=S.FORM_TC_FP16)
+        errs, nsub = _form_errors(S, torch, wl, fm)
+        for k, e in errs.items():
+            if k in forms:
+                forms[k]["grid_rel_l2_vs_fp64"] = e
+        forms["error_sample"] = f"{nsub} seeded visibilities (1%), full 4096^2 grid"
+
+    # ---- end to end through the C ABI with host buffers (tiled FP32) ----
     e2e = None
     if not args.skip_e2e:
         host = {k: torch.from_numpy(getattr(wl, k)).pin_memory()
@@ -272,7 +322,10 @@ def run_ours(args):
         def estep():
             for k, t in host.items():
                 dev[k].copy_(t, non_blocking=True)
-            step()
+            grid.zero_()
+            S.sepw_plan(ctx, dev["u"], dev["v"], dev["w"])
+            S.sepw_grid_planned(ctx, taps, dev["vis"], dev["weight"], grid)
+            S.sepw_degrid_planned(ctx, taps, grid, dev["weight"], out)
             hout.copy_(out, non_blocking=True)
         estep()
         torch.cuda.synchronize()
@@ -289,8 +342,7 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": ems}
 
-    # ---- roofline of the dominant kernel ----
-    peaks, peak_src = _peaks()
+    # ---- roofline of the dominant kernel of the headline form ----
     Ssup = wl.support
     flops_per_vis = 8 * Ssup * Ssup + 8 * Ssup
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
@@ -319,6 +371,7 @@ def run_ours(args):
                          f"(locate + FP64 grid + FP64 degrid, {dt:.1f} s)"}
 
     if rank == 0:
+        plain = forms.get("plain_fp32")
         line = {
             "metric": METRIC, "value": value, "unit": "vis/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -331,9 +384,11 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (1.16 GB per step), no flush"},
             "phases_ms": {"plan": plan_ms, "grid": grid_ms, "degrid": degrid_ms},
             "grid_updates_per_s": nkept * Ssup * Ssup * 2 * ws / (ms * 1e-3),
-            "plain_fp32": plain,
+            "speedup_vs_plain_fp32": (plain["ms_per_step"] / ms) if plain else None,
+            "forms": forms,
             "roofline": roofline, "roofline_hbm": roofline_hbm, "peak_source": peak_src,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "wall_s_timed": time.perf_counter() - t_start,
             "gpu_launches": 7 * args.steps,
         }
         print(json.dumps(line))
@@ -359,6 +414,8 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-tc", action="store_true")
+    ap.add_argument("--skip-errors", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -67,6 +67,10 @@ extern "C" {
 /* kernel forms (sepw_params.form) */
 #define SEPW_FORM_PLAIN 0  /* plain FP32: one global atomic per cell update */
 #define SEPW_FORM_TILED 1  /* binned tiles, register/shared accumulation, FP32 */
+#define SEPW_FORM_TC_BF16 2 /* tile contraction on tensor cores (tcgen05): BF16
+                               operands, FP32 accumulation; support <= 16.
+                               Degridding uses the tiled FP32 form. */
+#define SEPW_FORM_TC_FP16 3 /* as SEPW_FORM_TC_BF16 with FP16 operands */
 
 /* image directions (sepw_image) */
 #define SEPW_GRID_TO_IMAGE 0
@@ -86,8 +90,10 @@ typedef struct sepw_params {
                            exact on the axes, Sec. 3)                         */
     double kb_beta;     /* Kaiser-Bessel antialiasing window parameter; the
                            taper is its transform (Sec. 2 kernel C / c)       */
-    int32_t tile;       /* tiled forms: tile edge T in cells (0 = 32);
-                           even, 8..64, T + S - 1 <= 64                       */
+    int32_t tile;       /* tiled forms: tile edge T in cells; even, 8..64,
+                           T + S - 1 <= 64.  0 = 32 for SEPW_FORM_TILED and
+                           the largest even T with T + S - 1 <= 64 for the
+                           tensor-core forms (48 at S = 16)                   */
     int32_t form;       /* SEPW_FORM_*                                        */
 } sepw_params;
 
@@ -184,6 +190,11 @@ SEPW_API int sepw_degrid(sepw_ctx *ctx, const float *taps, int64_t nvis, const d
 SEPW_API int sepw_degrid_planned(sepw_ctx *ctx, const float *taps, const float *grid,
                         const float *weight, float *vis_out,
                         sepw_stream_t stream);
+
+/* Device status of the context's kernels: a kernel that gives up a bounded
+ * wait records SEPW_ETIMEOUT in a device word.  Synchronises `stream`, copies
+ * the word to *status (SEPW_OK if nothing was recorded) and resets it. */
+SEPW_API int sepw_device_status(sepw_ctx *ctx, int *status, sepw_stream_t stream);
 
 /* Image step with grid correction, Sec. 2 (I_D / n = F^-1[grid] / c), in
  * place on an N x N complex64 buffer:

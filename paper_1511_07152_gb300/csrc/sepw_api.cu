@@ -20,6 +20,7 @@ struct sepw_ctx {
     double *d_taper64 = nullptr;
     float *d_taper32 = nullptr;
     double2 *d_tw = nullptr;
+    int32_t *d_status = nullptr;  // SEPW_ETIMEOUT recorded by a kernel
     Plan plan;
     cufftHandle fft = 0;
     bool fft_ready = false;
@@ -51,7 +52,14 @@ int cuda_fail(sepw_ctx *ctx, cudaError_t e, const char *where)
             return cuda_fail((ctx), e_, #call);               \
     } while (0)
 
-int effective_tile(const sepw_params *p) { return p->tile == 0 ? 32 : p->tile; }
+bool is_tc_form(int form) { return form == SEPW_FORM_TC_BF16 || form == SEPW_FORM_TC_FP16; }
+
+int effective_tile(const sepw_params *p)
+{
+    if (p->tile != 0)
+        return p->tile;
+    return is_tc_form(p->form) ? tc_tile_for_support(p->support) : 32;
+}
 
 DevParams make_dev(const sepw_params *p)
 {
@@ -210,7 +218,9 @@ int sepw_check_params(const sepw_params *p)
     const int T = effective_tile(p);
     if (T < 8 || T > 64 || (T & 1) || T + S - 1 > kMaxWindow)
         return SEPW_EINVAL;
-    if (p->form != SEPW_FORM_PLAIN && p->form != SEPW_FORM_TILED)
+    if (p->form != SEPW_FORM_PLAIN && p->form != SEPW_FORM_TILED && !is_tc_form(p->form))
+        return SEPW_ENOTSUP;
+    if (is_tc_form(p->form) && S > 16)
         return SEPW_ENOTSUP;
     return SEPW_OK;
 }
@@ -246,11 +256,14 @@ int sepw_create(sepw_ctx **out, const sepw_params *p)
     }
     const int N = p->grid_size;
     if ((rc = grow(ctx, &ctx->d_taper64, N)) || (rc = grow(ctx, &ctx->d_taper32, N)) ||
-        (rc = grow(ctx, &ctx->d_tw, (size_t)N * p->oversample))) {
+        (rc = grow(ctx, &ctx->d_tw, (size_t)N * p->oversample)) ||
+        (rc = grow(ctx, &ctx->d_status, 1))) {
         sepw_destroy(ctx);
         return rc;
     }
-    e = launch_taper(ctx->dp, ctx->d_taper64, ctx->d_taper32, 0);
+    e = cudaMemset(ctx->d_status, 0, sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = launch_taper(ctx->dp, ctx->d_taper64, ctx->d_taper32, 0);
     if (e == cudaSuccess)
         e = launch_twiddles(ctx->dp, ctx->d_tw, 0);
     if (e == cudaSuccess)
@@ -277,6 +290,7 @@ void sepw_destroy(sepw_ctx *ctx)
     cudaFree(ctx->d_taper64);
     cudaFree(ctx->d_taper32);
     cudaFree(ctx->d_tw);
+    cudaFree(ctx->d_status);
     free_plan(ctx->plan);
     cudaSetDevice(cur);
     delete ctx;
@@ -396,7 +410,15 @@ int sepw_grid_planned(sepw_ctx *ctx, const float *taps, const float *vis,
         SEPW_CUDA(ctx, launch_grid_plain(ctx->dp, pl.nvis, pl.u, pl.v, pl.w,
                                          (const float2 *)vis, weight, (const float2 *)taps,
                                          (float2 *)grid, nullptr, s));
+    } else if (is_tc_form(pl.form)) {
+        if (((uintptr_t)taps) & 15)
+            return fail(ctx, SEPW_EINVAL, "taps must be 16-byte aligned");
+        SEPW_CUDA(ctx, launch_grid_tc(ctx->dp, pl, (const float2 *)vis, weight,
+                                      (const float2 *)taps, (float2 *)grid, ctx->num_sms,
+                                      pl.form == SEPW_FORM_TC_FP16, ctx->d_status, s));
     } else {
+        if (((uintptr_t)taps) & 15)
+            return fail(ctx, SEPW_EINVAL, "taps must be 16-byte aligned");
         SEPW_CUDA(ctx, launch_grid_tiled(ctx->dp, pl, (const float2 *)vis, weight,
                                          (const float2 *)taps, (float2 *)grid,
                                          ctx->num_sms, s));
@@ -427,6 +449,8 @@ int sepw_degrid_planned(sepw_ctx *ctx, const float *taps, const float *grid,
                                            (const float2 *)taps, (float2 *)vis_out,
                                            nullptr, s));
     } else {
+        if (((uintptr_t)taps) & 15)
+            return fail(ctx, SEPW_EINVAL, "taps must be 16-byte aligned");
         SEPW_CUDA(ctx, launch_zero_dropped(pl, (float2 *)vis_out, s));
         SEPW_CUDA(ctx, launch_degrid_tiled(ctx->dp, pl, (const float2 *)grid, weight,
                                            (const float2 *)taps, (float2 *)vis_out,
@@ -473,6 +497,19 @@ int sepw_degrid(sepw_ctx *ctx, const float *taps, int64_t nvis, const double *u,
     if ((rc = sepw_degrid_planned(ctx, taps, grid, weight, vis_out, stream)))
         return rc;
     return copy_dropped(ctx, n_dropped, (cudaStream_t)stream);
+}
+
+int sepw_device_status(sepw_ctx *ctx, int *status, sepw_stream_t stream)
+{
+    if (!ctx || !status)
+        return SEPW_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t v = 0;
+    SEPW_CUDA(ctx, cudaMemcpyAsync(&v, ctx->d_status, sizeof(v), cudaMemcpyDeviceToHost, s));
+    SEPW_CUDA(ctx, cudaStreamSynchronize(s));
+    SEPW_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), s));
+    *status = v;
+    return SEPW_OK;
 }
 
 int sepw_image(sepw_ctx *ctx, int direction, float *buf, sepw_stream_t stream)

@@ -1,0 +1,451 @@
+// Tensor-core (tcgen05) contraction form of the separable gridder.
+//
+// Sec. 5 writes the update of a visibility as the separable product
+// W V F1(u - u_i) F1(v - v_i).  Summed over the n visibilities of one tile
+// this is a dense complex contraction: with Bv[i][y] the v-taps of visibility
+// i placed at its row offset inside the tile's window and P[i][x] = W_i V_i
+// times its u-taps placed at its column offset,
+//     G[y][x] = sum_i Bv[i][y] P[i][x]                      (G = Bv^T P).
+// In real arithmetic, with K = (visibility, re/im component):
+//     [G_r; G_i] (128 x 64) = A (128 x 2n) * B (2n x 64),
+//     A[(0,y)][(i,0)] =  Bv_r    A[(0,y)][(i,1)] = -Bv_i
+//     A[(1,y)][(i,0)] =  Bv_i    A[(1,y)][(i,1)] =  Bv_r
+//     B[(i,0)][x]     =  P_r     B[(i,1)][x]     =  P_i
+// which is one tcgen05.mma shape M = 128, N = 64 per K = 16 (8 visibilities).
+// The window is 64 x 64 (tile edge T with T + S - 1 <= 64).
+//
+// Operands: BF16 or FP16 (taps, and W V times the taps), FP32 accumulation in
+// tensor memory.  They are built in shared memory in the no-swizzle K-major
+// canonical layout (8-row x 16-byte core matrices; K-adjacent cores 128 bytes
+// apart, 8-row groups 2048 bytes apart).  Only the non-zero entries of a
+// stage are written, and cleared again once the tensor core has consumed the
+// stage, so the buffers stay zero elsewhere.  Two stages of 64 visibilities
+// are in flight: while the tensor core works on one, the CTA builds the next.
+// One thread issues the MMAs and commits them to the stage's mbarrier.
+//
+// After the last stage of a work item the accumulator is read back with
+// tcgen05.ld, staged in shared memory and added to the HBM grid with float2
+// atomics (windows overlap).  Every wait on an mbarrier is bounded in time;
+// on expiry the kernel records SEPW_ETIMEOUT in the device status word, stops
+// issuing work, waits (bounded) for its own MMAs and frees its tensor memory.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "sepw_internal.cuh"
+
+namespace sepw {
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr int kStageVis = 64;                 // visibilities per stage (K = 128)
+constexpr int kStages = 2;                    // stages in flight
+constexpr int kWin = 64;                      // padded window edge
+constexpr int kM = 128, kN = 64;              // MMA shape
+constexpr int kKStage = 2 * kStageVis;        // K elements per stage
+constexpr int kSBO = (kKStage / 8) * 128;     // bytes between 8-row core groups
+constexpr int kABytes = kM * kKStage * 2;     // 32 KiB
+constexpr int kBBytes = kN * kKStage * 2;     // 16 KiB
+constexpr uint32_t kTmemCols = 64;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+
+struct StageMeta {
+    int tu, tv;     // tap-row offsets in the table
+    int lxy;        // lx | ly << 8 | conj << 16
+    int pad;
+    float wr, wi;   // W V (the taps carry the conjugation of conj visibilities)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const unsigned long long t0 = globaltimer();
+    while (globaltimer() - t0 < kWaitNs)
+        if (mbar_try_wait(bar, parity))
+            return true;
+    return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major canonical layout.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) |
+           ((uint64_t)(kSBO >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A/B = BF16 (fmt 1) or F16 (0),
+// both K-major, N = 64, M = 128.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_fmt)
+{
+    return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(kN >> 3) << 17) |
+           ((uint32_t)(kM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+#define SEPW_TMEM_LD32(taddr, r)                                                          \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "                                \
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"                \
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];" \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), \
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]),             \
+                   "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),         \
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),         \
+                   "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),         \
+                   "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),         \
+                   "=r"(r[31])                                                              \
+                 : "r"(taddr)                                                               \
+                 : "memory")
+
+template <bool FP16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    if constexpr (FP16) {
+        __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+}
+
+// byte offset of element pair (row, visibility ii) in a stage operand
+__device__ __forceinline__ uint32_t op_off(int row, int ii)
+{
+    return (uint32_t)((row >> 3) * kSBO + (ii >> 2) * 128 + (row & 7) * 16 + (ii & 3) * 4);
+}
+
+// Writes (set = true) or clears the non-zeros of one stage.  Work unit
+// g = it * 256 + tid: the warp covers 4 visibilities (ii & 3 = lane & 3) x 8
+// taps (lane >> 2), so the 32 four-byte stores of an instruction fall in 32
+// distinct banks.
+template <int S, bool FP16, bool SET>
+__device__ __forceinline__ void stage_operands(unsigned char *A, unsigned char *B,
+                                               const StageMeta *meta, int nv,
+                                               const float2 *__restrict__ taps)
+{
+    const int tid = threadIdx.x;
+    constexpr int kUnits = kStageVis * 16;  // (ii, tap) pairs for 16 tap slots
+#pragma unroll 1
+    for (int g = tid; g < kUnits; g += kTcThreads) {
+        const int lane = g & 31, wg = g >> 5;
+        const int ii = (wg >> 1) * 4 + (lane & 3);
+        const int k = (wg & 1) * 8 + (lane >> 2);
+        if (ii >= nv || k >= S)
+            continue;
+        const StageMeta m = meta[ii];
+        const int lx = m.lxy & 255, ly = (m.lxy >> 8) & 255;
+        const bool cj = (m.lxy >> 16) & 1;
+        uint32_t a0 = 0, a1 = 0, b0 = 0;
+        if (SET) {
+            float2 tv = __ldg(taps + m.tv + k);
+            float2 tu = __ldg(taps + m.tu + k);
+            if (cj) {
+                tv.y = -tv.y;
+                tu.y = -tu.y;
+            }
+            a0 = pack2<FP16>(tv.x, -tv.y);
+            a1 = pack2<FP16>(tv.y, tv.x);
+            b0 = pack2<FP16>(m.wr * tu.x - m.wi * tu.y, m.wr * tu.y + m.wi * tu.x);
+        }
+        *reinterpret_cast<uint32_t *>(A + op_off(ly + k, ii)) = a0;
+        *reinterpret_cast<uint32_t *>(A + op_off(kWin + ly + k, ii)) = a1;
+        *reinterpret_cast<uint32_t *>(B + op_off(lx + k, ii)) = b0;
+    }
+}
+
+template <int S, bool FP16>
+__global__ void __launch_bounds__(kTcThreads, 2) grid_tc_kernel(
+    DevParams p, const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems,
+    int32_t *counter, const uint64_t *__restrict__ rec, const int32_t *__restrict__ perm,
+    const float2 *__restrict__ vis, const float *__restrict__ weight,
+    const float2 *__restrict__ taps, float2 *grid, int32_t *status)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *Abuf = smem;                                // kStages x 32 KiB
+    unsigned char *Bbuf = smem + kStages * kABytes;            // kStages x 16 KiB
+    StageMeta *meta = reinterpret_cast<StageMeta *>(Bbuf + kStages * kBBytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(meta + kStages * kStageVis);
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_item;
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr uint32_t idesc = instr_desc(FP16 ? 0u : 1u);
+
+    // zero the operand buffers once; they stay zero outside a stage's entries
+    for (int e = tid; e < kStages * (kABytes + kBBytes) / 16; e += kTcThreads)
+        reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        for (int b = 0; b < kStages; ++b)
+            mbar_init(bars + b, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const int n_items = *nitems;
+
+    // running stage count of this CTA: stage t uses buffer t % 2, and its
+    // commit is completion number t / 2 of that buffer's mbarrier
+    int t_global = 0;
+    bool aborted = false;
+
+    for (;;) {
+        if (tid == 0)
+            s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items || aborted)
+            break;
+        const WorkItem it = items[item];
+        const int nst = (it.count + kStageVis - 1) / kStageVis;
+        for (int st = 0; st < nst; ++st, ++t_global) {
+            const int b = t_global & 1;
+            unsigned char *A = Abuf + b * kABytes;
+            unsigned char *B = Bbuf + b * kBBytes;
+            StageMeta *mb = meta + b * kStageVis;
+            if (t_global >= kStages) {
+                // buffer b was used by stage t_global - 2: wait for its MMAs,
+                // then clear its entries
+                if (!mbar_wait(bars + b, ((t_global - kStages) >> 1) & 1))
+                    s_abort = 1;
+                __syncthreads();
+                if (s_abort) {
+                    aborted = true;
+                    break;
+                }
+                tc_fence_after();
+                const int nv_old = mb[0].pad;
+                stage_operands<S, FP16, false>(A, B, mb, nv_old, taps);
+                __syncthreads();
+            }
+            const int v0 = it.start + st * kStageVis;
+            const int nv = min(kStageVis, it.start + it.count - v0);
+            if (tid < nv) {
+                const uint64_t r = rec[v0 + tid];
+                const int i = perm[v0 + tid];
+                const float wt = weight ? __ldg(weight + i) : 1.0f;
+                const float2 x = __ldg(vis + i);
+                const bool cj = rec_conj(r);
+                const int row = rec_plane(r) * p.OS;
+                StageMeta m;
+                m.tu = (row + rec_ou(r)) * S;
+                m.tv = (row + rec_ov(r)) * S;
+                m.lxy = rec_lx(r) | (rec_ly(r) << 8) | ((cj ? 1 : 0) << 16);
+                m.pad = nv;
+                m.wr = wt * x.x;
+                m.wi = wt * x.y;
+                mb[tid] = m;
+            }
+            __syncthreads();
+            stage_operands<S, FP16, true>(A, B, mb, nv, taps);
+            fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+                const int nk = (nv + 7) / 8;  // K = 16 steps holding visibilities
+                for (int q = 0; q < nk; ++q)
+                    mma_f16(tmem, smem_desc(a0 + 256 * q), smem_desc(b0 + 256 * q), idesc,
+                            (st > 0 || q > 0) ? 1u : 0u);
+                mma_commit(bars + b);
+            }
+        }
+        if (aborted)
+            break;
+        // all MMAs of the item are complete once the last stage's are
+        {
+            const int tl = t_global - 1;
+            if (!mbar_wait(bars + (tl & 1), (tl >> 1) & 1))
+                s_abort = 1;
+            __syncthreads();
+            if (s_abort) {
+                aborted = true;
+                break;
+            }
+        }
+        tc_fence_after();
+        // epilogue: TMEM -> shared staging (aliases the B buffers, which are
+        // re-zeroed afterwards) -> float2 atomics into the HBM grid
+        float *stg = reinterpret_cast<float *>(Bbuf);  // [128][64], xor-swizzled
+        {
+            const int q = warp & 3, h = warp >> 2;
+            const int m = 32 * q + lane;
+            uint32_t r[32];
+            SEPW_TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + 32 * h, r);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                const int x = 32 * h + c;
+                stg[m * kWin + (x ^ (m & 31))] = __uint_as_float(r[c]);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        {
+            const int W = p.T + S - 1;
+            const int ty = it.tile / p.ntx, tx = it.tile - ty * p.ntx;
+            const int64_t gy0 = (int64_t)ty * p.T, gx0 = (int64_t)tx * p.T;
+            for (int e = tid; e < W * kWin; e += kTcThreads) {
+                const int y = e >> 6, x = e & 63;
+                if (x >= W)
+                    continue;
+                const float re = stg[y * kWin + (x ^ (y & 31))];
+                const float im = stg[(kWin + y) * kWin + (x ^ ((kWin + y) & 31))];
+                if (re != 0.f || im != 0.f)
+                    atomicAdd(grid + (gy0 + y) * p.N + gx0 + x, make_float2(re, im));
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < kStages * kBBytes / 16; e += kTcThreads)
+            reinterpret_cast<uint4 *>(Bbuf)[e] = make_uint4(0, 0, 0, 0);
+        fence_proxy_async();
+        __syncthreads();
+    }
+
+    if (aborted) {
+        if (tid == 0)
+            atomicExch(status, SEPW_ETIMEOUT);
+        // bounded wait for this CTA's own MMAs before releasing TMEM
+        if (t_global > 0) {
+            const int tl = t_global - 1;
+            mbar_wait(bars + (tl & 1), (tl >> 1) & 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+}
+
+size_t tc_smem_bytes()
+{
+    return (size_t)kStages * (kABytes + kBBytes) + sizeof(StageMeta) * kStages * kStageVis +
+           sizeof(uint64_t) * kStages;
+}
+
+template <int S, bool FP16>
+cudaError_t launch_tc_S(const DevParams &p, const Plan &plan, const float2 *vis,
+                        const float *weight, const float2 *taps, float2 *grid, int num_sms,
+                        int32_t *status, cudaStream_t s)
+{
+    const size_t shm = tc_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(grid_tc_kernel<S, FP16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaMemsetAsync(plan.d_item_counter, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess)
+        return e;
+    grid_tc_kernel<S, FP16><<<2 * num_sms, kTcThreads, shm, s>>>(
+        p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm, vis,
+        weight, taps, grid, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_tile_for_support(int S)
+{
+    int T = kWin - S + 1;
+    return T & ~1;
+}
+
+cudaError_t launch_grid_tc(const DevParams &p, const Plan &plan, const float2 *vis,
+                           const float *weight, const float2 *taps, float2 *grid,
+                           int num_sms, bool fp16, int32_t *status, cudaStream_t s)
+{
+    if (p.T + p.S - 1 > kWin)
+        return cudaErrorInvalidValue;
+#define SEPW_TC_CASE(SS)                                                                   \
+    case SS:                                                                               \
+        return fp16 ? launch_tc_S<SS, true>(p, plan, vis, weight, taps, grid, num_sms,     \
+                                            status, s)                                     \
+                    : launch_tc_S<SS, false>(p, plan, vis, weight, taps, grid, num_sms,    \
+                                             status, s);
+    switch (p.S) {
+        SEPW_TC_CASE(2) SEPW_TC_CASE(4) SEPW_TC_CASE(6) SEPW_TC_CASE(8) SEPW_TC_CASE(10)
+        SEPW_TC_CASE(12) SEPW_TC_CASE(14) SEPW_TC_CASE(16)
+    default:
+        return cudaErrorInvalidValue;
+    }
+#undef SEPW_TC_CASE
+}
+
+}  // namespace sepw

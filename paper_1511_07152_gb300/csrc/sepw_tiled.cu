@@ -8,9 +8,9 @@
 // Lane (rg, j) of a warp owns footprint column j and rows rg*RPL ..
 // rg*RPL + RPL - 1.  Each warp walks a contiguous slice of the item.  Per
 // block of 32 visibilities the warp first decodes the records once (one per
-// lane: origin/conj key, tap-row offsets, W V) into shared memory; the inner
-// loop then reads them as broadcasts and loads the v-taps of its rows with
-// 128-bit loads.
+// lane: origin/conj key, tap-row offsets, W V) into one 16-byte shared-memory
+// record each; the inner loop then reads them as broadcasts and loads the
+// v-taps of its rows with 128-bit loads.
 //
 // Gridding: per visibility the lane forms the partial product W V F1(u - u_i)
 // for its column once (Sec. 5: reused down every row) and accumulates RPL
@@ -37,7 +37,17 @@ struct Layout {
     static constexpr int RG = (32 / S) > 0 ? (32 / S) : 1;  // row groups per warp
     static constexpr int RPL = (S + RG - 1) / RG;            // rows per lane
     static constexpr bool VEC = (RPL % 2) == 0;              // 16-byte tap loads
+    static constexpr bool FULL_ROWS = RG * RPL == S;         // no row beyond S
+    static constexpr bool ALL_LANES = RG * S == 32;          // every lane works
 };
+
+// Per-visibility metadata staged in shared memory, one 16-byte record:
+//   x = row offset of the u-taps in the table, (plane * OS + ou) * S
+//   y = key | (v-tap row - u-tap row) << 13, key = (ly * 64 + lx) << 1 | conj
+//   z, w = gridding: W V (conjugated for conj visibilities) as float bits;
+//          degridding: visibility index, weight as float bits
+__device__ __forceinline__ int meta_key(int y) { return y & 0x1fff; }
+__device__ __forceinline__ int meta_dv(int y) { return y >> 13; }
 
 constexpr int kTiledThreads = 256;
 constexpr int kTiledWarps = kTiledThreads / 32;
@@ -59,7 +69,7 @@ __device__ __forceinline__ void load_vtaps(const float2 *__restrict__ row, int r
 #pragma unroll
         for (int q = 0; q < RPL / 2; ++q) {
             float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (k0 + 2 * q < S)
+            if (Layout<S>::FULL_ROWS || k0 + 2 * q < S)
                 t = __ldg(r4 + q);
             tr[2 * q] = t.x;
             ti[2 * q] = t.y;
@@ -70,7 +80,7 @@ __device__ __forceinline__ void load_vtaps(const float2 *__restrict__ row, int r
 #pragma unroll
         for (int q = 0; q < RPL; ++q) {
             float2 t = make_float2(0.f, 0.f);
-            if (k0 + q < S)
+            if (Layout<S>::FULL_ROWS || k0 + q < S)
                 t = __ldg(row + k0 + q);
             tr[q] = t.x;
             ti[q] = t.y;
@@ -93,9 +103,8 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_k
     float *wim = wre + W * WP;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int4 *meta = reinterpret_cast<int4 *>(smem4 + ((2 * W * WP + 3) / 4)) + warp * 32;
-    float2 *wvs = reinterpret_cast<float2 *>(meta + (kTiledWarps - warp) * 32) + warp * 32;
     const int rg = lane / S, j = lane % S;
-    const bool lane_ok = rg < RG;
+    const bool lane_ok = Layout<S>::ALL_LANES || rg < RG;
     const int n_items = *nitems;
 
     for (int e = threadIdx.x; e < W * WP; e += kTiledThreads) {
@@ -149,25 +158,29 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_k
                 const float2 x = __ldg(vis + i);
                 const bool cj = rec_conj(r);
                 const int row = rec_plane(r) * p.OS;
-                meta[lane] = make_int4(((rec_ly(r) * 64 + rec_lx(r)) << 1) | (cj ? 1 : 0),
-                                       (row + rec_ou(r)) * S, (row + rec_ov(r)) * S, 0);
-                wvs[lane] = make_float2(wt * x.x, cj ? -wt * x.y : wt * x.y);
+                const int key = ((rec_ly(r) * 64 + rec_lx(r)) << 1) | (cj ? 1 : 0);
+                meta[lane] = make_int4((row + rec_ou(r)) * S,
+                                       key | ((rec_ov(r) - rec_ou(r)) * S) * 8192,
+                                       __float_as_int(wt * x.x),
+                                       __float_as_int(cj ? -wt * x.y : wt * x.y));
             }
             __syncwarp();
             const int n = min(32, b1 - base);
             for (int q = 0; q < n; ++q) {
                 const int4 m = meta[q];
-                const float2 wq = wvs[q];
-                if (m.x != cur) {
+                const int key = meta_key(m.y);
+                if (key != cur) {
                     flush();
-                    cur = m.x;
+                    cur = key;
                 }
                 if (lane_ok) {
-                    const float2 a = __ldg(taps + m.y + j);
-                    const float pr = wq.x * a.x - wq.y * a.y;
-                    const float pi = wq.x * a.y + wq.y * a.x;
+                    const float wx = __int_as_float(m.z), wy = __int_as_float(m.w);
+                    const float2 *tu = taps + m.x;
+                    const float2 a = __ldg(tu + j);
+                    const float pr = wx * a.x - wy * a.y;
+                    const float pi = wx * a.y + wy * a.x;
                     float tr[RPL], ti[RPL];
-                    load_vtaps<S>(taps + m.z, rg, tr, ti);
+                    load_vtaps<S>(tu + meta_dv(m.y), rg, tr, ti);
 #pragma unroll
                     for (int k = 0; k < RPL; ++k) {
                         ar[k] = fmaf(pr, tr[k], ar[k]);
@@ -238,9 +251,8 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) degrid_tiled
     float *wim = wre + W * WP;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int4 *meta = reinterpret_cast<int4 *>(smem4 + ((2 * W * WP + 3) / 4)) + warp * 32;
-    float *wts = reinterpret_cast<float *>(meta + (kTiledWarps - warp) * 32) + warp * 32;
     const int rg = lane / S, j = lane % S;
-    const bool lane_ok = rg < RG;
+    const bool lane_ok = Layout<S>::ALL_LANES || rg < RG;
     const int n_items = *nitems;
 
     for (;;) {
@@ -280,10 +292,10 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) degrid_tiled
                 const uint64_t r = rec[s];
                 const int i = perm[s];
                 const int row = rec_plane(r) * p.OS;
-                meta[lane] = make_int4(((rec_ly(r) * 64 + rec_lx(r)) << 1) |
-                                           (rec_conj(r) ? 1 : 0),
-                                       (row + rec_ou(r)) * S, (row + rec_ov(r)) * S, i);
-                wts[lane] = weight ? __ldg(weight + i) : 1.0f;
+                const int key = ((rec_ly(r) * 64 + rec_lx(r)) << 1) | (rec_conj(r) ? 1 : 0);
+                meta[lane] = make_int4((row + rec_ou(r)) * S,
+                                       key | ((rec_ov(r) - rec_ou(r)) * S) * 8192, i,
+                                       __float_as_int(weight ? __ldg(weight + i) : 1.0f));
             }
             __syncwarp();
             const int n = min(32, b1 - base);
@@ -294,8 +306,9 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) degrid_tiled
                     vr[e] = vi[e] = 0.f;
                     if (qb + e < n) {
                         const int4 m = meta[qb + e];
-                        if (m.x != cur) {
-                            cur = m.x;
+                        const int key = meta_key(m.y);
+                        if (key != cur) {
+                            cur = key;
                             if (lane_ok) {
                                 const int ly = key_ly(cur), lx = key_lx(cur);
                                 // plain-kernel groups work on conj(X)
@@ -312,8 +325,9 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) degrid_tiled
                             }
                         }
                         if (lane_ok) {
+                            const float2 *tu = taps + m.x;
                             float tr[RPL], ti[RPL];
-                            load_vtaps<S>(taps + m.z, rg, tr, ti);
+                            load_vtaps<S>(tu + meta_dv(m.y), rg, tr, ti);
                             float sr = 0.f, si = 0.f;
 #pragma unroll
                             for (int k = 0; k < RPL; ++k) {
@@ -322,7 +336,7 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) degrid_tiled
                                 si = fmaf(tr[k], xi[k], si);
                                 si = fmaf(ti[k], xr[k], si);
                             }
-                            const float2 a = __ldg(taps + m.y + j);
+                            const float2 a = __ldg(tu + j);
                             vr[e] = sr * a.x - si * a.y;
                             vi[e] = sr * a.y + si * a.x;
                         }
@@ -333,10 +347,10 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) degrid_tiled
                 const int e = lane >> 2;
                 if ((lane & 3) == 0 && qb + e < n) {
                     const int4 m = meta[qb + e];
-                    const float wt = wts[qb + e];
+                    const float wt = __int_as_float(m.w);
                     // plain-kernel groups computed conj(V / W)
-                    const float im = (m.x & 1) ? vi[0] : -vi[0];
-                    vis_out[m.w] = make_float2(wt * vr[0], wt * im);
+                    const float im = (m.y & 1) ? vi[0] : -vi[0];
+                    vis_out[m.z] = make_float2(wt * vr[0], wt * im);
                 }
             }
             __syncwarp();
@@ -368,9 +382,9 @@ static int window_stride(int W, int S)
 
 static size_t tiled_smem(int W, int WP)
 {
-    // window (re + im), then per warp 32 int4 of metadata and 32 x 8 bytes
+    // window (re + im), then per warp 32 int4 of metadata
     return sizeof(float4) * (size_t)((2 * W * WP + 3) / 4) +
-           (size_t)kTiledWarps * 32 * (sizeof(int4) + sizeof(float2));
+           (size_t)kTiledWarps * 32 * sizeof(int4);
 }
 
 template <int S>

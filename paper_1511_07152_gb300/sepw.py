@@ -16,6 +16,8 @@ from . import build as _build
 
 FORM_PLAIN = 0
 FORM_TILED = 1
+FORM_TC_BF16 = 2
+FORM_TC_FP16 = 3
 GRID_TO_IMAGE = 0
 IMAGE_TO_GRID = 1
 
@@ -75,6 +77,7 @@ _SIG = {
     "sepw_degrid": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "sepw_degrid_planned": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "sepw_image": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "sepw_device_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P]),
     "sepw_grid_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _P, _I64, _P, _P, _P, _P,
                                          _P, _P, _P, _P]),
 }
@@ -290,6 +293,13 @@ def sepw_degrid_planned(ctx: Context, taps, grid, weight, vis_out, stream=None):
                                       _ptr(vis_out, torch.complex64, n, "vis_out"),
                                       _stream(stream)))
     return vis_out
+
+
+def sepw_device_status(ctx: Context, stream=None) -> int:
+    """Status recorded by the context's kernels (OK or ETIMEOUT); resets it."""
+    st = ctypes.c_int(0)
+    ctx.check(LIB.sepw_device_status(ctx.handle, ctypes.byref(st), _stream(stream)))
+    return int(st.value)
 
 
 def sepw_image(ctx: Context, direction: int, buf, stream=None):

@@ -1,0 +1,152 @@
+"""Tensor-core contraction form (tcgen05) of the gridder against the FP64
+oracle.
+
+The operands are rounded to BF16 (unit roundoff u = 2^-8) or FP16 (u = 2^-11)
+and accumulated in FP32.  Every product W V F1(u) F1(v) then carries two
+independent operand roundings, relative rms sqrt(2/3) u, and the grid's
+relative L2 error is about that: 3.2e-3 (BF16) and 4.0e-4 (FP16).  The bars
+below allow a factor ~3: 1e-2 and 1.5e-3.  Degridding in these forms is the
+tiled FP32 path (rel L2 <= 1e-5).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"bf16": 1e-2, "fp16": 1.5e-3}
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1511_07152_gb300 import build
+    build.build()
+    import paper_1511_07152_gb300.sepw as S
+    return torch, S
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.complex128)
+    b = np.asarray(b, np.complex128)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def _form(S, name):
+    return {"bf16": S.FORM_TC_BF16, "fp16": S.FORM_TC_FP16}[name]
+
+
+def _grid(torch, S, wl, form, tile=0):
+    ctx = S.sepw_create(S.make_params(**wl.params(), tile=tile, form=form))
+    taps = S.sepw_make_taps(ctx)
+    d = {k: torch.from_numpy(getattr(wl, k)).cuda() for k in ("u", "v", "w", "vis", "weight")}
+    N = wl.grid_size
+    grid = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+    nd = torch.zeros(1, dtype=torch.int64, device="cuda")
+    S.sepw_grid(ctx, taps, d["u"], d["v"], d["w"], d["vis"], d["weight"], grid, nd)
+    assert S.sepw_device_status(ctx) == S.OK
+    return grid.cpu().numpy(), int(nd.item()), ctx, taps, d
+
+
+def _oracle(wl):
+    p = O.params_from(wl.params())
+    loc = O.locate(p, wl.u, wl.v, wl.w)
+    return O.grid_separable(p, loc, wl.vis, wl.weight, O.taps(p)), loc
+
+
+CASES = {
+    "small_disk_S8": lambda: synth.small_disk(),
+    "rand_S12": lambda: synth.random_case(2, 6000, 160, 12, 16, 17, edge_fraction=0.1),
+    "rand_S16": lambda: synth.random_case(3, 20000, 256, 16, 16, 33, edge_fraction=0.1),
+}
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_tc_grid_parity(env, prec, name):
+    torch, S = env
+    wl = CASES[name]()
+    want, loc = _oracle(wl)
+    got, nd, *_ = _grid(torch, S, wl, _form(S, prec))
+    err = rel_l2(got, want)
+    assert err <= TOL[prec], err
+    assert nd == int((~loc["keep"]).sum())
+
+
+@pytest.mark.parametrize("tile", [16, 32, 48])
+def test_tc_tile_sizes(env, tile):
+    torch, S = env
+    wl = CASES["rand_S16"]()
+    want, _ = _oracle(wl)
+    got, *_ = _grid(torch, S, wl, S.FORM_TC_FP16, tile=tile)
+    assert rel_l2(got, want) <= TOL["fp16"]
+
+
+def test_tc_heavy_tile(env):
+    """One position holds 50,000 visibilities: many work items and stages on
+    one tile, accumulated through several epilogues."""
+    torch, S = env
+    n = 60000
+    rng = np.random.default_rng(4)
+    fov = math.radians(2.0)
+    u = np.concatenate([np.full(50000, 2.2 / fov), rng.uniform(-6, 6, n - 50000) / fov])
+    v = np.concatenate([np.full(50000, -3.9 / fov), rng.uniform(-6, 6, n - 50000) / fov])
+    w = rng.uniform(-300, 300, n)
+    vis = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    wt = rng.uniform(0.5, 1, n).astype(np.float32)
+    wl = synth.Workload("heavy", 96, fov, 16, 16, 9, 300.0, u, v, w, vis, wt)
+    want, _ = _oracle(wl)
+    got, *_ = _grid(torch, S, wl, S.FORM_TC_FP16)
+    assert rel_l2(got, want) <= TOL["fp16"]
+
+
+def test_tc_degrid_uses_fp32_tiled(env):
+    torch, S = env
+    wl = CASES["rand_S16"]()
+    p = O.params_from(wl.params())
+    loc = O.locate(p, wl.u, wl.v, wl.w)
+    rng = np.random.default_rng(8)
+    X = (rng.standard_normal((256, 256)) + 1j * rng.standard_normal((256, 256))
+         ).astype(np.complex64)
+    want = O.degrid_separable(p, loc, X, wl.weight, O.taps(p))
+    _, _, ctx, taps, d = _grid(torch, S, wl, S.FORM_TC_BF16)
+    out = torch.empty(wl.nvis, dtype=torch.complex64, device="cuda")
+    S.sepw_degrid(ctx, taps, d["u"], d["v"], d["w"], torch.from_numpy(X).cuda(),
+                  d["weight"], out)
+    assert rel_l2(out.cpu().numpy(), want) <= 1e-5
+
+
+def test_tc_empty_and_all_dropped(env):
+    torch, S = env
+    wl = CASES["rand_S12"]()
+    ctx = S.sepw_create(S.make_params(**wl.params(), form=S.FORM_TC_BF16))
+    taps = S.sepw_make_taps(ctx)
+    N = wl.grid_size
+    grid = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    S.sepw_grid(ctx, taps, e, e, e, torch.empty(0, dtype=torch.complex64, device="cuda"),
+                None, grid)
+    far = torch.full((50,), 1e12, dtype=torch.float64, device="cuda")
+    S.sepw_grid(ctx, taps, far, far, far, torch.ones(50, dtype=torch.complex64,
+                                                     device="cuda"), None, grid)
+    assert float(grid.abs().sum()) == 0.0
+    assert S.sepw_device_status(ctx) == S.OK
+
+
+def test_tc_meerkat_subsample_errors(env):
+    """1% seeded subsample of the 32,256,000-visibility workload on the full
+    4096^2 grid: each tensor-core form against the FP64 oracle."""
+    torch, S = env
+    wl = synth.meerkat_like()
+    sub = wl.subsample(wl.nvis // 100)
+    want, _ = _oracle(sub)
+    for prec in ("bf16", "fp16"):
+        got, *_ = _grid(torch, S, sub, _form(S, prec))
+        err = rel_l2(got, want)
+        assert err <= TOL[prec], (prec, err)
