@@ -73,6 +73,10 @@ DevParams make_dev(const sepw_params *p)
     d.fov = p->fov;
     d.half = (double)(d.N / 2);
     d.os_d = (double)d.OS;
+    d.os_log2 = -1;
+    for (int k = 0; k < 31; ++k)
+        if ((1 << k) == d.OS)
+            d.os_log2 = k;
     d.plane_r = d.P > 1 ? (double)(d.P - 1) / p->w_max : 0.0;
     d.w_max = p->w_max;
     d.gamma = p->gamma;

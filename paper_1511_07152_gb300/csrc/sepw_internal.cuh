@@ -16,6 +16,7 @@ struct DevParams {
     double fov;       // inverse cell size: x = u * fov + N/2
     double half;      // N/2 as a double
     double os_d;      // OS as a double
+    int32_t os_log2;  // log2(OS) if OS is a power of two, else -1
     double plane_r;   // (P-1)/w_max (0 if P == 1)
     double w_max;
     double gamma;
@@ -29,22 +30,62 @@ struct Loc {
     bool keep;
 };
 
+// Exact floor of a double, in integer arithmetic on its bits (no FP64
+// instruction).  Returns false for NaN, +-inf and |y| >= 2^52 (whose floor is
+// y itself and always outside the accepted range).  Bit-for-bit the same as
+// the IEEE floor() for every other input.
+__device__ __forceinline__ bool floor_bits(double y, long long &out)
+{
+    const long long b = __double_as_longlong(y);
+    const int eb = (int)((b >> 52) & 0x7FF);
+    if (eb >= 1023 + 52)
+        return false;  // huge, inf or NaN
+    const bool neg = b < 0;
+    if (eb < 1023) {  // |y| < 1
+        const bool nonzero = (b & 0x7FFFFFFFFFFFFFFFll) != 0;
+        out = (neg && nonzero) ? -1 : 0;
+        return true;
+    }
+    const int shift = 52 - (eb - 1023);  // 1..52
+    const long long mant = (b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll;
+    const long long ip = mant >> shift;
+    const bool frac = (mant & ((1ll << shift) - 1)) != 0;
+    out = neg ? -ip - (frac ? 1 : 0) : ip;
+    return true;
+}
+
+// x * 2^k, exact: exponent add when x is normal and stays normal, IEEE
+// multiply otherwise (zero, subnormal, overflow; all rounded identically).
+__device__ __forceinline__ double scale_pow2(double x, int k, double os_d)
+{
+    const long long b = __double_as_longlong(x);
+    const int eb = (int)((b >> 52) & 0x7FF);
+    if (eb >= 1 && eb + k <= 2046)
+        return __longlong_as_double(b + ((long long)k << 52));
+    return __dmul_rn(x, os_d);
+}
+
 // Locate one axis: x = coord*fov + N/2, t = floor(x*OS + 0.5) in IEEE double
 // with every operation rounded separately (no FMA contraction), then
 // c = floor(t/OS), o = t - c*OS; the footprint c - S/2 + 1 .. c + S/2 must lie
 // inside [0, N).  Returns false (drop) otherwise or for non-finite input.
+// Only the multiplies and adds use the FP64 pipe; the floor, the range checks
+// and the power-of-two scaling are exact integer operations on the bits.
 __device__ __forceinline__ bool locate_axis(double coord, const DevParams &p,
                                             int32_t &c, int32_t &o)
 {
-    double x = __dadd_rn(__dmul_rn(coord, p.fov), p.half);
-    double t = floor(__dadd_rn(__dmul_rn(x, p.os_d), 0.5));
-    if (!(fabs(t) < 1099511627776.0))  // 2^40; false for NaN
+    const double x = __dadd_rn(__dmul_rn(coord, p.fov), p.half);
+    const double xs = p.os_log2 >= 0 ? scale_pow2(x, p.os_log2, p.os_d)
+                                     : __dmul_rn(x, p.os_d);
+    long long ti;
+    if (!floor_bits(__dadd_rn(xs, 0.5), ti))
         return false;
-    long long ti = (long long)t;
-    long long OS = p.OS;
-    long long cc = ti >= 0 ? ti / OS : -((-ti + OS - 1) / OS);
-    long long oo = ti - cc * OS;
-    long long f = cc - p.S / 2 + 1;
+    if (ti >= 1099511627776ll || ti <= -1099511627776ll)  // |t| < 2^40
+        return false;
+    const long long OS = p.OS;
+    const long long cc = ti >= 0 ? ti / OS : -((-ti + OS - 1) / OS);
+    const long long oo = ti - cc * OS;
+    const long long f = cc - p.S / 2 + 1;
     if (f < 0 || f + p.S - 1 > p.N - 1)
         return false;
     c = (int32_t)cc;
@@ -52,8 +93,8 @@ __device__ __forceinline__ bool locate_axis(double coord, const DevParams &p,
     return true;
 }
 
-// Plane: floor(|w| * r + 0.5) with r = (P-1)/w_max, dropped beyond P-1;
-// conj = (w < 0).
+// Plane: floor(|w| * r + 0.5) with r = (P-1)/w_max, dropped beyond P-1 or if
+// not finite; conj = (w < 0).
 __device__ __forceinline__ Loc locate(double u, double v, double w, const DevParams &p)
 {
     Loc L;
@@ -62,8 +103,12 @@ __device__ __forceinline__ Loc locate(double u, double v, double w, const DevPar
     int32_t cu, cv, ou, ov;
     bool ok = locate_axis(u, p, cu, ou);
     ok = locate_axis(v, p, cv, ov) && ok;
-    double q = floor(__dadd_rn(__dmul_rn(fabs(w), p.plane_r), 0.5));
-    ok = ok && isfinite(w) && (q <= (double)(p.P - 1));
+    const long long wb = __double_as_longlong(w);
+    const double aw = __longlong_as_double(wb & 0x7FFFFFFFFFFFFFFFll);
+    long long q;
+    const bool wfin = ((wb >> 52) & 0x7FF) != 0x7FF;
+    ok = ok && wfin && floor_bits(__dadd_rn(__dmul_rn(aw, p.plane_r), 0.5), q) &&
+         q <= (long long)(p.P - 1);
     L.keep = ok;
     if (ok) {
         L.cu = cu;
@@ -71,7 +116,7 @@ __device__ __forceinline__ Loc locate(double u, double v, double w, const DevPar
         L.ou = ou;
         L.ov = ov;
         L.plane = (int32_t)q;
-        L.conj = w < 0.0;
+        L.conj = wb < 0 && (wb & 0x7FFFFFFFFFFFFFFFll) != 0;
     }
     return L;
 }

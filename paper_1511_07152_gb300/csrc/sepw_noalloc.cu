@@ -119,6 +119,10 @@ extern "C" int sepw_grid_noalloc(const sepw_params *prm, const float *taps, int6
     dp.fov = prm->fov;
     dp.half = (double)(dp.N / 2);
     dp.os_d = (double)dp.OS;
+    dp.os_log2 = -1;
+    for (int k = 0; k < 31; ++k)
+        if ((1 << k) == dp.OS)
+            dp.os_log2 = k;
     dp.plane_r = dp.P > 1 ? (double)(dp.P - 1) / prm->w_max : 0.0;
     dp.w_max = prm->w_max;
     dp.gamma = prm->gamma;

@@ -19,9 +19,11 @@
 // canonical layout (8-row x 16-byte core matrices; K-adjacent cores 128 bytes
 // apart, 8-row groups 2048 bytes apart).  Only the non-zero entries of a
 // stage are written, and cleared again once the tensor core has consumed the
-// stage, so the buffers stay zero elsewhere.  Two stages of 64 visibilities
-// are in flight: while the tensor core works on one, the CTA builds the next.
-// One thread issues the MMAs and commits them to the stage's mbarrier.
+// stage, so the buffers stay zero elsewhere: each of the 512 threads owns one
+// (visibility, tap pair) unit of a stage and clears the same unit two stages
+// later.  Two stages of 64 visibilities are in flight: while the tensor core
+// works on one, the CTA builds the next.  One thread issues the MMAs and
+// commits them to the stage's mbarrier.
 //
 // After the last stage of a work item the accumulator is read back with
 // tcgen05.ld, staged in shared memory and added to the HBM grid with float2
@@ -36,9 +38,10 @@
 namespace sepw {
 namespace {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
 constexpr int kStageVis = 64;                 // visibilities per stage (K = 128)
 constexpr int kStages = 2;                    // stages in flight
+constexpr int kMetaRing = 4;                  // stage metadata slots (>= 2 * kStages)
 constexpr int kWin = 64;                      // padded window edge
 constexpr int kM = 128, kN = 64;              // MMA shape
 constexpr int kKStage = 2 * kStageVis;        // K elements per stage
@@ -159,6 +162,15 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  : "r"(taddr)                                                               \
                  : "memory")
 
+#define SEPW_TMEM_LD16(taddr, r)                                                          \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "                                \
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"          \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), \
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]),             \
+                   "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])          \
+                 : "r"(taddr)                                                               \
+                 : "memory")
+
 template <bool FP16>
 __device__ __forceinline__ uint32_t pack2(float lo, float hi)
 {
@@ -177,31 +189,34 @@ __device__ __forceinline__ uint32_t op_off(int row, int ii)
     return (uint32_t)((row >> 3) * kSBO + (ii >> 2) * 128 + (row & 7) * 16 + (ii & 3) * 4);
 }
 
-// Writes (set = true) or clears the non-zeros of one stage.  Work unit
-// g = it * 256 + tid: the warp covers 4 visibilities (ii & 3 = lane & 3) x 8
-// taps (lane >> 2), so the 32 four-byte stores of an instruction fall in 32
-// distinct banks.
+// Writes (SET) or clears the non-zeros of one stage.  Thread t owns the
+// unit (visibility ii = 4 * (t >> 5) + (t & 3), taps k and k + 8 with
+// k = (t & 31) >> 2): the 32 four-byte stores of a warp instruction then land
+// in 32 distinct banks (row & 7 differs across k, ii & 3 across the lane
+// quads).  The same thread clears the same entries of the stage two steps
+// later, from that stage's metadata.
 template <int S, bool FP16, bool SET>
-__device__ __forceinline__ void stage_operands(unsigned char *A, unsigned char *B,
-                                               const StageMeta *meta, int nv,
-                                               const float2 *__restrict__ taps)
+__device__ __forceinline__ void stage_unit(unsigned char *A, unsigned char *B,
+                                           const StageMeta *meta, int nv,
+                                           const float2 *__restrict__ taps)
 {
     const int tid = threadIdx.x;
-    constexpr int kUnits = kStageVis * 16;  // (ii, tap) pairs for 16 tap slots
-#pragma unroll 1
-    for (int g = tid; g < kUnits; g += kTcThreads) {
-        const int lane = g & 31, wg = g >> 5;
-        const int ii = (wg >> 1) * 4 + (lane & 3);
-        const int k = (wg & 1) * 8 + (lane >> 2);
-        if (ii >= nv || k >= S)
+    const int ii = 4 * (tid >> 5) + (tid & 3);
+    const int k = (tid & 31) >> 2;
+    if (ii >= nv)
+        return;
+    const StageMeta m = meta[ii];
+    const int lx = m.lxy & 255, ly = (m.lxy >> 8) & 255;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int kk = k + 8 * h;
+        if (kk >= S)
             continue;
-        const StageMeta m = meta[ii];
-        const int lx = m.lxy & 255, ly = (m.lxy >> 8) & 255;
-        const bool cj = (m.lxy >> 16) & 1;
         uint32_t a0 = 0, a1 = 0, b0 = 0;
         if (SET) {
-            float2 tv = __ldg(taps + m.tv + k);
-            float2 tu = __ldg(taps + m.tu + k);
+            const bool cj = (m.lxy >> 16) & 1;
+            float2 tv = __ldg(taps + m.tv + kk);
+            float2 tu = __ldg(taps + m.tu + kk);
             if (cj) {
                 tv.y = -tv.y;
                 tu.y = -tu.y;
@@ -210,14 +225,14 @@ __device__ __forceinline__ void stage_operands(unsigned char *A, unsigned char *
             a1 = pack2<FP16>(tv.y, tv.x);
             b0 = pack2<FP16>(m.wr * tu.x - m.wi * tu.y, m.wr * tu.y + m.wi * tu.x);
         }
-        *reinterpret_cast<uint32_t *>(A + op_off(ly + k, ii)) = a0;
-        *reinterpret_cast<uint32_t *>(A + op_off(kWin + ly + k, ii)) = a1;
-        *reinterpret_cast<uint32_t *>(B + op_off(lx + k, ii)) = b0;
+        *reinterpret_cast<uint32_t *>(A + op_off(ly + kk, ii)) = a0;
+        *reinterpret_cast<uint32_t *>(A + op_off(kWin + ly + kk, ii)) = a1;
+        *reinterpret_cast<uint32_t *>(B + op_off(lx + kk, ii)) = b0;
     }
 }
 
 template <int S, bool FP16>
-__global__ void __launch_bounds__(kTcThreads, 2) grid_tc_kernel(
+__global__ void __launch_bounds__(kTcThreads, 1) grid_tc_kernel(
     DevParams p, const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems,
     int32_t *counter, const uint64_t *__restrict__ rec, const int32_t *__restrict__ perm,
     const float2 *__restrict__ vis, const float *__restrict__ weight,
@@ -227,7 +242,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) grid_tc_kernel(
     unsigned char *Abuf = smem;                                // kStages x 32 KiB
     unsigned char *Bbuf = smem + kStages * kABytes;            // kStages x 16 KiB
     StageMeta *meta = reinterpret_cast<StageMeta *>(Bbuf + kStages * kBBytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(meta + kStages * kStageVis);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(meta + kMetaRing * kStageVis);
     __shared__ uint32_t s_tmem;
     __shared__ int s_item;
     __shared__ int s_abort;
@@ -276,21 +291,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) grid_tc_kernel(
             const int b = t_global & 1;
             unsigned char *A = Abuf + b * kABytes;
             unsigned char *B = Bbuf + b * kBBytes;
-            StageMeta *mb = meta + b * kStageVis;
+            StageMeta *mb = meta + (t_global % kMetaRing) * kStageVis;
             if (t_global >= kStages) {
                 // buffer b was used by stage t_global - 2: wait for its MMAs,
-                // then clear its entries
+                // then clear its entries (metadata slot of that stage)
                 if (!mbar_wait(bars + b, ((t_global - kStages) >> 1) & 1))
                     s_abort = 1;
-                __syncthreads();
-                if (s_abort) {
-                    aborted = true;
-                    break;
-                }
                 tc_fence_after();
-                const int nv_old = mb[0].pad;
-                stage_operands<S, FP16, false>(A, B, mb, nv_old, taps);
-                __syncthreads();
+                const StageMeta *mo = meta + ((t_global - kStages) % kMetaRing) * kStageVis;
+                stage_unit<S, FP16, false>(A, B, mo, mo[0].pad, taps);
             }
             const int v0 = it.start + st * kStageVis;
             const int nv = min(kStageVis, it.start + it.count - v0);
@@ -311,7 +320,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) grid_tc_kernel(
                 mb[tid] = m;
             }
             __syncthreads();
-            stage_operands<S, FP16, true>(A, B, mb, nv, taps);
+            if (s_abort) {
+                aborted = true;
+                break;
+            }
+            stage_unit<S, FP16, true>(A, B, mb, nv, taps);
             fence_proxy_async();
             __syncthreads();
             if (tid == 0) {
@@ -342,14 +355,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) grid_tc_kernel(
         // re-zeroed afterwards) -> float2 atomics into the HBM grid
         float *stg = reinterpret_cast<float *>(Bbuf);  // [128][64], xor-swizzled
         {
-            const int q = warp & 3, h = warp >> 2;
+            const int q = warp & 3, h = warp >> 2;  // lane quarter, 16-column group
             const int m = 32 * q + lane;
-            uint32_t r[32];
-            SEPW_TMEM_LD32(tmem + ((uint32_t)(32 * q) << 16) + 32 * h, r);
+            uint32_t r[16];
+            SEPW_TMEM_LD16(tmem + ((uint32_t)(32 * q) << 16) + 16 * h, r);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                const int x = 32 * h + c;
+            for (int c = 0; c < 16; ++c) {
+                const int x = 16 * h + c;
                 stg[m * kWin + (x ^ (m & 31))] = __uint_as_float(r[c]);
             }
         }
@@ -396,7 +409,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) grid_tc_kernel(
 
 size_t tc_smem_bytes()
 {
-    return (size_t)kStages * (kABytes + kBBytes) + sizeof(StageMeta) * kStages * kStageVis +
+    return (size_t)kStages * (kABytes + kBBytes) + sizeof(StageMeta) * kMetaRing * kStageVis +
            sizeof(uint64_t) * kStages;
 }
 
@@ -413,7 +426,7 @@ cudaError_t launch_tc_S(const DevParams &p, const Plan &plan, const float2 *vis,
     e = cudaMemsetAsync(plan.d_item_counter, 0, sizeof(int32_t), s);
     if (e != cudaSuccess)
         return e;
-    grid_tc_kernel<S, FP16><<<2 * num_sms, kTcThreads, shm, s>>>(
+    grid_tc_kernel<S, FP16><<<num_sms, kTcThreads, shm, s>>>(
         p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm, vis,
         weight, taps, grid, status);
     return cudaGetLastError();
