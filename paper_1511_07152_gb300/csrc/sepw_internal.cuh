@@ -30,27 +30,27 @@ struct Loc {
     bool keep;
 };
 
-// Exact floor of a double, in integer arithmetic on its bits (no FP64
-// instruction).  Returns false for NaN, +-inf and |y| >= 2^52 (whose floor is
-// y itself and always outside the accepted range).  Bit-for-bit the same as
-// the IEEE floor() for every other input.
-__device__ __forceinline__ bool floor_bits(double y, long long &out)
+// floor(fl(x + 0.5)), the IEEE sum rounded to nearest then floored, computed
+// exactly from the bits of x without an FP64 add.  For |x| < 2^52 the sum
+// x + 0.5 either is representable or rounds only within [2^k, 2^k + 1) for an
+// integer power of two 2^k, which leaves its floor unchanged; the one
+// exception is x = 0.5 - 2^-54, whose sum 1 - 2^-54 is a tie that rounds to
+// 1.0.  So the result is floor(x + 1/2) of the exact real sum, except there.
+// Returns false for NaN, +-inf and |x| >= 2^52 (outside the accepted range).
+__device__ __forceinline__ bool floor_add_half_bits(double x, long long &out)
 {
-    const long long b = __double_as_longlong(y);
+    const long long b = __double_as_longlong(x);
     const int eb = (int)((b >> 52) & 0x7FF);
     if (eb >= 1023 + 52)
-        return false;  // huge, inf or NaN
-    const bool neg = b < 0;
-    if (eb < 1023) {  // |y| < 1
-        const bool nonzero = (b & 0x7FFFFFFFFFFFFFFFll) != 0;
-        out = (neg && nonzero) ? -1 : 0;
+        return false;
+    if (eb < 1022) {  // |x| < 1/2: the sum lies in (0, 1)
+        out = (b == 0x3FDFFFFFFFFFFFFFll) ? 1 : 0;
         return true;
     }
-    const int shift = 52 - (eb - 1023);  // 1..52
+    const int shift = 52 - (eb - 1023);  // 1..53
     const long long mant = (b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll;
-    const long long ip = mant >> shift;
-    const bool frac = (mant & ((1ll << shift) - 1)) != 0;
-    out = neg ? -ip - (frac ? 1 : 0) : ip;
+    const long long num = (b < 0 ? -mant : mant) + (1ll << (shift - 1));
+    out = num >> shift;  // arithmetic shift: floor division by 2^shift
     return true;
 }
 
@@ -69,22 +69,30 @@ __device__ __forceinline__ double scale_pow2(double x, int k, double os_d)
 // with every operation rounded separately (no FMA contraction), then
 // c = floor(t/OS), o = t - c*OS; the footprint c - S/2 + 1 .. c + S/2 must lie
 // inside [0, N).  Returns false (drop) otherwise or for non-finite input.
-// Only the multiplies and adds use the FP64 pipe; the floor, the range checks
-// and the power-of-two scaling are exact integer operations on the bits.
+// Only u*fov and + N/2 use the FP64 pipe; the power-of-two scaling, the
+// rounded + 0.5 with its floor, and the range checks are exact integer
+// operations on the bits.
 __device__ __forceinline__ bool locate_axis(double coord, const DevParams &p,
                                             int32_t &c, int32_t &o)
 {
     const double x = __dadd_rn(__dmul_rn(coord, p.fov), p.half);
-    const double xs = p.os_log2 >= 0 ? scale_pow2(x, p.os_log2, p.os_d)
-                                     : __dmul_rn(x, p.os_d);
-    long long ti;
-    if (!floor_bits(__dadd_rn(xs, 0.5), ti))
-        return false;
-    if (ti >= 1099511627776ll || ti <= -1099511627776ll)  // |t| < 2^40
-        return false;
-    const long long OS = p.OS;
-    const long long cc = ti >= 0 ? ti / OS : -((-ti + OS - 1) / OS);
-    const long long oo = ti - cc * OS;
+    long long ti, cc, oo;
+    if (p.os_log2 >= 0) {
+        if (!floor_add_half_bits(scale_pow2(x, p.os_log2, p.os_d), ti))
+            return false;
+        if (ti >= 1099511627776ll || ti <= -1099511627776ll)  // |t| < 2^40
+            return false;
+        cc = ti >> p.os_log2;  // floor division by OS = 2^k
+        oo = ti - (cc << p.os_log2);
+    } else {
+        if (!floor_add_half_bits(__dmul_rn(x, p.os_d), ti))
+            return false;
+        if (ti >= 1099511627776ll || ti <= -1099511627776ll)
+            return false;
+        const long long OS = p.OS;
+        cc = ti >= 0 ? ti / OS : -((-ti + OS - 1) / OS);
+        oo = ti - cc * OS;
+    }
     const long long f = cc - p.S / 2 + 1;
     if (f < 0 || f + p.S - 1 > p.N - 1)
         return false;
@@ -107,7 +115,7 @@ __device__ __forceinline__ Loc locate(double u, double v, double w, const DevPar
     const double aw = __longlong_as_double(wb & 0x7FFFFFFFFFFFFFFFll);
     long long q;
     const bool wfin = ((wb >> 52) & 0x7FF) != 0x7FF;
-    ok = ok && wfin && floor_bits(__dadd_rn(__dmul_rn(aw, p.plane_r), 0.5), q) &&
+    ok = ok && wfin && floor_add_half_bits(__dmul_rn(aw, p.plane_r), q) &&
          q <= (long long)(p.P - 1);
     L.keep = ok;
     if (ok) {

@@ -19,11 +19,13 @@
 // canonical layout (8-row x 16-byte core matrices; K-adjacent cores 128 bytes
 // apart, 8-row groups 2048 bytes apart).  Only the non-zero entries of a
 // stage are written, and cleared again once the tensor core has consumed the
-// stage, so the buffers stay zero elsewhere: each of the 512 threads owns one
-// (visibility, tap pair) unit of a stage and clears the same unit two stages
-// later.  Two stages of 64 visibilities are in flight: while the tensor core
-// works on one, the CTA builds the next.  One thread issues the MMAs and
-// commits them to the stage's mbarrier.
+// stage, so the buffers stay zero elsewhere: each of the 512 producer threads
+// owns one (visibility, tap pair) unit of every stage, reads its visibility's
+// record itself, and clears its entries of a buffer when the buffer comes
+// round again.  Two stages of 64 visibilities are in flight.  Producer warps
+// arrive on the stage's "full" mbarrier; a separate warp waits on it, issues
+// the MMAs and commits them to the stage's "empty" mbarrier, so no CTA-wide
+// barrier is needed inside a work item.
 //
 // After the last stage of a work item the accumulator is read back with
 // tcgen05.ld, staged in shared memory and added to the HBM grid with float2
@@ -41,7 +43,6 @@ namespace {
 constexpr int kTcThreads = 512;
 constexpr int kStageVis = 64;                 // visibilities per stage (K = 128)
 constexpr int kStages = 2;                    // stages in flight
-constexpr int kMetaRing = 4;                  // stage metadata slots (>= 2 * kStages)
 constexpr int kWin = 64;                      // padded window edge
 constexpr int kM = 128, kN = 64;              // MMA shape
 constexpr int kKStage = 2 * kStageVis;        // K elements per stage
@@ -50,13 +51,6 @@ constexpr int kABytes = kM * kKStage * 2;     // 32 KiB
 constexpr int kBBytes = kN * kKStage * 2;     // 16 KiB
 constexpr uint32_t kTmemCols = 64;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
-
-struct StageMeta {
-    int tu, tv;     // tap-row offsets in the table
-    int lxy;        // lx | ly << 8 | conj << 16
-    int pad;
-    float wr, wi;   // W V (the taps carry the conjugation of conj visibilities)
-};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -189,41 +183,32 @@ __device__ __forceinline__ uint32_t op_off(int row, int ii)
     return (uint32_t)((row >> 3) * kSBO + (ii >> 2) * 128 + (row & 7) * 16 + (ii & 3) * 4);
 }
 
-// Writes (SET) or clears the non-zeros of one stage.  Thread t owns the
-// unit (visibility ii = 4 * (t >> 5) + (t & 3), taps k and k + 8 with
-// k = (t & 31) >> 2): the 32 four-byte stores of a warp instruction then land
-// in 32 distinct banks (row & 7 differs across k, ii & 3 across the lane
-// quads).  The same thread clears the same entries of the stage two steps
-// later, from that stage's metadata.
-template <int S, bool FP16, bool SET>
-__device__ __forceinline__ void stage_unit(unsigned char *A, unsigned char *B,
-                                           const StageMeta *meta, int nv,
-                                           const float2 *__restrict__ taps)
+// One producer thread's unit of a stage: visibility ii = 4 * warp + (lane & 3)
+// and the taps k, k + 8 with k = lane >> 2.  The 32 four-byte stores of a
+// warp instruction land in 32 distinct banks (row & 7 differs across k,
+// ii & 3 across the lane quads).  Placement of a unit: lx | ly << 8, or -1.
+template <int S, bool FP16>
+__device__ __forceinline__ void unit_store(unsigned char *A, unsigned char *B, int ii, int k,
+                                           int place, const float2 *tv, const float2 *tu,
+                                           float wr, float wi, bool cj, bool set)
 {
-    const int tid = threadIdx.x;
-    const int ii = 4 * (tid >> 5) + (tid & 3);
-    const int k = (tid & 31) >> 2;
-    if (ii >= nv)
-        return;
-    const StageMeta m = meta[ii];
-    const int lx = m.lxy & 255, ly = (m.lxy >> 8) & 255;
+    const int lx = place & 255, ly = place >> 8;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int kk = k + 8 * h;
         if (kk >= S)
             continue;
         uint32_t a0 = 0, a1 = 0, b0 = 0;
-        if (SET) {
-            const bool cj = (m.lxy >> 16) & 1;
-            float2 tv = __ldg(taps + m.tv + kk);
-            float2 tu = __ldg(taps + m.tu + kk);
+        if (set) {
+            float2 v = __ldg(tv + kk);
+            float2 u = __ldg(tu + kk);
             if (cj) {
-                tv.y = -tv.y;
-                tu.y = -tu.y;
+                v.y = -v.y;
+                u.y = -u.y;
             }
-            a0 = pack2<FP16>(tv.x, -tv.y);
-            a1 = pack2<FP16>(tv.y, tv.x);
-            b0 = pack2<FP16>(m.wr * tu.x - m.wi * tu.y, m.wr * tu.y + m.wi * tu.x);
+            a0 = pack2<FP16>(v.x, -v.y);
+            a1 = pack2<FP16>(v.y, v.x);
+            b0 = pack2<FP16>(wr * u.x - wi * u.y, wr * u.y + wi * u.x);
         }
         *reinterpret_cast<uint32_t *>(A + op_off(ly + kk, ii)) = a0;
         *reinterpret_cast<uint32_t *>(A + op_off(kWin + ly + kk, ii)) = a1;
@@ -231,31 +216,38 @@ __device__ __forceinline__ void stage_unit(unsigned char *A, unsigned char *B,
     }
 }
 
+constexpr int kProducerWarps = kTcThreads / 32;  // 16
+constexpr int kTcBlock = kTcThreads + 32;        // + one MMA-issuing warp
+
 template <int S, bool FP16>
-__global__ void __launch_bounds__(kTcThreads, 1) grid_tc_kernel(
+__global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
     DevParams p, const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems,
     int32_t *counter, const uint64_t *__restrict__ rec, const int32_t *__restrict__ perm,
     const float2 *__restrict__ vis, const float *__restrict__ weight,
     const float2 *__restrict__ taps, float2 *grid, int32_t *status)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *Abuf = smem;                                // kStages x 32 KiB
-    unsigned char *Bbuf = smem + kStages * kABytes;            // kStages x 16 KiB
-    StageMeta *meta = reinterpret_cast<StageMeta *>(Bbuf + kStages * kBBytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(meta + kMetaRing * kStageVis);
+    unsigned char *Abuf = smem;                      // kStages x 32 KiB
+    unsigned char *Bbuf = smem + kStages * kABytes;  // kStages x 16 KiB
+    uint64_t *full = reinterpret_cast<uint64_t *>(Bbuf + kStages * kBBytes);
+    uint64_t *empty = full + kStages;
+    uint64_t *accf = empty + kStages;
     __shared__ uint32_t s_tmem;
     __shared__ int s_item;
-    __shared__ int s_abort;
+    __shared__ volatile int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool mma_warp = warp == kProducerWarps;
     constexpr uint32_t idesc = instr_desc(FP16 ? 0u : 1u);
 
-    // zero the operand buffers once; they stay zero outside a stage's entries
-    for (int e = tid; e < kStages * (kABytes + kBBytes) / 16; e += kTcThreads)
+    for (int e = tid; e < kStages * (kABytes + kBBytes) / 16; e += kTcBlock)
         reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
-        for (int b = 0; b < kStages; ++b)
-            mbar_init(bars + b, 1);
+        for (int b = 0; b < kStages; ++b) {
+            mbar_init(full + b, kProducerWarps);
+            mbar_init(empty + b, 1);
+        }
+        mbar_init(accf, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -273,88 +265,101 @@ __global__ void __launch_bounds__(kTcThreads, 1) grid_tc_kernel(
     const uint32_t tmem = s_tmem;
     const int n_items = *nitems;
 
-    // running stage count of this CTA: stage t uses buffer t % 2, and its
-    // commit is completion number t / 2 of that buffer's mbarrier
-    int t_global = 0;
-    bool aborted = false;
+    // producer unit of this thread and the placements of its last two stages
+    const int ii = 4 * warp + (lane & 3);
+    const int k = lane >> 2;
+    int place_prev[2] = {-1, -1};  // indexed by stage parity
+
+    int t_global = 0;  // stages of this CTA so far (buffer t & 1)
+    int n_done = 0;    // items of this CTA so far (accf parity)
 
     for (;;) {
         if (tid == 0)
             s_item = atomicAdd(counter, 1);
         __syncthreads();
         const int item = s_item;
-        if (item >= n_items || aborted)
+        if (item >= n_items || s_abort)
             break;
         const WorkItem it = items[item];
         const int nst = (it.count + kStageVis - 1) / kStageVis;
-        for (int st = 0; st < nst; ++st, ++t_global) {
-            const int b = t_global & 1;
-            unsigned char *A = Abuf + b * kABytes;
-            unsigned char *B = Bbuf + b * kBBytes;
-            StageMeta *mb = meta + (t_global % kMetaRing) * kStageVis;
-            if (t_global >= kStages) {
-                // buffer b was used by stage t_global - 2: wait for its MMAs,
-                // then clear its entries (metadata slot of that stage)
-                if (!mbar_wait(bars + b, ((t_global - kStages) >> 1) & 1))
+
+        if (!mma_warp) {
+            for (int st = 0; st < nst; ++st) {
+                const int t = t_global + st;
+                const int b = t & 1;
+                unsigned char *A = Abuf + b * kABytes;
+                unsigned char *B = Bbuf + b * kBBytes;
+                const int v0 = it.start + st * kStageVis;
+                const int nv = min(kStageVis, it.start + it.count - v0);
+                // this unit's record (8 lanes share one visibility)
+                int place = -1, tu_off = 0, tv_off = 0;
+                float wr = 0.f, wi = 0.f;
+                bool cj = false;
+                if (ii < nv) {
+                    const uint64_t r = rec[v0 + ii];
+                    const int i = perm[v0 + ii];
+                    const float wt = weight ? __ldg(weight + i) : 1.0f;
+                    const float2 x = __ldg(vis + i);
+                    const int row = rec_plane(r) * p.OS;
+                    tu_off = (row + rec_ou(r)) * S;
+                    tv_off = (row + rec_ov(r)) * S;
+                    cj = rec_conj(r);
+                    wr = wt * x.x;
+                    wi = wt * x.y;
+                    place = rec_lx(r) | (rec_ly(r) << 8);
+                }
+                if (t >= kStages) {
+                    // buffer b held stage t - 2: wait for its MMAs, clear it
+                    if (!s_abort && !mbar_wait(empty + b, ((t - kStages) >> 1) & 1))
+                        s_abort = 1;
+                    tc_fence_after();
+                    if (place_prev[b] >= 0)
+                        unit_store<S, FP16>(A, B, ii, k, place_prev[b], taps, taps, 0.f, 0.f,
+                                            false, false);
+                }
+                if (place >= 0)
+                    unit_store<S, FP16>(A, B, ii, k, place, taps + tv_off, taps + tu_off, wr,
+                                        wi, cj, true);
+                place_prev[b] = place;
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                     smem_u32(full + b))
+                                 : "memory");
+            }
+        } else if (lane == 0) {
+            for (int st = 0; st < nst; ++st) {
+                const int t = t_global + st;
+                const int b = t & 1;
+                if (!s_abort && !mbar_wait(full + b, (t >> 1) & 1))
                     s_abort = 1;
+                if (s_abort)
+                    continue;
                 tc_fence_after();
-                const StageMeta *mo = meta + ((t_global - kStages) % kMetaRing) * kStageVis;
-                stage_unit<S, FP16, false>(A, B, mo, mo[0].pad, taps);
-            }
-            const int v0 = it.start + st * kStageVis;
-            const int nv = min(kStageVis, it.start + it.count - v0);
-            if (tid < nv) {
-                const uint64_t r = rec[v0 + tid];
-                const int i = perm[v0 + tid];
-                const float wt = weight ? __ldg(weight + i) : 1.0f;
-                const float2 x = __ldg(vis + i);
-                const bool cj = rec_conj(r);
-                const int row = rec_plane(r) * p.OS;
-                StageMeta m;
-                m.tu = (row + rec_ou(r)) * S;
-                m.tv = (row + rec_ov(r)) * S;
-                m.lxy = rec_lx(r) | (rec_ly(r) << 8) | ((cj ? 1 : 0) << 16);
-                m.pad = nv;
-                m.wr = wt * x.x;
-                m.wi = wt * x.y;
-                mb[tid] = m;
-            }
-            __syncthreads();
-            if (s_abort) {
-                aborted = true;
-                break;
-            }
-            stage_unit<S, FP16, true>(A, B, mb, nv, taps);
-            fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+                const int v0 = it.start + st * kStageVis;
+                const int nv = min(kStageVis, it.start + it.count - v0);
+                const uint32_t a0 = smem_u32(Abuf + b * kABytes);
+                const uint32_t b0 = smem_u32(Bbuf + b * kBBytes);
                 const int nk = (nv + 7) / 8;  // K = 16 steps holding visibilities
                 for (int q = 0; q < nk; ++q)
                     mma_f16(tmem, smem_desc(a0 + 256 * q), smem_desc(b0 + 256 * q), idesc,
                             (st > 0 || q > 0) ? 1u : 0u);
-                mma_commit(bars + b);
+                mma_commit(empty + b);
             }
+            if (!s_abort)
+                mma_commit(accf);
         }
-        if (aborted)
-            break;
-        // all MMAs of the item are complete once the last stage's are
-        {
-            const int tl = t_global - 1;
-            if (!mbar_wait(bars + (tl & 1), (tl >> 1) & 1))
-                s_abort = 1;
-            __syncthreads();
-            if (s_abort) {
-                aborted = true;
-                break;
-            }
-        }
+        t_global += nst;
+
+        // epilogue: wait for the accumulator, TMEM -> shared staging (the B
+        // buffers, re-zeroed afterwards) -> float2 atomics into the HBM grid
+        if (!s_abort && !mbar_wait(accf, n_done & 1))
+            s_abort = 1;
+        ++n_done;
         tc_fence_after();
-        // epilogue: TMEM -> shared staging (aliases the B buffers, which are
-        // re-zeroed afterwards) -> float2 atomics into the HBM grid
         float *stg = reinterpret_cast<float *>(Bbuf);  // [128][64], xor-swizzled
-        {
+        if (!mma_warp && !s_abort) {
             const int q = warp & 3, h = warp >> 2;  // lane quarter, 16-column group
             const int m = 32 * q + lane;
             uint32_t r[16];
@@ -368,11 +373,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) grid_tc_kernel(
         }
         tc_fence_before();
         __syncthreads();
-        {
+        if (!s_abort) {
             const int W = p.T + S - 1;
             const int ty = it.tile / p.ntx, tx = it.tile - ty * p.ntx;
             const int64_t gy0 = (int64_t)ty * p.T, gx0 = (int64_t)tx * p.T;
-            for (int e = tid; e < W * kWin; e += kTcThreads) {
+            for (int e = tid; e < W * kWin; e += kTcBlock) {
                 const int y = e >> 6, x = e & 63;
                 if (x >= W)
                     continue;
@@ -383,20 +388,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) grid_tc_kernel(
             }
         }
         __syncthreads();
-        for (int e = tid; e < kStages * kBBytes / 16; e += kTcThreads)
+        for (int e = tid; e < kStages * kBBytes / 16; e += kTcBlock)
             reinterpret_cast<uint4 *>(Bbuf)[e] = make_uint4(0, 0, 0, 0);
         fence_proxy_async();
-        __syncthreads();
     }
 
-    if (aborted) {
+    if (s_abort) {
         if (tid == 0)
             atomicExch(status, SEPW_ETIMEOUT);
         // bounded wait for this CTA's own MMAs before releasing TMEM
-        if (t_global > 0) {
-            const int tl = t_global - 1;
-            mbar_wait(bars + (tl & 1), (tl >> 1) & 1);
-        }
+        if (mma_warp && lane == 0 && n_done > 0)
+            mbar_wait(accf, (n_done - 1) & 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -409,8 +411,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) grid_tc_kernel(
 
 size_t tc_smem_bytes()
 {
-    return (size_t)kStages * (kABytes + kBBytes) + sizeof(StageMeta) * kMetaRing * kStageVis +
-           sizeof(uint64_t) * kStages;
+    return (size_t)kStages * (kABytes + kBBytes) + sizeof(uint64_t) * (2 * kStages + 1);
 }
 
 template <int S, bool FP16>
@@ -426,7 +427,7 @@ cudaError_t launch_tc_S(const DevParams &p, const Plan &plan, const float2 *vis,
     e = cudaMemsetAsync(plan.d_item_counter, 0, sizeof(int32_t), s);
     if (e != cudaSuccess)
         return e;
-    grid_tc_kernel<S, FP16><<<num_sms, kTcThreads, shm, s>>>(
+    grid_tc_kernel<S, FP16><<<num_sms, kTcBlock, shm, s>>>(
         p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm, vis,
         weight, taps, grid, status);
     return cudaGetLastError();
