@@ -186,33 +186,43 @@ __device__ __forceinline__ uint32_t op_off(int row, int ii)
 // One producer thread's unit of a stage: visibility ii = 4 * warp + (lane & 3)
 // and the taps k, k + 8 with k = lane >> 2.  The 32 four-byte stores of a
 // warp instruction land in 32 distinct banks (row & 7 differs across k,
-// ii & 3 across the lane quads).  Placement of a unit: lx | ly << 8, or -1.
+// ii & 3 across the lane quads).  Rows k and k + 8 are one 8-row core group
+// (kSBO bytes) apart, and the second block of A (row + 64) eight groups, so a
+// unit needs two offsets: offA = op_off(ly + k, ii), offB = op_off(lx + k, ii).
 template <int S, bool FP16>
-__device__ __forceinline__ void unit_store(unsigned char *A, unsigned char *B, int ii, int k,
-                                           int place, const float2 *tv, const float2 *tu,
-                                           float wr, float wi, bool cj, bool set)
+__device__ __forceinline__ void unit_set(unsigned char *A, unsigned char *B, uint32_t offA,
+                                         uint32_t offB, int k, const float2 *tv,
+                                         const float2 *tu, float wr, float wi, bool cj)
 {
-    const int lx = place & 255, ly = place >> 8;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int kk = k + 8 * h;
         if (kk >= S)
             continue;
-        uint32_t a0 = 0, a1 = 0, b0 = 0;
-        if (set) {
-            float2 v = __ldg(tv + kk);
-            float2 u = __ldg(tu + kk);
-            if (cj) {
-                v.y = -v.y;
-                u.y = -u.y;
-            }
-            a0 = pack2<FP16>(v.x, -v.y);
-            a1 = pack2<FP16>(v.y, v.x);
-            b0 = pack2<FP16>(wr * u.x - wi * u.y, wr * u.y + wi * u.x);
+        float2 v = __ldg(tv + kk);
+        float2 u = __ldg(tu + kk);
+        if (cj) {
+            v.y = -v.y;
+            u.y = -u.y;
         }
-        *reinterpret_cast<uint32_t *>(A + op_off(ly + kk, ii)) = a0;
-        *reinterpret_cast<uint32_t *>(A + op_off(kWin + ly + kk, ii)) = a1;
-        *reinterpret_cast<uint32_t *>(B + op_off(lx + kk, ii)) = b0;
+        *reinterpret_cast<uint32_t *>(A + offA + h * kSBO) = pack2<FP16>(v.x, -v.y);
+        *reinterpret_cast<uint32_t *>(A + offA + (8 + h) * kSBO) = pack2<FP16>(v.y, v.x);
+        *reinterpret_cast<uint32_t *>(B + offB + h * kSBO) =
+            pack2<FP16>(wr * u.x - wi * u.y, wr * u.y + wi * u.x);
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void unit_clear(unsigned char *A, unsigned char *B, uint32_t offA,
+                                           uint32_t offB, int k)
+{
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (k + 8 * h >= S)
+            continue;
+        *reinterpret_cast<uint32_t *>(A + offA + h * kSBO) = 0u;
+        *reinterpret_cast<uint32_t *>(A + offA + (8 + h) * kSBO) = 0u;
+        *reinterpret_cast<uint32_t *>(B + offB + h * kSBO) = 0u;
     }
 }
 
@@ -265,10 +275,11 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
     const uint32_t tmem = s_tmem;
     const int n_items = *nitems;
 
-    // producer unit of this thread and the placements of its last two stages
+    // producer unit of this thread; operand offsets of its last two stages
+    // (0xffffffff: nothing written) for the clears
     const int ii = 4 * warp + (lane & 3);
     const int k = lane >> 2;
-    int place_prev[2] = {-1, -1};  // indexed by stage parity
+    uint32_t oldA[2] = {0xffffffffu, 0xffffffffu}, oldB[2] = {0, 0};
 
     int t_global = 0;  // stages of this CTA so far (buffer t & 1)
     int n_done = 0;    // items of this CTA so far (accf parity)
@@ -284,43 +295,52 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
         const int nst = (it.count + kStageVis - 1) / kStageVis;
 
         if (!mma_warp) {
+            // records of the unit's visibility, one stage ahead
+            uint64_t r_next = 0;
+            int i_next = -1;
+            if (ii < it.count) {
+                r_next = rec[it.start + ii];
+                i_next = perm[it.start + ii];
+            }
             for (int st = 0; st < nst; ++st) {
                 const int t = t_global + st;
                 const int b = t & 1;
                 unsigned char *A = Abuf + b * kABytes;
                 unsigned char *B = Bbuf + b * kBBytes;
-                const int v0 = it.start + st * kStageVis;
-                const int nv = min(kStageVis, it.start + it.count - v0);
-                // this unit's record (8 lanes share one visibility)
-                int place = -1, tu_off = 0, tv_off = 0;
-                float wr = 0.f, wi = 0.f;
-                bool cj = false;
-                if (ii < nv) {
-                    const uint64_t r = rec[v0 + ii];
-                    const int i = perm[v0 + ii];
-                    const float wt = weight ? __ldg(weight + i) : 1.0f;
-                    const float2 x = __ldg(vis + i);
-                    const int row = rec_plane(r) * p.OS;
-                    tu_off = (row + rec_ou(r)) * S;
-                    tv_off = (row + rec_ov(r)) * S;
-                    cj = rec_conj(r);
-                    wr = wt * x.x;
-                    wi = wt * x.y;
-                    place = rec_lx(r) | (rec_ly(r) << 8);
+                const uint64_t r = r_next;
+                const int i = i_next;
+                float2 x = make_float2(0.f, 0.f);
+                float wt = 1.0f;
+                if (i >= 0) {
+                    x = __ldg(vis + i);
+                    if (weight)
+                        wt = __ldg(weight + i);
+                }
+                const int vn = it.start + (st + 1) * kStageVis + ii;
+                i_next = -1;
+                if (st + 1 < nst && vn < it.start + it.count) {
+                    r_next = rec[vn];
+                    i_next = perm[vn];
                 }
                 if (t >= kStages) {
                     // buffer b held stage t - 2: wait for its MMAs, clear it
                     if (!s_abort && !mbar_wait(empty + b, ((t - kStages) >> 1) & 1))
                         s_abort = 1;
                     tc_fence_after();
-                    if (place_prev[b] >= 0)
-                        unit_store<S, FP16>(A, B, ii, k, place_prev[b], taps, taps, 0.f, 0.f,
-                                            false, false);
+                    if (oldA[b] != 0xffffffffu)
+                        unit_clear<S>(A, B, oldA[b], oldB[b], k);
                 }
-                if (place >= 0)
-                    unit_store<S, FP16>(A, B, ii, k, place, taps + tv_off, taps + tu_off, wr,
-                                        wi, cj, true);
-                place_prev[b] = place;
+                oldA[b] = 0xffffffffu;
+                if (i >= 0) {
+                    const int row = rec_plane(r) * p.OS;
+                    const uint32_t offA = op_off(rec_ly(r) + k, ii);
+                    const uint32_t offB = op_off(rec_lx(r) + k, ii);
+                    unit_set<S, FP16>(A, B, offA, offB, k, taps + (row + rec_ov(r)) * S,
+                                      taps + (row + rec_ou(r)) * S, wt * x.x, wt * x.y,
+                                      rec_conj(r));
+                    oldA[b] = offA;
+                    oldB[b] = offB;
+                }
                 fence_proxy_async();
                 __syncwarp();
                 if (lane == 0)
