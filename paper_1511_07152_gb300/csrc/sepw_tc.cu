@@ -42,7 +42,7 @@ namespace {
 
 constexpr int kTcThreads = 512;
 constexpr int kStageVis = 64;                 // visibilities per stage (K = 128)
-constexpr int kStages = 2;                    // stages in flight
+constexpr int kStages = 3;                    // stages in flight
 constexpr int kWin = 64;                      // padded window edge
 constexpr int kM = 128, kN = 64;              // MMA shape
 constexpr int kKStage = 2 * kStageVis;        // K elements per stage
@@ -279,9 +279,14 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
     // (0xffffffff: nothing written) for the clears
     const int ii = 4 * warp + (lane & 3);
     const int k = lane >> 2;
-    uint32_t oldA[2] = {0xffffffffu, 0xffffffffu}, oldB[2] = {0, 0};
+    uint32_t oldA[kStages], oldB[kStages];
+#pragma unroll
+    for (int q = 0; q < kStages; ++q) {
+        oldA[q] = 0xffffffffu;
+        oldB[q] = 0;
+    }
 
-    int t_global = 0;  // stages of this CTA so far (buffer t & 1)
+    int t_global = 0;  // stages of this CTA so far (buffer t % kStages)
     int n_done = 0;    // items of this CTA so far (accf parity)
 
     for (;;) {
@@ -304,7 +309,7 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
             }
             for (int st = 0; st < nst; ++st) {
                 const int t = t_global + st;
-                const int b = t & 1;
+                const int b = t % kStages;
                 unsigned char *A = Abuf + b * kABytes;
                 unsigned char *B = Bbuf + b * kBBytes;
                 const uint64_t r = r_next;
@@ -322,15 +327,25 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
                     r_next = rec[vn];
                     i_next = perm[vn];
                 }
+                uint32_t pa = 0xffffffffu, pb = 0;
+#pragma unroll
+                for (int q = 0; q < kStages; ++q)
+                    if (q == b) {
+                        pa = oldA[q];
+                        pb = oldB[q];
+                    }
                 if (t >= kStages) {
-                    // buffer b held stage t - 2: wait for its MMAs, clear it
-                    if (!s_abort && !mbar_wait(empty + b, ((t - kStages) >> 1) & 1))
+                    // buffer b held stage t - kStages: wait (lane 0) for its
+                    // MMAs, then clear the entries this unit wrote there
+                    if (lane == 0 && !s_abort &&
+                        !mbar_wait(empty + b, ((t - kStages) / kStages) & 1))
                         s_abort = 1;
+                    __syncwarp();
                     tc_fence_after();
-                    if (oldA[b] != 0xffffffffu)
-                        unit_clear<S>(A, B, oldA[b], oldB[b], k);
+                    if (pa != 0xffffffffu)
+                        unit_clear<S>(A, B, pa, pb, k);
                 }
-                oldA[b] = 0xffffffffu;
+                pa = 0xffffffffu;
                 if (i >= 0) {
                     const int row = rec_plane(r) * p.OS;
                     const uint32_t offA = op_off(rec_ly(r) + k, ii);
@@ -338,9 +353,15 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
                     unit_set<S, FP16>(A, B, offA, offB, k, taps + (row + rec_ov(r)) * S,
                                       taps + (row + rec_ou(r)) * S, wt * x.x, wt * x.y,
                                       rec_conj(r));
-                    oldA[b] = offA;
-                    oldB[b] = offB;
+                    pa = offA;
+                    pb = offB;
                 }
+#pragma unroll
+                for (int q = 0; q < kStages; ++q)
+                    if (q == b) {
+                        oldA[q] = pa;
+                        oldB[q] = pb;
+                    }
                 fence_proxy_async();
                 __syncwarp();
                 if (lane == 0)
@@ -351,8 +372,8 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
         } else if (lane == 0) {
             for (int st = 0; st < nst; ++st) {
                 const int t = t_global + st;
-                const int b = t & 1;
-                if (!s_abort && !mbar_wait(full + b, (t >> 1) & 1))
+                const int b = t % kStages;
+                if (!s_abort && !mbar_wait(full + b, (t / kStages) & 1))
                     s_abort = 1;
                 if (s_abort)
                     continue;
@@ -374,8 +395,9 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
 
         // epilogue: wait for the accumulator, TMEM -> shared staging (the B
         // buffers, re-zeroed afterwards) -> float2 atomics into the HBM grid
-        if (!s_abort && !mbar_wait(accf, n_done & 1))
+        if (lane == 0 && !s_abort && !mbar_wait(accf, n_done & 1))
             s_abort = 1;
+        __syncwarp();
         ++n_done;
         tc_fence_after();
         float *stg = reinterpret_cast<float *>(Bbuf);  // [128][64], xor-swizzled
