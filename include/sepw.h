@@ -159,6 +159,28 @@ SEPW_API int sepw_locate(sepw_ctx *ctx, int64_t nvis, const double *u, const dou
 SEPW_API int sepw_plan(sepw_ctx *ctx, int64_t nvis, const double *u, const double *v,
               const double *w, sepw_stream_t stream);
 
+/* Batched plan (W-stacking layers, frequency channels, Sec. 4.3): ngrids
+ * separate N x N grids, visibilities of grid g at indices
+ * vis_offsets[g] .. vis_offsets[g+1]-1 of u, v, w (and vis, weight in the
+ * gridding calls).  vis_offsets is a HOST array of ngrids + 1 non-decreasing
+ * values starting at 0; it is copied during the call (so the call itself
+ * cannot be captured in a CUDA graph; capture the *_planned calls instead).
+ * The tiled and tensor-core forms grid the whole batch in ONE persistent
+ * launch of sepw_grid_planned / sepw_degrid_planned, whose grid argument is
+ * then ngrids * N * N complex64 (grid g at offset g * N * N); the plain form
+ * issues one launch per grid.  Tiles of all grids share the work list. */
+SEPW_API int sepw_plan_batched(sepw_ctx *ctx, int32_t ngrids, const int64_t *vis_offsets,
+                               const double *u, const double *v, const double *w,
+                               sepw_stream_t stream);
+
+/* sepw_plan_batched + sepw_grid_planned: grids (ngrids * N * N complex64)
+ * are accumulated into (+=). */
+SEPW_API int sepw_grid_batched(sepw_ctx *ctx, const float *taps, int32_t ngrids,
+                               const int64_t *vis_offsets, const double *u,
+                               const double *v, const double *w, const float *vis,
+                               const float *weight, float *grids, int64_t *n_dropped,
+                               sepw_stream_t stream);
+
 /* Number of visibilities dropped by the current plan.  Host pointer;
  * synchronises `stream`. */
 SEPW_API int sepw_plan_dropped(sepw_ctx *ctx, int64_t *n_dropped_host,

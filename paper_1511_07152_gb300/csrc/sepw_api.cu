@@ -115,6 +115,7 @@ void free_plan(Plan &pl)
     cudaFree(pl.d_nitems);
     cudaFree(pl.d_item_counter);
     cudaFree(pl.d_dropped);
+    cudaFree(pl.d_offsets);
     pl = Plan();
 }
 
@@ -139,11 +140,14 @@ int check_dev(sepw_ctx *ctx, const void *ptr, const char *name, bool allow_null)
     return SEPW_OK;
 }
 
-int ensure_plan_capacity(sepw_ctx *ctx, int64_t nvis)
+int ensure_plan_capacity(sepw_ctx *ctx, int64_t nvis, int ngrids)
 {
     Plan &pl = ctx->plan;
     int rc;
-    const int ntiles = ctx->dp.ntx * ctx->dp.ntx;
+    const int64_t ntiles64 = (int64_t)ctx->dp.ntx * ctx->dp.ntx * ngrids;
+    if (ntiles64 > (1ll << 30))
+        return fail(ctx, SEPW_EINVAL, "too many tiles (%lld)", (long long)ntiles64);
+    const int ntiles = (int)ntiles64;
     if (!pl.d_nitems) {
         if ((rc = grow(ctx, &pl.d_nitems, 1)) || (rc = grow(ctx, &pl.d_item_counter, 2)) ||
             (rc = grow(ctx, &pl.d_dropped, 1)))
@@ -345,25 +349,36 @@ int sepw_locate(sepw_ctx *ctx, int64_t nvis, const double *u, const double *v,
     return SEPW_OK;
 }
 
-int sepw_plan(sepw_ctx *ctx, int64_t nvis, const double *u, const double *v,
-              const double *w, sepw_stream_t stream)
+static int plan_impl(sepw_ctx *ctx, int32_t ngrids, const int64_t *offsets_host, int64_t nvis,
+                     const double *u, const double *v, const double *w, cudaStream_t s)
 {
-    if (!ctx)
-        return SEPW_EINVAL;
     ctx->plan.valid = false;
     if (nvis < 0 || nvis > (int64_t)INT32_MAX - 1)
         return fail(ctx, SEPW_EINVAL, "nvis out of range [0, 2^31 - 2]");
+    if (ngrids < 1)
+        return fail(ctx, SEPW_EINVAL, "ngrids < 1");
     int rc;
     if (nvis > 0 && ((rc = check_dev(ctx, u, "u", false)) ||
                      (rc = check_dev(ctx, v, "v", false)) ||
                      (rc = check_dev(ctx, w, "w", false))))
         return rc;
-    if ((rc = ensure_plan_capacity(ctx, nvis)))
+    if ((rc = ensure_plan_capacity(ctx, nvis, ngrids)))
         return rc;
     Plan &pl = ctx->plan;
     pl.form = ctx->p.form;
     pl.nvis = nvis;
-    cudaStream_t s = (cudaStream_t)stream;
+    pl.ngrids = ngrids;
+    pl.h_offsets.assign(offsets_host, offsets_host + ngrids + 1);
+    if (ngrids > 1) {
+        if (pl.offsets_capacity < ngrids + 1) {
+            if ((rc = grow(ctx, &pl.d_offsets, (size_t)ngrids + 1)))
+                return rc;
+            pl.offsets_capacity = ngrids + 1;
+        }
+        SEPW_CUDA(ctx, cudaMemcpyAsync(pl.d_offsets, pl.h_offsets.data(),
+                                       sizeof(int64_t) * (ngrids + 1), cudaMemcpyHostToDevice,
+                                       s));
+    }
     if (ctx->p.form == SEPW_FORM_PLAIN) {
         pl.u = u;
         pl.v = v;
@@ -376,6 +391,32 @@ int sepw_plan(sepw_ctx *ctx, int64_t nvis, const double *u, const double *v,
     }
     pl.valid = true;
     return SEPW_OK;
+}
+
+int sepw_plan(sepw_ctx *ctx, int64_t nvis, const double *u, const double *v,
+              const double *w, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    const int64_t offsets[2] = {0, nvis};
+    return plan_impl(ctx, 1, offsets, nvis, u, v, w, (cudaStream_t)stream);
+}
+
+int sepw_plan_batched(sepw_ctx *ctx, int32_t ngrids, const int64_t *vis_offsets,
+                      const double *u, const double *v, const double *w,
+                      sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    if (ngrids < 1 || !vis_offsets)
+        return fail(ctx, SEPW_EINVAL, "ngrids < 1 or vis_offsets NULL");
+    if (vis_offsets[0] != 0)
+        return fail(ctx, SEPW_EINVAL, "vis_offsets[0] != 0");
+    for (int g = 0; g < ngrids; ++g)
+        if (vis_offsets[g + 1] < vis_offsets[g])
+            return fail(ctx, SEPW_EINVAL, "vis_offsets decrease at grid %d", g);
+    return plan_impl(ctx, ngrids, vis_offsets, vis_offsets[ngrids], u, v, w,
+                     (cudaStream_t)stream);
 }
 
 int sepw_plan_dropped(sepw_ctx *ctx, int64_t *n_dropped_host, sepw_stream_t stream)
@@ -411,9 +452,16 @@ int sepw_grid_planned(sepw_ctx *ctx, const float *taps, const float *vis,
         return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (pl.form == SEPW_FORM_PLAIN) {
-        SEPW_CUDA(ctx, launch_grid_plain(ctx->dp, pl.nvis, pl.u, pl.v, pl.w,
-                                         (const float2 *)vis, weight, (const float2 *)taps,
-                                         (float2 *)grid, nullptr, s));
+        // one plain launch per grid of the batch
+        const int64_t n2 = (int64_t)ctx->p.grid_size * ctx->p.grid_size;
+        for (int g = 0; g < pl.ngrids; ++g) {
+            const int64_t a0 = pl.h_offsets[g], n = pl.h_offsets[g + 1] - a0;
+            SEPW_CUDA(ctx, launch_grid_plain(ctx->dp, n, pl.u + a0, pl.v + a0, pl.w + a0,
+                                             (const float2 *)vis + a0,
+                                             weight ? weight + a0 : nullptr,
+                                             (const float2 *)taps, (float2 *)grid + g * n2,
+                                             nullptr, s));
+        }
     } else if (is_tc_form(pl.form)) {
         if (((uintptr_t)taps) & 15)
             return fail(ctx, SEPW_EINVAL, "taps must be 16-byte aligned");
@@ -448,10 +496,15 @@ int sepw_degrid_planned(sepw_ctx *ctx, const float *taps, const float *grid,
         return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (pl.form == SEPW_FORM_PLAIN) {
-        SEPW_CUDA(ctx, launch_degrid_plain(ctx->dp, pl.nvis, pl.u, pl.v, pl.w,
-                                           (const float2 *)grid, weight,
-                                           (const float2 *)taps, (float2 *)vis_out,
-                                           nullptr, s));
+        const int64_t n2 = (int64_t)ctx->p.grid_size * ctx->p.grid_size;
+        for (int g = 0; g < pl.ngrids; ++g) {
+            const int64_t a0 = pl.h_offsets[g], n = pl.h_offsets[g + 1] - a0;
+            SEPW_CUDA(ctx, launch_degrid_plain(ctx->dp, n, pl.u + a0, pl.v + a0, pl.w + a0,
+                                               (const float2 *)grid + g * n2,
+                                               weight ? weight + a0 : nullptr,
+                                               (const float2 *)taps,
+                                               (float2 *)vis_out + a0, nullptr, s));
+        }
     } else {
         if (((uintptr_t)taps) & 15)
             return fail(ctx, SEPW_EINVAL, "taps must be 16-byte aligned");
@@ -485,6 +538,21 @@ int sepw_grid(sepw_ctx *ctx, const float *taps, int64_t nvis, const double *u,
     if (rc)
         return rc;
     if ((rc = sepw_grid_planned(ctx, taps, vis, weight, grid, stream)))
+        return rc;
+    return copy_dropped(ctx, n_dropped, (cudaStream_t)stream);
+}
+
+int sepw_grid_batched(sepw_ctx *ctx, const float *taps, int32_t ngrids,
+                      const int64_t *vis_offsets, const double *u, const double *v,
+                      const double *w, const float *vis, const float *weight, float *grids,
+                      int64_t *n_dropped, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    int rc = sepw_plan_batched(ctx, ngrids, vis_offsets, u, v, w, stream);
+    if (rc)
+        return rc;
+    if ((rc = sepw_grid_planned(ctx, taps, vis, weight, grids, stream)))
         return rc;
     return copy_dropped(ctx, n_dropped, (cudaStream_t)stream);
 }

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(256) locate_bin_kernel(
     DevParams p, int64_t nvis, const double *__restrict__ u, const double *__restrict__ v,
     const double *__restrict__ w, int32_t *__restrict__ tile_of,
     uint64_t *__restrict__ rec0, int32_t *tile_count, unsigned long long *dropped,
-    int32_t *__restrict__ drop_list)
+    int32_t *__restrict__ drop_list, int ngrids, const int64_t *__restrict__ offsets)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool active = i < nvis;
@@ -35,7 +35,19 @@ __global__ void __launch_bounds__(256) locate_bin_kernel(
         if (L.keep) {
             int fx = L.cu - p.S / 2 + 1, fy = L.cv - p.S / 2 + 1;
             int tx = fx / p.T, ty = fy / p.T;
-            tile = ty * p.ntx + tx;
+            int g = 0;
+            if (ngrids > 1) {  // grid of visibility i: offsets[g] <= i < offsets[g+1]
+                int lo = 0, hi = ngrids - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (offsets[mid] <= i)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                g = lo;
+            }
+            tile = (g * p.ntx + ty) * p.ntx + tx;
             rec0[i] = pack_rec(fx - tx * p.T, fy - ty * p.T, L.ou, L.ov, L.plane, L.conj);
         }
         tile_of[i] = tile;
@@ -254,7 +266,7 @@ cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
     if (nvis > 0) {
         locate_bin_kernel<<<(unsigned)((nvis + 255) / 256), 256, 0, s>>>(
             p, nvis, u, v, w, plan.d_tile, plan.d_rec0, plan.d_tile_count, plan.d_dropped,
-            plan.d_drop_list);
+            plan.d_drop_list, plan.ngrids, plan.d_offsets);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
     }

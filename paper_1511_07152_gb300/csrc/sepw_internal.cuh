@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/sepw.h"
 
 namespace sepw {
@@ -129,6 +131,27 @@ __device__ __forceinline__ Loc locate(double u, double v, double w, const DevPar
     return L;
 }
 
+// Tile id -> origin of the tile in its grid.  A batched plan numbers the
+// tiles of grid g after those of grids 0 .. g-1 (ntx^2 tiles per grid), so the
+// grid's base offset follows from the tile id as well.
+struct TileOrigin {
+    int64_t base;  // element offset of the tile's grid
+    int64_t gy0;   // first row of the tile
+    int64_t gx0;   // first column of the tile
+};
+__device__ __forceinline__ TileOrigin tile_origin(const DevParams &p, int tile)
+{
+    const int per = p.ntx * p.ntx;
+    const int g = tile / per;
+    const int tl = tile - g * per;
+    const int ty = tl / p.ntx, tx = tl - ty * p.ntx;
+    TileOrigin o;
+    o.base = (int64_t)g * p.N * p.N;
+    o.gy0 = (int64_t)ty * p.T;
+    o.gx0 = (int64_t)tx * p.T;
+    return o;
+}
+
 // Packed per-visibility record of a plan (tiled forms), in slot order:
 //   bits  0..5   lx  footprint origin column inside the tile (0..T-1)
 //   bits  6..11  ly  footprint origin row inside the tile
@@ -182,7 +205,10 @@ struct Plan {
     int32_t *d_item_counter = nullptr; // [2] persistent-kernel work counters
     unsigned long long *d_dropped = nullptr;  // [1]
     int32_t *d_drop_list = nullptr;           // [nvis] indices of dropped visibilities
-    int32_t nkept_host_bound = 0;
+    int32_t ngrids = 1;                // batched plans: grids in the batch
+    int64_t *d_offsets = nullptr;      // [ngrids + 1] visibility offsets per grid
+    int32_t offsets_capacity = 0;
+    std::vector<int64_t> h_offsets;    // plain form: per-grid ranges
     // plain form: the coordinates are read directly
     const double *u = nullptr, *v = nullptr, *w = nullptr;
 };
@@ -216,6 +242,7 @@ cudaError_t launch_degrid_plain(const DevParams &p, int64_t nvis, const double *
 // sepw_bin.cu
 cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
                         const double *v, const double *w, Plan &plan, cudaStream_t s);
+// batched: plan.ngrids > 1 and plan.d_offsets hold the per-grid ranges
 cudaError_t launch_zero_dropped(const Plan &plan, float2 *vis, cudaStream_t s);
 
 // sepw_tiled.cu

@@ -417,8 +417,7 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
         __syncthreads();
         if (!s_abort) {
             const int W = p.T + S - 1;
-            const int ty = it.tile / p.ntx, tx = it.tile - ty * p.ntx;
-            const int64_t gy0 = (int64_t)ty * p.T, gx0 = (int64_t)tx * p.T;
+            const TileOrigin o = tile_origin(p, it.tile);
             for (int e = tid; e < W * kWin; e += kTcBlock) {
                 const int y = e >> 6, x = e & 63;
                 if (x >= W)
@@ -426,7 +425,8 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
                 const float re = stg[y * kWin + (x ^ (y & 31))];
                 const float im = stg[(kWin + y) * kWin + (x ^ ((kWin + y) & 31))];
                 if (re != 0.f || im != 0.f)
-                    atomicAdd(grid + (gy0 + y) * p.N + gx0 + x, make_float2(re, im));
+                    atomicAdd(grid + o.base + (o.gy0 + y) * p.N + o.gx0 + x,
+                              make_float2(re, im));
             }
         }
         __syncthreads();

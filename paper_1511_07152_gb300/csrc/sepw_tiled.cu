@@ -194,14 +194,14 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_k
         }
         flush();
         __syncthreads();
-        const int ty = it.tile / p.ntx, tx = it.tile - ty * p.ntx;
-        const int64_t gy0 = (int64_t)ty * p.T, gx0 = (int64_t)tx * p.T;
+        const TileOrigin o = tile_origin(p, it.tile);
         for (int e = threadIdx.x; e < W * W; e += kTiledThreads) {
             const int rr = e / W, cc = e - rr * W;
             const int a = rr * WP + cc;
             const float re = wre[a], im = wim[a];
             if (re != 0.f || im != 0.f) {
-                atomicAdd(grid + (gy0 + rr) * p.N + gx0 + cc, make_float2(re, im));
+                atomicAdd(grid + o.base + (o.gy0 + rr) * p.N + o.gx0 + cc,
+                          make_float2(re, im));
                 wre[a] = 0.f;
                 wim[a] = 0.f;
             }
@@ -264,14 +264,13 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) degrid_tiled
         if (item >= n_items)
             break;
         const WorkItem it = items[item];
-        const int ty = it.tile / p.ntx, tx = it.tile - ty * p.ntx;
-        const int64_t gy0 = (int64_t)ty * p.T, gx0 = (int64_t)tx * p.T;
+        const TileOrigin o = tile_origin(p, it.tile);
         for (int e = threadIdx.x; e < W * W; e += kTiledThreads) {
             const int rr = e / W, cc = e - rr * W;
-            const int64_t gy = gy0 + rr, gx = gx0 + cc;
+            const int64_t gy = o.gy0 + rr, gx = o.gx0 + cc;
             float2 g = make_float2(0.f, 0.f);
             if (gy < p.N && gx < p.N)
-                g = __ldg(grid + gy * p.N + gx);
+                g = __ldg(grid + o.base + gy * p.N + gx);
             wre[rr * WP + cc] = g.x;
             wim[rr * WP + cc] = g.y;
         }

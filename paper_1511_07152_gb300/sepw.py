@@ -78,6 +78,9 @@ _SIG = {
     "sepw_degrid_planned": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "sepw_image": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "sepw_device_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P]),
+    "sepw_plan_batched": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, _P]),
+    "sepw_grid_batched": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P,
+                                         _P, _P]),
     "sepw_grid_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _P, _I64, _P, _P, _P, _P,
                                          _P, _P, _P, _P]),
 }
@@ -231,6 +234,52 @@ def sepw_plan(ctx: Context, u, v, w, stream=None):
                             _ptr(v, torch.float64, n, "v"), _ptr(w, torch.float64, n, "w"),
                             _stream(stream)))
     ctx.plan_nvis = n
+    ctx.plan_ngrids = 1
+
+
+def _offsets(offsets):
+    import numpy as np
+    o = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    if o.ndim != 1 or o.size < 2:
+        raise ValueError("vis_offsets must be 1-D with ngrids + 1 entries")
+    return o
+
+
+def sepw_plan_batched(ctx: Context, vis_offsets, u, v, w, stream=None):
+    """Plan ngrids = len(vis_offsets) - 1 grids in one work list (host
+    offsets, copied during the call)."""
+    import torch
+    o = _offsets(vis_offsets)
+    n = u.numel()
+    if int(o[-1]) != n:
+        raise ValueError("vis_offsets[-1] must equal the number of visibilities")
+    ctx.check(LIB.sepw_plan_batched(ctx.handle, o.size - 1, o.ctypes.data,
+                                    _ptr(u, torch.float64, n, "u"),
+                                    _ptr(v, torch.float64, n, "v"),
+                                    _ptr(w, torch.float64, n, "w"), _stream(stream)))
+    ctx.plan_nvis = n
+    ctx.plan_ngrids = o.size - 1
+
+
+def sepw_grid_batched(ctx: Context, taps, vis_offsets, u, v, w, vis, weight, grids,
+                      n_dropped=None, stream=None):
+    import torch
+    o = _offsets(vis_offsets)
+    n = u.numel()
+    N = ctx.params.grid_size
+    ng = o.size - 1
+    ctx.check(LIB.sepw_grid_batched(ctx.handle, _ptr(taps, torch.complex64, ctx.ntaps, "taps"),
+                                    ng, o.ctypes.data, _ptr(u, torch.float64, n, "u"),
+                                    _ptr(v, torch.float64, n, "v"),
+                                    _ptr(w, torch.float64, n, "w"),
+                                    _ptr(vis, torch.complex64, n, "vis"),
+                                    _ptr(weight, torch.float32, n, "weight"),
+                                    _ptr(grids, torch.complex64, ng * N * N, "grids"),
+                                    _ptr(n_dropped, torch.int64, 1, "n_dropped"),
+                                    _stream(stream)))
+    ctx.plan_nvis = n
+    ctx.plan_ngrids = ng
+    return grids
 
 
 def sepw_plan_dropped(ctx: Context, stream=None) -> int:
@@ -251,17 +300,18 @@ def sepw_grid(ctx: Context, taps, u, v, w, vis, weight, grid, n_dropped=None, st
                             _ptr(grid, torch.complex64, N * N, "grid"),
                             _ptr(n_dropped, torch.int64, 1, "n_dropped"), _stream(stream)))
     ctx.plan_nvis = n
+    ctx.plan_ngrids = 1
     return grid
 
 
 def sepw_grid_planned(ctx: Context, taps, vis, weight, grid, stream=None):
     import torch
     n = ctx.plan_nvis
-    N = ctx.params.grid_size
+    N = ctx.params.grid_size * ctx.params.grid_size * getattr(ctx, "plan_ngrids", 1)
     ctx.check(LIB.sepw_grid_planned(ctx.handle, _ptr(taps, torch.complex64, ctx.ntaps, "taps"),
                                     _ptr(vis, torch.complex64, n, "vis"),
                                     _ptr(weight, torch.float32, n, "weight"),
-                                    _ptr(grid, torch.complex64, N * N, "grid"),
+                                    _ptr(grid, torch.complex64, N, "grid"),
                                     _stream(stream)))
     return grid
 
@@ -279,16 +329,17 @@ def sepw_degrid(ctx: Context, taps, u, v, w, grid, weight, vis_out, n_dropped=No
                               _ptr(vis_out, torch.complex64, n, "vis_out"),
                               _ptr(n_dropped, torch.int64, 1, "n_dropped"), _stream(stream)))
     ctx.plan_nvis = n
+    ctx.plan_ngrids = 1
     return vis_out
 
 
 def sepw_degrid_planned(ctx: Context, taps, grid, weight, vis_out, stream=None):
     import torch
     n = ctx.plan_nvis
-    N = ctx.params.grid_size
+    N = ctx.params.grid_size * ctx.params.grid_size * getattr(ctx, "plan_ngrids", 1)
     ctx.check(LIB.sepw_degrid_planned(ctx.handle,
                                       _ptr(taps, torch.complex64, ctx.ntaps, "taps"),
-                                      _ptr(grid, torch.complex64, N * N, "grid"),
+                                      _ptr(grid, torch.complex64, N, "grid"),
                                       _ptr(weight, torch.float32, n, "weight"),
                                       _ptr(vis_out, torch.complex64, n, "vis_out"),
                                       _stream(stream)))
