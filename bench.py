@@ -266,7 +266,8 @@ def run_batched(S, torch, args):
     out = {"workload": wl.name, "ngrids": ng, "nvis": wl.nvis, "support": wl.support,
            "counts_min_max": [int(wl.extra["counts"].min()), int(wl.extra["counts"].max())],
            "autotune": tuned}
-    for name, form, tile in (("tiled_fp32", S.FORM_TILED, tuned["tile"]),
+    tuned_tile = tuned["tile"] if tuned["form"] == "tiled" else 0
+    for name, form, tile in (("tiled_fp32", S.FORM_TILED, tuned_tile),
                              ("tc_fp16", S.FORM_TC_FP16, 0)):
         ctx = S.sepw_create(S.make_params(**wl.params(), tile=tile, form=form))
         taps = S.sepw_make_taps(ctx)

@@ -24,7 +24,10 @@ FORM_ERROR = {"plain": 1e-5, "tiled": 1e-5, "tc_bf16": 1e-2, "tc_fp16": 1.5e-3}
 
 def candidate_tiles(support: int, form: str) -> list[int]:
     """Even tile edges T with T + S - 1 <= 64 (the shared / tensor-memory
-    window), restricted to the sizes worth timing."""
+    window), restricted to the sizes worth timing.  The plain form has no
+    tiles (one candidate, 0)."""
+    if form == "plain":
+        return [0]
     out = []
     for T in (16, 24, 32, 40, 48, 56):
         if T + support - 1 <= 64:
@@ -106,7 +109,8 @@ def tune(params: dict, u, v, w, vis, weight, max_error: float = 1e-5, forms=None
         hit = cache.get(key)
         if hit and FORM_ERROR[hit["form"]] <= max_error:
             return hit
-    forms = forms or [f for f in ("tiled", "tc_fp16", "tc_bf16") if FORM_ERROR[f] <= max_error]
+    forms = forms or [f for f in ("plain", "tiled", "tc_fp16", "tc_bf16")
+                      if FORM_ERROR[f] <= max_error]
     codes = {v_: k for k, v_ in FORM_NAMES.items()}
     N = params["grid_size"]
     ng = 1 if vis_offsets is None else len(vis_offsets) - 1

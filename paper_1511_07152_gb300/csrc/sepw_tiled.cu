@@ -111,15 +111,28 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_k
         wre[e] = 0.f;
         wim[e] = 0.f;
     }
+    __shared__ WorkItem s_it;
+    __shared__ float2 *s_tile_grid;  // grid cell of the tile's window origin
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0)
-            s_item = atomicAdd(counter, 1);
+        if (threadIdx.x == 0) {
+            const int item = atomicAdd(counter, 1);
+            s_item = item;
+            if (item < n_items) {
+                s_it = items[item];
+                const TileOrigin o = tile_origin(p, s_it.tile);
+                s_tile_grid = grid + o.base + o.gy0 * p.N + o.gx0;
+            }
+        }
         __syncthreads();
         const int item = s_item;
         if (item >= n_items)
             break;
-        const WorkItem it = items[item];
+        const WorkItem it = s_it;
+        float2 *tgrid = s_tile_grid;
+        // sparse items (fewer cell updates than window cells) skip the shared
+        // window and add their register blocks straight into the grid
+        const bool direct = it.count * S * S < W * W;
         const int per = (it.count + kTiledWarps - 1) / kTiledWarps;
         const int b0 = it.start + min(it.count, warp * per);
         const int b1 = it.start + min(it.count, (warp + 1) * per);
@@ -134,13 +147,21 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_k
             if (cur >= 0 && lane_ok) {
                 const int ly = key_ly(cur), lx = key_lx(cur);
                 const float sg = (cur & 1) ? -1.f : 1.f;
+                if (direct) {
+                    float2 *g = tgrid + (int64_t)(ly + rg * RPL) * p.N + lx + j;
 #pragma unroll
-                for (int q = 0; q < RPL; ++q) {
-                    const int k = rg * RPL + q;
-                    if (k < S) {
-                        const int a = (ly + k) * WP + lx + j;
-                        atomicAdd(wre + a, ar[q]);
-                        atomicAdd(wim + a, sg * ai[q]);
+                    for (int q = 0; q < RPL; ++q)
+                        if (rg * RPL + q < S)
+                            atomicAdd(g + (int64_t)q * p.N, make_float2(ar[q], sg * ai[q]));
+                } else {
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q) {
+                        const int k = rg * RPL + q;
+                        if (k < S) {
+                            const int a = (ly + k) * WP + lx + j;
+                            atomicAdd(wre + a, ar[q]);
+                            atomicAdd(wim + a, sg * ai[q]);
+                        }
                     }
                 }
             }
@@ -193,17 +214,19 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_k
             __syncwarp();
         }
         flush();
+        if (direct)
+            continue;
         __syncthreads();
-        const TileOrigin o = tile_origin(p, it.tile);
-        for (int e = threadIdx.x; e < W * W; e += kTiledThreads) {
-            const int rr = e / W, cc = e - rr * W;
-            const int a = rr * WP + cc;
-            const float re = wre[a], im = wim[a];
-            if (re != 0.f || im != 0.f) {
-                atomicAdd(grid + o.base + (o.gy0 + rr) * p.N + o.gx0 + cc,
-                          make_float2(re, im));
-                wre[a] = 0.f;
-                wim[a] = 0.f;
+        for (int rr = warp; rr < W; rr += kTiledWarps) {
+            float2 *grow = tgrid + (int64_t)rr * p.N;
+            for (int cc = lane; cc < W; cc += 32) {
+                const int a = rr * WP + cc;
+                const float re = wre[a], im = wim[a];
+                if (re != 0.f || im != 0.f) {
+                    atomicAdd(grow + cc, make_float2(re, im));
+                    wre[a] = 0.f;
+                    wim[a] = 0.f;
+                }
             }
         }
     }
@@ -265,14 +288,16 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) degrid_tiled
             break;
         const WorkItem it = items[item];
         const TileOrigin o = tile_origin(p, it.tile);
-        for (int e = threadIdx.x; e < W * W; e += kTiledThreads) {
-            const int rr = e / W, cc = e - rr * W;
-            const int64_t gy = o.gy0 + rr, gx = o.gx0 + cc;
-            float2 g = make_float2(0.f, 0.f);
-            if (gy < p.N && gx < p.N)
-                g = __ldg(grid + o.base + gy * p.N + gx);
-            wre[rr * WP + cc] = g.x;
-            wim[rr * WP + cc] = g.y;
+        for (int rr = warp; rr < W; rr += kTiledWarps) {
+            const int64_t gy = o.gy0 + rr;
+            const float2 *grow = grid + o.base + gy * p.N + o.gx0;
+            for (int cc = lane; cc < W; cc += 32) {
+                float2 g = make_float2(0.f, 0.f);
+                if (gy < p.N && o.gx0 + cc < p.N)
+                    g = __ldg(grow + cc);
+                wre[rr * WP + cc] = g.x;
+                wim[rr * WP + cc] = g.y;
+            }
         }
         __syncthreads();
         const int per = (it.count + kTiledWarps - 1) / kTiledWarps;
