@@ -17,10 +17,10 @@
 // complex products with the v-taps into a register block.  A block of
 // visibilities with one key shares the register block; for conj visibilities
 // it accumulates conj(W V) F1 F1 and is conjugated when it is flushed, so the
-// inner loop needs no sign handling.  The register block is added into the
-// shared window (shared-memory atomics) when the key changes, and the window
-// is added to the HBM grid once per item (float2 atomics: windows of
-// neighbouring tiles and other items of the same tile overlap).
+// inner loop needs no sign handling.  The register block is added to the HBM
+// grid with float2 atomics (native L2 reductions) when the key changes.  (A
+// shared-memory window in between was slower: float adds to shared memory
+// run as compare-and-swap loops, several instructions per add.)
 //
 // Degridding (the adjoint): the window is loaded from HBM; the lane keeps its
 // RPL window values (conjugated for plain-kernel groups) in registers while
@@ -51,7 +51,7 @@ __device__ __forceinline__ int meta_dv(int y) { return y >> 13; }
 
 constexpr int kTiledThreads = 256;
 constexpr int kTiledWarps = kTiledThreads / 32;
-constexpr int kTiledBlocksPerSM = 3;
+constexpr int kTiledBlocksPerSM = 4;
 
 __device__ __forceinline__ int key_ly(int key) { return (key >> 1) >> 6; }
 __device__ __forceinline__ int key_lx(int key) { return (key >> 1) & 63; }
@@ -90,29 +90,22 @@ __device__ __forceinline__ void load_vtaps(const float2 *__restrict__ row, int r
 
 template <int S>
 __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_kernel(
-    DevParams p, int WP, const WorkItem *__restrict__ items,
-    const int32_t *__restrict__ nitems, int32_t *counter, const uint64_t *__restrict__ rec,
-    const int32_t *__restrict__ perm, const float2 *__restrict__ vis,
-    const float *__restrict__ weight, const float2 *__restrict__ taps, float2 *grid)
+    DevParams p, const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems,
+    int32_t *counter, const uint64_t *__restrict__ rec, const int32_t *__restrict__ perm,
+    const float2 *__restrict__ vis, const float *__restrict__ weight,
+    const float2 *__restrict__ taps, float2 *grid)
 {
     constexpr int RG = Layout<S>::RG, RPL = Layout<S>::RPL;
-    extern __shared__ float4 smem4[];
+    __shared__ int4 s_meta[kTiledWarps * 32];
     __shared__ int s_item;
-    const int W = p.T + S - 1;
-    float *wre = reinterpret_cast<float *>(smem4);
-    float *wim = wre + W * WP;
+    __shared__ WorkItem s_it;
+    __shared__ float2 *s_tile_grid;  // grid cell of the tile's window origin
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int4 *meta = reinterpret_cast<int4 *>(smem4 + ((2 * W * WP + 3) / 4)) + warp * 32;
+    int4 *meta = s_meta + warp * 32;
     const int rg = lane / S, j = lane % S;
     const bool lane_ok = Layout<S>::ALL_LANES || rg < RG;
     const int n_items = *nitems;
 
-    for (int e = threadIdx.x; e < W * WP; e += kTiledThreads) {
-        wre[e] = 0.f;
-        wim[e] = 0.f;
-    }
-    __shared__ WorkItem s_it;
-    __shared__ float2 *s_tile_grid;  // grid cell of the tile's window origin
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -129,10 +122,7 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_k
         if (item >= n_items)
             break;
         const WorkItem it = s_it;
-        float2 *tgrid = s_tile_grid;
-        // sparse items (fewer cell updates than window cells) skip the shared
-        // window and add their register blocks straight into the grid
-        const bool direct = it.count * S * S < W * W;
+        float2 *const tgrid = s_tile_grid;
         const int per = (it.count + kTiledWarps - 1) / kTiledWarps;
         const int b0 = it.start + min(it.count, warp * per);
         const int b1 = it.start + min(it.count, (warp + 1) * per);
@@ -143,27 +133,16 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_k
             ar[q] = ai[q] = 0.f;
         int cur = -1;
 
+        // adds the register block of key `cur` to the grid (float2 atomics,
+        // native L2 reductions) and clears it
         auto flush = [&]() {
             if (cur >= 0 && lane_ok) {
-                const int ly = key_ly(cur), lx = key_lx(cur);
                 const float sg = (cur & 1) ? -1.f : 1.f;
-                if (direct) {
-                    float2 *g = tgrid + (int64_t)(ly + rg * RPL) * p.N + lx + j;
+                float2 *g = tgrid + (int64_t)(key_ly(cur) + rg * RPL) * p.N + key_lx(cur) + j;
 #pragma unroll
-                    for (int q = 0; q < RPL; ++q)
-                        if (rg * RPL + q < S)
-                            atomicAdd(g + (int64_t)q * p.N, make_float2(ar[q], sg * ai[q]));
-                } else {
-#pragma unroll
-                    for (int q = 0; q < RPL; ++q) {
-                        const int k = rg * RPL + q;
-                        if (k < S) {
-                            const int a = (ly + k) * WP + lx + j;
-                            atomicAdd(wre + a, ar[q]);
-                            atomicAdd(wim + a, sg * ai[q]);
-                        }
-                    }
-                }
+                for (int q = 0; q < RPL; ++q)
+                    if (Layout<S>::FULL_ROWS || rg * RPL + q < S)
+                        atomicAdd(g + (int64_t)q * p.N, make_float2(ar[q], sg * ai[q]));
             }
 #pragma unroll
             for (int q = 0; q < RPL; ++q)
@@ -214,21 +193,6 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_k
             __syncwarp();
         }
         flush();
-        if (direct)
-            continue;
-        __syncthreads();
-        for (int rr = warp; rr < W; rr += kTiledWarps) {
-            float2 *grow = tgrid + (int64_t)rr * p.N;
-            for (int cc = lane; cc < W; cc += 32) {
-                const int a = rr * WP + cc;
-                const float re = wre[a], im = wim[a];
-                if (re != 0.f || im != 0.f) {
-                    atomicAdd(grow + cc, make_float2(re, im));
-                    wre[a] = 0.f;
-                    wim[a] = 0.f;
-                }
-            }
-        }
     }
 }
 
@@ -416,15 +380,12 @@ static cudaError_t launch_grid_S(const DevParams &p, const Plan &plan, const flo
                                  const float *weight, const float2 *taps, float2 *grid,
                                  int num_sms, cudaStream_t s)
 {
-    const int W = p.T + S - 1;
-    const int WP = window_stride(W, S);
-    const size_t shm = tiled_smem(W, WP);
     cudaError_t e = cudaMemsetAsync(plan.d_item_counter, 0, sizeof(int32_t), s);
     if (e != cudaSuccess)
         return e;
-    grid_tiled_kernel<S><<<num_sms * kTiledBlocksPerSM, kTiledThreads, shm, s>>>(
-        p, WP, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm,
-        vis, weight, taps, grid);
+    grid_tiled_kernel<S><<<num_sms * kTiledBlocksPerSM, kTiledThreads, 0, s>>>(
+        p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm, vis,
+        weight, taps, grid);
     return cudaGetLastError();
 }
 
