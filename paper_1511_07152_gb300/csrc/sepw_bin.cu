@@ -73,7 +73,9 @@ __global__ void __launch_bounds__(256) locate_bin_kernel(
 }
 
 // Pass 2 (one block of 1024 threads): exclusive scans of the tile counts
-// (-> slot cursors) and of the per-tile chunk counts (-> work items).
+// (-> slot cursors) and of the per-tile chunk counts (-> work items).  Full
+// chunks (kChunk visibilities) are listed before the partial ones, so that
+// dynamically scheduled workers take the heavy items first.
 constexpr int kScanThreads = 1024;
 
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(
@@ -81,48 +83,62 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
     WorkItem *__restrict__ items, int32_t *nitems)
 {
     __shared__ int64_t s_cnt[kScanThreads];
-    __shared__ int32_t s_chk[kScanThreads];
-    int t = threadIdx.x;
-    int per = (ntiles + kScanThreads - 1) / kScanThreads;
-    int lo = min(ntiles, t * per), hi = min(ntiles, lo + per);
+    __shared__ int32_t s_full[kScanThreads];
+    __shared__ int32_t s_part[kScanThreads];
+    const int t = threadIdx.x;
+    const int per = (ntiles + kScanThreads - 1) / kScanThreads;
+    const int lo = min(ntiles, t * per), hi = min(ntiles, lo + per);
     int64_t c = 0;
-    int32_t k = 0;
+    int32_t nf = 0, np = 0;
     for (int i = lo; i < hi; ++i) {
-        int n = tile_count[i];
+        const int n = tile_count[i];
         c += n;
-        k += (n + kChunk - 1) / kChunk;
+        nf += n / kChunk;
+        np += (n % kChunk) != 0;
     }
     s_cnt[t] = c;
-    s_chk[t] = k;
+    s_full[t] = nf;
+    s_part[t] = np;
     __syncthreads();
-    // Hillis-Steele inclusive scan over 1024 partials
+    // Hillis-Steele inclusive scans over the 1024 partials
     for (int off = 1; off < kScanThreads; off <<= 1) {
-        int64_t a = t >= off ? s_cnt[t - off] : 0;
-        int32_t b = t >= off ? s_chk[t - off] : 0;
+        const int64_t a = t >= off ? s_cnt[t - off] : 0;
+        const int32_t b = t >= off ? s_full[t - off] : 0;
+        const int32_t d = t >= off ? s_part[t - off] : 0;
         __syncthreads();
         s_cnt[t] += a;
-        s_chk[t] += b;
+        s_full[t] += b;
+        s_part[t] += d;
         __syncthreads();
     }
+    const int32_t total_full = s_full[kScanThreads - 1];
     int64_t off_c = s_cnt[t] - c;
-    int32_t off_k = s_chk[t] - k;
+    int32_t off_f = s_full[t] - nf;
+    int32_t off_p = total_full + s_part[t] - np;
     for (int i = lo; i < hi; ++i) {
-        int n = tile_count[i];
+        const int n = tile_count[i];
         cursor[i] = (int32_t)off_c;
-        int nk = (n + kChunk - 1) / kChunk;
+        const int nk = n / kChunk;
         for (int q = 0; q < nk; ++q) {
             WorkItem it;
             it.tile = i;
             it.start = (int32_t)(off_c + (int64_t)q * kChunk);
-            it.count = min(kChunk, n - q * kChunk);
+            it.count = kChunk;
             it.pad = 0;
-            items[off_k + q] = it;
+            items[off_f++] = it;
+        }
+        if (n % kChunk) {
+            WorkItem it;
+            it.tile = i;
+            it.start = (int32_t)(off_c + (int64_t)nk * kChunk);
+            it.count = n % kChunk;
+            it.pad = 0;
+            items[off_p++] = it;
         }
         off_c += n;
-        off_k += nk;
     }
     if (t == kScanThreads - 1)
-        *nitems = s_chk[t];
+        *nitems = total_full + s_part[t];
 }
 
 // Pass 3: scatter visibility ids and records to their tile's slots.

@@ -1,8 +1,9 @@
 // Tiled FP32 gridder and degridder (the separable update of Sec. 5, binned).
 //
-// A persistent CTA takes work items (<= kChunk visibilities of one T x T tile,
-// sorted by (footprint origin, conj)) from an atomic counter.  The tile's
-// window of (T + S - 1)^2 cells lives in shared memory (separate re / im
+// Work items are <= kChunk visibilities of one T x T tile, sorted by
+// (footprint origin, conj), taken from an atomic counter: by a whole warp in
+// the gridder, by a whole CTA in the degridder.  The degridder keeps the
+// tile's window of (T + S - 1)^2 cells in shared memory (separate re / im
 // planes; row stride chosen so the row groups of a warp hit disjoint banks).
 //
 // Lane (rg, j) of a warp owns footprint column j and rows rg*RPL ..
@@ -97,35 +98,24 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_k
 {
     constexpr int RG = Layout<S>::RG, RPL = Layout<S>::RPL;
     __shared__ int4 s_meta[kTiledWarps * 32];
-    __shared__ int s_item;
-    __shared__ WorkItem s_it;
-    __shared__ float2 *s_tile_grid;  // grid cell of the tile's window origin
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int4 *meta = s_meta + warp * 32;
     const int rg = lane / S, j = lane % S;
     const bool lane_ok = Layout<S>::ALL_LANES || rg < RG;
     const int n_items = *nitems;
 
+    // every warp takes whole work items on its own: no block-wide barrier
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int item = atomicAdd(counter, 1);
-            s_item = item;
-            if (item < n_items) {
-                s_it = items[item];
-                const TileOrigin o = tile_origin(p, s_it.tile);
-                s_tile_grid = grid + o.base + o.gy0 * p.N + o.gx0;
-            }
-        }
-        __syncthreads();
-        const int item = s_item;
+        int item = 0;
+        if (lane == 0)
+            item = atomicAdd(counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items)
             break;
-        const WorkItem it = s_it;
-        float2 *const tgrid = s_tile_grid;
-        const int per = (it.count + kTiledWarps - 1) / kTiledWarps;
-        const int b0 = it.start + min(it.count, warp * per);
-        const int b1 = it.start + min(it.count, (warp + 1) * per);
+        const WorkItem it = items[item];
+        const TileOrigin o = tile_origin(p, it.tile);
+        float2 *const tgrid = grid + o.base + o.gy0 * p.N + o.gx0;
+        const int b0 = it.start, b1 = it.start + it.count;
 
         float ar[RPL], ai[RPL];
 #pragma unroll
