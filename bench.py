@@ -307,6 +307,38 @@ def run_batched(S, torch, args):
     return out
 
 
+def run_predict_autograd(S, torch, args):
+    """Workload 4: differentiable prediction of ~4M visibilities from a 2048^2
+    model (support 16, oversampling 16, 64 planes): forward = IMAGE_TO_GRID +
+    degridding, backward = gridding + adjoint image step (torch.autograd)."""
+    import synth
+    from paper_1511_07152_gb300 import autograd as AG
+    model, wl = synth.point_source_model()
+    ctx = S.sepw_create(S.make_params(**wl.params(), form=S.FORM_TILED))
+    taps = S.sepw_make_taps(ctx)
+    d = {k: torch.from_numpy(getattr(wl, k)).cuda() for k in ("u", "v", "w", "vis", "weight")}
+    S.sepw_plan(ctx, d["u"], d["v"], d["w"])
+    I = torch.from_numpy(model).cuda().requires_grad_(True)
+    target = d["vis"]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fw, bw = [], []
+    for k in range(max(3, args.steps // 2) + 2):
+        I.grad = None
+        ev[0].record()
+        loss = AG.chi2(AG.predict(I, ctx, taps), target, d["weight"])
+        ev[1].record()
+        loss.backward()
+        ev[2].record()
+        torch.cuda.synchronize()
+        if k >= 2:
+            fw.append(ev[0].elapsed_time(ev[1]))
+            bw.append(ev[1].elapsed_time(ev[2]))
+    return {"workload": wl.name, "nvis": wl.nvis, "grid": wl.grid_size,
+            "forward_ms": statistics.median(fw), "backward_ms": statistics.median(bw),
+            "note": "loss = weighted chi^2 (float64 sum); forward and backward each include "
+                    "one 2048^2 cuFFT and one degrid/grid of all visibilities"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -451,6 +483,9 @@ def run_ours(args):
     batched = None
     if rank == 0 and not args.skip_batched:
         batched = run_batched(S, torch, args)
+    predict = None
+    if rank == 0 and not args.skip_autograd:
+        predict = run_predict_autograd(S, torch, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
@@ -474,7 +509,7 @@ def run_ours(args):
             "phases_ms": {"plan": plan_ms, "grid": grid_ms, "degrid": degrid_ms},
             "grid_updates_per_s": nkept * Ssup * Ssup * 2 * ws / (ms * 1e-3),
             "speedup_vs_plain_fp32": (plain["ms_per_step"] / ms) if plain else None,
-            "forms": forms, "batched": batched,
+            "forms": forms, "batched": batched, "predict_autograd": predict,
             "roofline": roofline, "roofline_hbm": roofline_hbm, "peak_source": peak_src,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "wall_s_timed": time.perf_counter() - t_start,
@@ -506,6 +541,7 @@ def main():
     ap.add_argument("--skip-tc", action="store_true")
     ap.add_argument("--skip-errors", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-autograd", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

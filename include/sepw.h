@@ -75,6 +75,7 @@ extern "C" {
 /* image directions (sepw_image) */
 #define SEPW_GRID_TO_IMAGE 0
 #define SEPW_IMAGE_TO_GRID 1
+#define SEPW_IMAGE_TO_GRID_ADJOINT 2  /* exact adjoint of SEPW_IMAGE_TO_GRID */
 
 typedef struct CUstream_st *sepw_stream_t; /* same type as cudaStream_t */
 
@@ -225,8 +226,12 @@ SEPW_API int sepw_device_status(sepw_ctx *ctx, int *status, sepw_stream_t stream
  *   SEPW_IMAGE_TO_GRID (prediction direction):  grid[cv][cu] =
  *       sum_{a,b} exp(-2 pi i ((cu-N/2) nu_a + (cv-N/2) nu_b)) I[b][a] /
  *       (n_ab c1(nu_a) c1(nu_b))
- * with n_ab = sqrt(1 - l_a^2 - m_b^2).  Uses cuFFT (FP32 C2C); the plan is
- * created on first use. */
+ * with n_ab = sqrt(1 - l_a^2 - m_b^2).
+ *   SEPW_IMAGE_TO_GRID_ADJOINT (the backward pass of prediction):
+ *       I[b][a] = 1 / (n_ab c1(nu_a) c1(nu_b)) *
+ *       sum_{cu,cv} grid[cv][cu] exp(2 pi i ((cu-N/2) nu_a + (cv-N/2) nu_b))
+ *       = GRID_TO_IMAGE / n_ab^2.
+ * Uses cuFFT (FP32 C2C); the plan is created on first use. */
 SEPW_API int sepw_image(sepw_ctx *ctx, int direction, float *buf, sepw_stream_t stream);
 
 /* Limits of sepw_grid_noalloc's fixed scratch array. */

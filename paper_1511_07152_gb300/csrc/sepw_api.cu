@@ -588,7 +588,8 @@ int sepw_image(sepw_ctx *ctx, int direction, float *buf, sepw_stream_t stream)
 {
     if (!ctx)
         return SEPW_EINVAL;
-    if (direction != SEPW_GRID_TO_IMAGE && direction != SEPW_IMAGE_TO_GRID)
+    if (direction != SEPW_GRID_TO_IMAGE && direction != SEPW_IMAGE_TO_GRID &&
+        direction != SEPW_IMAGE_TO_GRID_ADJOINT)
         return fail(ctx, SEPW_EINVAL, "bad direction %d", direction);
     int rc = check_dev(ctx, buf, "buf", false);
     if (rc)
@@ -604,8 +605,8 @@ int sepw_image(sepw_ctx *ctx, int direction, float *buf, sepw_stream_t stream)
         return fail(ctx, SEPW_ECUDA, "cufftSetStream failed");
     SEPW_CUDA(ctx, launch_image_pre(ctx->dp, direction, ctx->d_taper32, (float2 *)buf, s));
     cufftResult r = cufftExecC2C(ctx->fft, (cufftComplex *)buf, (cufftComplex *)buf,
-                                 direction == SEPW_GRID_TO_IMAGE ? CUFFT_INVERSE
-                                                                 : CUFFT_FORWARD);
+                                 direction == SEPW_IMAGE_TO_GRID ? CUFFT_FORWARD
+                                                                 : CUFFT_INVERSE);
     if (r != CUFFT_SUCCESS)
         return fail(ctx, SEPW_ECUDA, "cufftExecC2C failed (%d)", (int)r);
     SEPW_CUDA(ctx, launch_image_post(ctx->dp, direction, ctx->d_taper32, (float2 *)buf, s));

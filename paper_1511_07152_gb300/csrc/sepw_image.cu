@@ -8,6 +8,8 @@
 // post-scaling passes:
 //   GRID_TO_IMAGE:  buf *= (-1)^(a+b);  inverse FFT;  buf *= (-1)^(a+b) n/(c c)
 //   IMAGE_TO_GRID:  buf *= (-1)^(a+b)/(n c c);  forward FFT;  buf *= (-1)^(a+b)
+//   IMAGE_TO_GRID_ADJOINT:
+//                   buf *= (-1)^(a+b);  inverse FFT;  buf *= (-1)^(a+b)/(n c c)
 #include "sepw_internal.cuh"
 
 namespace sepw {
@@ -41,16 +43,22 @@ static cudaError_t scale(const DevParams &p, int mode, const float *taper, float
     return cudaGetLastError();
 }
 
+// The inverse transform (GRID_TO_IMAGE and the adjoint of IMAGE_TO_GRID)
+// scales after the FFT; the forward transform (IMAGE_TO_GRID) before it.
 cudaError_t launch_image_pre(const DevParams &p, int direction, const float *taper,
                              float2 *buf, cudaStream_t s)
 {
-    return scale(p, direction == SEPW_GRID_TO_IMAGE ? 0 : 2, taper, buf, s);
+    return scale(p, direction == SEPW_IMAGE_TO_GRID ? 2 : 0, taper, buf, s);
 }
 
 cudaError_t launch_image_post(const DevParams &p, int direction, const float *taper,
                               float2 *buf, cudaStream_t s)
 {
-    return scale(p, direction == SEPW_GRID_TO_IMAGE ? 1 : 0, taper, buf, s);
+    if (direction == SEPW_GRID_TO_IMAGE)
+        return scale(p, 1, taper, buf, s);
+    if (direction == SEPW_IMAGE_TO_GRID_ADJOINT)
+        return scale(p, 2, taper, buf, s);
+    return scale(p, 0, taper, buf, s);
 }
 
 }  // namespace sepw

@@ -20,6 +20,7 @@ FORM_TC_BF16 = 2
 FORM_TC_FP16 = 3
 GRID_TO_IMAGE = 0
 IMAGE_TO_GRID = 1
+IMAGE_TO_GRID_ADJOINT = 2
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP, ENOPLAN, ETOOLARGE = 0, -1, -2, -3, -4, -5, -6, -7
 NOALLOC_MAX_VIS = 524288

@@ -1,0 +1,123 @@
+"""torch.autograd over the C ABI: Grid (backward = degridding) and Predict
+(IMAGE_TO_GRID + degridding; backward = gridding + the adjoint image step),
+against the FP64 oracle's analytic gradient and central finite differences."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1511_07152_gb300 import build
+    build.build()
+    import paper_1511_07152_gb300.sepw as S
+    from paper_1511_07152_gb300 import autograd as AG
+    return torch, S, AG
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.complex128).ravel()
+    b = np.asarray(b, np.complex128).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _setup(torch, S, wl, form=1):
+    ctx = S.sepw_create(S.make_params(**wl.params(), form=form))
+    taps = S.sepw_make_taps(ctx)
+    d = {k: torch.from_numpy(getattr(wl, k)).cuda() for k in ("u", "v", "w", "vis", "weight")}
+    S.sepw_plan(ctx, d["u"], d["v"], d["w"])
+    return ctx, taps, d
+
+
+def test_grid_backward_is_degridding(env):
+    torch, S, AG = env
+    wl = synth.random_case(41, 5000, 128, 8, 8, 9, w_max=300.0)
+    ctx, taps, d = _setup(torch, S, wl)
+    vis = d["vis"].clone().requires_grad_(True)
+    G = AG.grid(vis, ctx, taps, d["weight"])
+    rng = np.random.default_rng(2)
+    X = torch.from_numpy((rng.standard_normal((128, 128)) +
+                          1j * rng.standard_normal((128, 128))).astype(np.complex64)).cuda()
+    # L = Re <X, G>  =>  dL/dvis* = A^H X / 2 in torch's convention: grad = A^H X
+    L = (X.conj() * G).real.sum()
+    L.backward()
+    p = O.params_from(wl.params())
+    loc = O.locate(p, wl.u, wl.v, wl.w)
+    want = O.degrid_separable(p, loc, X.cpu().numpy(), wl.weight, O.taps(p))
+    assert rel_l2(vis.grad.cpu().numpy(), want) <= 1e-5
+
+
+def _oracle_grad(wl, image, target):
+    p = O.params_from(wl.params())
+    loc = O.locate(p, wl.u, wl.v, wl.w)
+    T = O.taps(p)
+    r = O.degrid_separable(p, loc, O.image_to_grid(p, image), None, T) - target
+    G = O.grid_separable(p, loc, wl.weight.astype(np.float64) * r, None, T)
+    l = O.pixel_l(p.N, p.fov)
+    L, M = np.meshgrid(l, l)
+    return 2 * np.real(O.grid_to_image(p, G) / (1 - L * L - M * M))
+
+
+@pytest.mark.parametrize("form", [1, 3])
+def test_predict_gradient_matches_oracle(env, form):
+    """Gradient of sum_i W_i |Predict(I)_i - V_i|^2 w.r.t. a real image."""
+    torch, S, AG = env
+    wl = synth.random_case(42, 6000, 128, 8, 8, 9, w_max=300.0, radius_cells=50.0)
+    ctx, taps, d = _setup(torch, S, wl, form=form)
+    rng = np.random.default_rng(3)
+    image = rng.standard_normal((128, 128)).astype(np.float32)
+    I = torch.from_numpy(image).cuda().requires_grad_(True)
+    target = d["vis"]
+    loss = AG.chi2(AG.predict(I, ctx, taps), target, d["weight"])
+    loss.backward()
+    want = _oracle_grad(wl, image.astype(np.float64), wl.vis.astype(np.complex128))
+    # the tensor-core form grids the backward in FP16 (rel. error ~4e-4)
+    tol = 1e-4 if form == 1 else 2e-3
+    assert rel_l2(I.grad.cpu().numpy(), want) <= tol
+
+
+def test_predict_finite_differences_point_source_model(env):
+    """Workload 4: 2048^2 model of 500 point sources + noise, ~4M
+    visibilities (support 16, oversampling 16, 64 planes), target =
+    Predict(model) + N(0, 0.01^2) noise; central differences with step 1e-3
+    on 64 seeded pixels.  The loss is quadratic in the image, so the
+    differences are exact up to the FP32 rounding of the two predictions,
+    estimated at ~2e-3 of the derivative; the bar is 1e-2 of the largest
+    derivative among the 64 pixels."""
+    torch, S, AG = env
+    model, wl = synth.point_source_model()
+    ctx, taps, d = _setup(torch, S, wl)
+    I = torch.from_numpy(model).cuda()
+    with torch.no_grad():
+        clean = AG.predict(I, ctx, taps)
+    rng = np.random.default_rng(151107152 * 10 + 40)
+    noise = (0.01 * (rng.standard_normal(wl.nvis) + 1j * rng.standard_normal(wl.nvis))
+             ).astype(np.complex64)
+    target = clean + torch.from_numpy(noise).cuda()
+    Ig = I.clone().requires_grad_(True)
+    loss = AG.chi2(AG.predict(Ig, ctx, taps), target, d["weight"])
+    loss.backward()
+    grad = Ig.grad.cpu().numpy()
+    h = 1e-3
+    N = wl.grid_size
+    pix = rng.integers(N // 4, 3 * N // 4, size=(64, 2))
+    fd = []
+    with torch.no_grad():
+        for b, a in pix:
+            e = torch.zeros_like(I)
+            e[b, a] = h
+            lp = AG.chi2(AG.predict(I + e, ctx, taps), target, d["weight"]).item()
+            lm = AG.chi2(AG.predict(I - e, ctx, taps), target, d["weight"]).item()
+            fd.append((lp - lm) / (2 * h))
+    fd = np.array(fd)
+    g = grad[pix[:, 0], pix[:, 1]]
+    assert np.max(np.abs(fd - g)) <= 1e-2 * np.max(np.abs(g))
