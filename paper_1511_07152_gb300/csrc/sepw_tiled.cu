@@ -6,13 +6,12 @@
 // tile's window of (T + S - 1)^2 cells in shared memory (separate re / im
 // planes; row stride chosen so the row groups of a warp hit disjoint banks).
 //
-// Per block of 32 visibilities a warp first decodes the records once (one per
+// Lane (rg, j) of a warp owns footprint column j and rows rg*RPL ..
+// rg*RPL + RPL - 1.  Each warp walks a contiguous slice of the item.  Per
+// block of 32 visibilities the warp first decodes the records once (one per
 // lane: origin/conj key, tap-row offsets, W V) into one 16-byte shared-memory
-// record each; the inner loops then read them as broadcasts and load the
-// v-taps with 128-bit loads.  In the gridder a warp handles 32 / S
-// visibilities at a time and lane j of each group of S lanes owns footprint
-// column j (all S rows); in the degridder lane (rg, j) owns column j and rows
-// rg*RPL .. rg*RPL + RPL - 1 of one visibility at a time.
+// record each; the inner loop then reads them as broadcasts and loads the
+// v-taps of its rows with 128-bit loads.
 //
 // Gridding: per visibility the lane forms the partial product W V F1(u - u_i)
 // for its column once (Sec. 5: reused down every row) and accumulates RPL
@@ -53,8 +52,7 @@ __device__ __forceinline__ int meta_dv(int y) { return y >> 13; }
 
 constexpr int kTiledThreads = 256;
 constexpr int kTiledWarps = kTiledThreads / 32;
-constexpr int kTiledBlocksPerSM = 4;  // degridder
-constexpr int kGridBlocksPerSM = 2;   // gridder: a full column per lane needs ~90 registers
+constexpr int kTiledBlocksPerSM = 4;
 
 __device__ __forceinline__ int key_ly(int key) { return (key >> 1) >> 6; }
 __device__ __forceinline__ int key_lx(int key) { return (key >> 1) & 63; }
@@ -91,44 +89,19 @@ __device__ __forceinline__ void load_vtaps(const float2 *__restrict__ row, int r
     }
 }
 
-// Gridder lane layout: a warp works on VPW = 32 / S visibilities at a time,
-// one per group of S lanes; lane j of a group owns footprint column j and all
-// S rows, so its register block is one full column (S complex values).
 template <int S>
-struct GridLayout {
-    static constexpr int VPW = (32 / S) > 0 ? (32 / S) : 1;  // visibilities per step
-    static constexpr bool ALL_LANES = VPW * S == 32;
-};
-
-// Loads the S v-taps of a row (16-byte loads when S is even).
-template <int S>
-__device__ __forceinline__ void load_row(const float2 *__restrict__ row, float (&tr)[S],
-                                         float (&ti)[S])
-{
-    const float4 *r4 = reinterpret_cast<const float4 *>(row);
-#pragma unroll
-    for (int q = 0; q < S / 2; ++q) {
-        const float4 t = __ldg(r4 + q);
-        tr[2 * q] = t.x;
-        ti[2 * q] = t.y;
-        tr[2 * q + 1] = t.z;
-        ti[2 * q + 1] = t.w;
-    }
-}
-
-template <int S>
-__global__ void __launch_bounds__(kTiledThreads, kGridBlocksPerSM) grid_tiled_kernel(
+__global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_kernel(
     DevParams p, const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems,
     int32_t *counter, const uint64_t *__restrict__ rec, const int32_t *__restrict__ perm,
     const float2 *__restrict__ vis, const float *__restrict__ weight,
     const float2 *__restrict__ taps, float2 *grid)
 {
-    constexpr int VPW = GridLayout<S>::VPW;
+    constexpr int RG = Layout<S>::RG, RPL = Layout<S>::RPL;
     __shared__ int4 s_meta[kTiledWarps * 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int4 *meta = s_meta + warp * 32;
-    const int g = lane / S, j = lane % S;  // visibility slot of the step, column
-    const bool lane_ok = GridLayout<S>::ALL_LANES || g < VPW;
+    const int rg = lane / S, j = lane % S;
+    const bool lane_ok = Layout<S>::ALL_LANES || rg < RG;
     const int n_items = *nitems;
 
     // every warp takes whole work items on its own: no block-wide barrier
@@ -144,24 +117,25 @@ __global__ void __launch_bounds__(kTiledThreads, kGridBlocksPerSM) grid_tiled_ke
         float2 *const tgrid = grid + o.base + o.gy0 * p.N + o.gx0;
         const int b0 = it.start, b1 = it.start + it.count;
 
-        float ar[S], ai[S];
+        float ar[RPL], ai[RPL];
 #pragma unroll
-        for (int q = 0; q < S; ++q)
+        for (int q = 0; q < RPL; ++q)
             ar[q] = ai[q] = 0.f;
         int cur = -1;
 
-        // adds this lane's column of the register block of key `cur` to the
-        // grid (float2 atomics, native L2 reductions) and clears it
+        // adds the register block of key `cur` to the grid (float2 atomics,
+        // native L2 reductions) and clears it
         auto flush = [&]() {
-            if (cur >= 0) {
+            if (cur >= 0 && lane_ok) {
                 const float sg = (cur & 1) ? -1.f : 1.f;
-                float2 *gp = tgrid + (int64_t)key_ly(cur) * p.N + key_lx(cur) + j;
+                float2 *g = tgrid + (int64_t)(key_ly(cur) + rg * RPL) * p.N + key_lx(cur) + j;
 #pragma unroll
-                for (int q = 0; q < S; ++q)
-                    atomicAdd(gp + (int64_t)q * p.N, make_float2(ar[q], sg * ai[q]));
+                for (int q = 0; q < RPL; ++q)
+                    if (Layout<S>::FULL_ROWS || rg * RPL + q < S)
+                        atomicAdd(g + (int64_t)q * p.N, make_float2(ar[q], sg * ai[q]));
             }
 #pragma unroll
-            for (int q = 0; q < S; ++q)
+            for (int q = 0; q < RPL; ++q)
                 ar[q] = ai[q] = 0.f;
         };
 
@@ -182,24 +156,23 @@ __global__ void __launch_bounds__(kTiledThreads, kGridBlocksPerSM) grid_tiled_ke
             }
             __syncwarp();
             const int n = min(32, b1 - base);
-            for (int q0 = 0; q0 < n; q0 += VPW) {
-                const int q = q0 + g;
-                if (lane_ok && q < n) {
-                    const int4 m = meta[q];
-                    const int key = meta_key(m.y);
-                    if (key != cur) {
-                        flush();
-                        cur = key;
-                    }
+            for (int q = 0; q < n; ++q) {
+                const int4 m = meta[q];
+                const int key = meta_key(m.y);
+                if (key != cur) {
+                    flush();
+                    cur = key;
+                }
+                if (lane_ok) {
                     const float wx = __int_as_float(m.z), wy = __int_as_float(m.w);
                     const float2 *tu = taps + m.x;
                     const float2 a = __ldg(tu + j);
                     const float pr = wx * a.x - wy * a.y;
                     const float pi = wx * a.y + wy * a.x;
-                    float tr[S], ti[S];
-                    load_row<S>(tu + meta_dv(m.y), tr, ti);
+                    float tr[RPL], ti[RPL];
+                    load_vtaps<S>(tu + meta_dv(m.y), rg, tr, ti);
 #pragma unroll
-                    for (int k = 0; k < S; ++k) {
+                    for (int k = 0; k < RPL; ++k) {
                         ar[k] = fmaf(pr, tr[k], ar[k]);
                         ar[k] = fmaf(-pi, ti[k], ar[k]);
                         ai[k] = fmaf(pr, ti[k], ai[k]);
@@ -209,8 +182,7 @@ __global__ void __launch_bounds__(kTiledThreads, kGridBlocksPerSM) grid_tiled_ke
             }
             __syncwarp();
         }
-        if (lane_ok)
-            flush();
+        flush();
     }
 }
 
@@ -401,7 +373,7 @@ static cudaError_t launch_grid_S(const DevParams &p, const Plan &plan, const flo
     cudaError_t e = cudaMemsetAsync(plan.d_item_counter, 0, sizeof(int32_t), s);
     if (e != cudaSuccess)
         return e;
-    grid_tiled_kernel<S><<<num_sms * kGridBlocksPerSM, kTiledThreads, 0, s>>>(
+    grid_tiled_kernel<S><<<num_sms * kTiledBlocksPerSM, kTiledThreads, 0, s>>>(
         p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm, vis,
         weight, taps, grid);
     return cudaGetLastError();
