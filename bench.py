@@ -465,8 +465,10 @@ def run_ours(args):
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
-    dom, dom_ms = ("grid_tiled_kernel", grid_ms) if grid_ms >= degrid_ms else \
-        ("degrid_tiled_kernel", degrid_ms)
+    # the tiled form's register-block kernels cover these supports
+    gk = "grid_tiled_block_kernel" if Ssup in (8, 12, 16) else "grid_tiled_kernel"
+    dk = "degrid_tiled_block_kernel" if Ssup in (4, 8, 12, 16) else "degrid_tiled_kernel"
+    dom, dom_ms = (gk, grid_ms) if grid_ms >= degrid_ms else (dk, degrid_ms)
     achieved = flops_per_vis * nkept / (dom_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak,

@@ -1,34 +1,42 @@
 // Tiled FP32 gridder and degridder (the separable update of Sec. 5, binned).
 //
 // Work items are <= kChunk visibilities of one T x T tile, sorted by
-// (footprint origin, conj), taken from an atomic counter: by a whole warp in
-// the gridder, by a whole CTA in the degridder.  The degridder keeps the
-// tile's window of (T + S - 1)^2 cells in shared memory (separate re / im
-// planes; row stride chosen so the row groups of a warp hit disjoint banks).
+// (footprint origin, conj) ("key"), taken from an atomic counter: by a whole
+// warp in the gridder, by a whole CTA in the degridder, which keeps the
+// tile's window of (T + S - 1)^2 cells in shared memory.  Per batch of
+// visibilities a warp first decodes the records once (one per lane: tap-row
+// offsets, W V or the output index and weight, key) into shared memory; the
+// inner loop reads them as broadcasts.
 //
-// Lane (rg, j) of a warp owns footprint column j and rows rg*RPL ..
-// rg*RPL + RPL - 1.  Each warp walks a contiguous slice of the item.  Per
-// block of 32 visibilities the warp first decodes the records once (one per
-// lane: origin/conj key, tap-row offsets, W V) into one 16-byte shared-memory
-// record each; the inner loop then reads them as broadcasts and loads the
-// v-taps of its rows with 128-bit loads.
+// What limits these kernels is the load data returned to the registers and
+// the instruction issue, not the FMA pipe: every lane loads the taps of the
+// cells it owns for every visibility.  Larger per-lane register blocks load
+// fewer taps per cell, so the forms below use, by support:
+//   * gridding, S = 8, 12, 16: lane (rg, cg) = (lane >> 3, lane & 7) owns
+//     rows rg + 4 r and columns cg + 8 c (S / 4 + S / 8 taps per lane per
+//     visibility);
+//   * degridding, S = 4 .. 16, S % 4 = 0: two virtual warps of 16 lanes take
+//     two visibilities per step; lane (rg, cg) = (t >> 2, t & 3) owns rows
+//     rg + 4 r and columns cg + 4 c (2 S / 4 taps per lane per visibility);
+//   * other supports: lane (rg, j) owns footprint column j and S / RG rows.
+// The interleaved cell assignment makes the lanes of one atomic or window
+// read cover a compact patch (few sectors per atomic, no bank conflicts).
 //
 // Gridding: per visibility the lane forms the partial product W V F1(u - u_i)
-// for its column once (Sec. 5: reused down every row) and accumulates RPL
-// complex products with the v-taps into a register block.  A block of
-// visibilities with one key shares the register block; for conj visibilities
-// it accumulates conj(W V) F1 F1 and is conjugated when it is flushed, so the
-// inner loop needs no sign handling.  The register block is added to the HBM
-// grid with float2 atomics (native L2 reductions) when the key changes.  (A
+// for its columns once (Sec. 5: reused down every row) and accumulates its
+// cells' products with the v-taps into a register block.  Visibilities with
+// one key share the register block; conj visibilities accumulate
+// conj(W V) F1 F1 and the block is conjugated when it is flushed, so the
+// inner loop needs no sign handling.  The block is added to the HBM grid with
+// float2 atomics (native L2 reductions) when the key changes.  (A
 // shared-memory window in between was slower: float adds to shared memory
 // run as compare-and-swap loops, several instructions per add.)
 //
-// Degridding (the adjoint): the window is loaded from HBM; the lane keeps its
-// RPL window values (conjugated for plain-kernel groups) in registers while
-// the key is unchanged, forms sum_k F1_v(k) X'(k) and multiplies by F1_u(j).
-// Eight visibilities are reduced over the 32 lanes together (reduce-scatter:
-// 9 shuffles per component instead of 40), then conjugated back as needed and
-// scaled by W.
+// Degridding (the adjoint): the lane keeps its window cells (conjugated for
+// plain-kernel groups) in registers while the key is unchanged, forms
+// sum_r F1_v(r) X(r, c) per column and then the sum over its columns with
+// F1_u(c); the partial sums of several visibilities are reduced over the
+// lanes together (reduce-scatter), conjugated back as needed and scaled by W.
 #include "sepw_internal.cuh"
 
 namespace sepw {
@@ -336,6 +344,348 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) degrid_tiled
     }
 }
 
+// ---------------------------------------------------------------------------
+// Degridding with 4 x 4 lane grids of B x B register blocks (S = 4 B).
+//
+// A warp is two virtual warps of 16 lanes, each with its own contiguous
+// slice of the item, so two visibilities are updated per warp step.  Lane
+// (rg, cg) = (t >> 2, t & 3) of a virtual warp owns the cells at footprint
+// rows rg + 4 r and columns cg + 4 c (r, c < B): per visibility B u-taps and
+// B v-taps.  Its 16 lanes read a 4 x 4 patch of the window at a time, which
+// with a row stride of 4 (mod 8) float2 hits every bank once.
+// ---------------------------------------------------------------------------
+template <int S>
+struct Blk {
+    static constexpr bool OK = S % 4 == 0 && S >= 4 && S <= 16;
+    static constexpr int B = S / 4;  // cells per lane along each axis
+    static constexpr int K = 16;     // visibilities staged per virtual warp
+    static constexpr int MS = K + 1; // staging stride (virtual warps on other banks)
+    static constexpr int BPS = S == 16 ? 3 : 4;  // resident CTAs per SM (registers)
+};
+
+// Loads the B taps k0, k0 + 4, ... of one table row.
+template <int B>
+__device__ __forceinline__ void load_taps4(const float2 *__restrict__ row, int k0,
+                                           float (&re)[B], float (&im)[B])
+{
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+        const float2 t = __ldg(row + k0 + 4 * c);
+        re[c] = t.x;
+        im[c] = t.y;
+    }
+}
+
+
+// Sum of v[e] over the 16 lanes of a virtual warp for e = 0..7 (re of four
+// visibilities, then im); on return v[0] holds the sum for component
+// (t >> 3) of visibility (t >> 1) & 3, identical on lanes t and t ^ 1.
+__device__ __forceinline__ void reduce16x8(float (&v)[8], int t)
+{
+    const bool b3 = t & 8, b2 = t & 4, b1 = t & 2;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = b3 ? v[i] : v[i + 4];
+        const float keep = b3 ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b2 ? v[i] : v[i + 2];
+        const float keep = b2 ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const float send = b1 ? v[0] : v[1];
+        const float keep = b1 ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+template <int S>
+__global__ void __launch_bounds__(kTiledThreads, Blk<S>::BPS) degrid_tiled_block_kernel(
+    DevParams p, int WP, const WorkItem *__restrict__ items,
+    const int32_t *__restrict__ nitems, int32_t *counter, const uint64_t *__restrict__ rec,
+    const int32_t *__restrict__ perm, const float2 *__restrict__ grid,
+    const float *__restrict__ weight, const float2 *__restrict__ taps,
+    float2 *__restrict__ vis_out)
+{
+    constexpr int B = Blk<S>::B, K = Blk<S>::K, MS = Blk<S>::MS;
+    extern __shared__ float4 smem4[];
+    __shared__ int s_item;
+    const int W = p.T + S - 1;
+    float2 *const win = reinterpret_cast<float2 *>(smem4);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int vw = lane >> 4, t = lane & 15, rg = t >> 2, cg = t & 3;
+    int4 *const meta = reinterpret_cast<int4 *>(smem4 + ((W * WP + 1) / 2)) + (warp * 2 + vw) * MS;
+    int *const keys = reinterpret_cast<int *>(meta - (warp * 2 + vw) * MS + kTiledWarps * 2 * MS) +
+                      (warp * 2 + vw) * MS;
+    const float2 *const tcol = taps + cg;
+    const float2 *const trow = taps + rg;
+    const int n_items = *nitems;
+    // this lane's first window cell relative to the footprint origin
+    const float2 *const lwin = win + rg * WP + cg;
+
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0)
+            s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items)
+            break;
+        const WorkItem it = items[item];
+        const TileOrigin o = tile_origin(p, it.tile);
+        for (int rr = warp; rr < W; rr += kTiledWarps) {
+            const int64_t gy = o.gy0 + rr;
+            const float2 *grow = grid + o.base + gy * p.N + o.gx0;
+            for (int cc = lane; cc < W; cc += 32) {
+                float2 g = make_float2(0.f, 0.f);
+                if (gy < p.N && o.gx0 + cc < p.N)
+                    g = __ldg(grow + cc);
+                win[rr * WP + cc] = g;
+            }
+        }
+        __syncthreads();
+        // 16 workers (two per warp) take contiguous slices of the item
+        const int per = (it.count + 2 * kTiledWarps - 1) / (2 * kTiledWarps);
+        const int wk = warp * 2 + vw;
+        const int v0 = it.start + min(it.count, wk * per);
+        const int v1 = it.start + min(it.count, (wk + 1) * per);
+
+        float xr[B][B], xi[B][B];
+        int cur = -1;
+        // both virtual warps run the same number of steps (warp shuffles)
+        for (int base = 0; base < per; base += K) {
+            const int s = v0 + base + t;
+            if (s < v1) {
+                const uint64_t r = rec[s];
+                const int i = perm[s];
+                const int row = rec_plane(r) * p.OS;
+                meta[t] = make_int4((row + rec_ou(r)) * S, (row + rec_ov(r)) * S, i,
+                                    __float_as_int(weight ? __ldg(weight + i) : 1.0f));
+                keys[t] = ((rec_ly(r) * 64 + rec_lx(r)) << 1) | (rec_conj(r) ? 1 : 0);
+            }
+            __syncwarp();
+            const int n = min(K, v1 - (v0 + base));  // may be <= 0
+            const int nw = max(n, __shfl_xor_sync(0xffffffffu, n, 16));
+            for (int qb = 0; qb < nw; qb += 4) {
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    v[e] = v[e + 4] = 0.f;
+                    if (qb + e < n) {
+                        const int key = keys[qb + e];
+                        if (key != cur) {
+                            cur = key;
+                            // plain-kernel groups work on conj(X)
+                            const float sg = (cur & 1) ? 1.f : -1.f;
+                            const float2 *wl = lwin + key_ly(cur) * WP + key_lx(cur);
+#pragma unroll
+                            for (int r = 0; r < B; ++r)
+#pragma unroll
+                                for (int c = 0; c < B; ++c) {
+                                    const float2 x = wl[4 * r * WP + 4 * c];
+                                    xr[r][c] = x.x;
+                                    xi[r][c] = sg * x.y;
+                                }
+                        }
+                        const int4 m = meta[qb + e];
+                        float ur[B], ui[B], vr[B], vi[B];
+                        load_taps4<B>(tcol + m.x, 0, ur, ui);
+                        load_taps4<B>(trow + m.y, 0, vr, vi);
+                        float sr = 0.f, si = 0.f;
+#pragma unroll
+                        for (int c = 0; c < B; ++c) {
+                            float tr = 0.f, ti = 0.f;  // sum_r F1_v(r) X(r, c)
+#pragma unroll
+                            for (int r = 0; r < B; ++r) {
+                                tr = fmaf(vr[r], xr[r][c], tr);
+                                tr = fmaf(-vi[r], xi[r][c], tr);
+                                ti = fmaf(vr[r], xi[r][c], ti);
+                                ti = fmaf(vi[r], xr[r][c], ti);
+                            }
+                            sr = fmaf(tr, ur[c], sr);
+                            sr = fmaf(-ti, ui[c], sr);
+                            si = fmaf(tr, ui[c], si);
+                            si = fmaf(ti, ur[c], si);
+                        }
+                        v[e] = sr;
+                        v[e + 4] = si;
+                    }
+                }
+                reduce16x8(v, t);
+                // lanes t < 8 with even t hold re of visibility (t >> 1);
+                // lane t + 8 holds its im
+                const float im = __shfl_down_sync(0xffffffffu, v[0], 8);
+                const int e = t >> 1;
+                if (t < 8 && (t & 1) == 0 && qb + e < n) {
+                    const int4 m = meta[qb + e];
+                    const float wt = __int_as_float(m.w);
+                    // plain-kernel groups computed conj(V / W)
+                    const float vi_ = (keys[qb + e] & 1) ? im : -im;
+                    vis_out[m.z] = make_float2(wt * v[0], wt * vi_);
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gridding with a 4 x 8 lane grid, S = 8, 12, 16.  Lane (rg, cg) =
+// (lane >> 3, lane & 7) owns the cells at footprint rows rg + 4 r
+// (r < S / 4) and columns cg + 8 c (c < ceil(S / 8), column < S).  The inner
+// loop runs over runs of equal keys found with one ballot per batch, so the
+// flush and its branch sit outside it.
+// ---------------------------------------------------------------------------
+template <int S>
+struct Blk2 {
+    static constexpr bool OK = S == 8 || S == 12 || S == 16;
+    static constexpr int RB = S / 4;        // rows per lane
+    static constexpr int CB = (S + 7) / 8;  // columns per lane
+    static constexpr bool FULL = S % 8 == 0;
+};
+
+template <int S>
+__global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_block_kernel(
+    DevParams p, const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems,
+    int32_t *counter, const uint64_t *__restrict__ rec, const int32_t *__restrict__ perm,
+    const float2 *__restrict__ vis, const float *__restrict__ weight,
+    const float2 *__restrict__ taps, float2 *grid)
+{
+    constexpr int RB = Blk2<S>::RB, CB = Blk2<S>::CB;
+    constexpr bool FULL = Blk2<S>::FULL;
+    __shared__ int4 s_meta[kTiledWarps * 32];
+    __shared__ int s_key[kTiledWarps * 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rg = lane >> 3, cg = lane & 7;
+    int4 *const meta = s_meta + warp * 32;
+    int *const keys = s_key + warp * 32;
+    // this lane's u-tap column and v-tap row within a table row
+    const float2 *const tcol = taps + cg;
+    const float2 *const trow = taps + rg;
+    const int n_items = *nitems;
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0)
+            item = atomicAdd(counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items)
+            break;
+        const WorkItem it = items[item];
+        const TileOrigin o = tile_origin(p, it.tile);
+        float2 *const tgrid = grid + o.base + (o.gy0 + rg) * p.N + o.gx0 + cg;
+        const int b0 = it.start, b1 = it.start + it.count;
+
+        float2 acc[RB][CB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+#pragma unroll
+            for (int c = 0; c < CB; ++c)
+                acc[r][c] = make_float2(0.f, 0.f);
+        int cur = -1;
+
+        // adds the register block of key `cur` to the grid and clears it;
+        // conj groups accumulated conj(W V) F1 F1 and are conjugated here
+        auto flush = [&]() {
+            if (cur >= 0) {
+                if (cur & 1) {
+#pragma unroll
+                    for (int r = 0; r < RB; ++r)
+#pragma unroll
+                        for (int c = 0; c < CB; ++c)
+                            acc[r][c].y = -acc[r][c].y;
+                }
+                float2 *g = tgrid + key_ly(cur) * p.N + key_lx(cur);
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+#pragma unroll
+                    for (int c = 0; c < CB; ++c)
+                        if (FULL || cg + 8 * c < S)
+                            atomicAdd(g + 8 * c, acc[r][c]);
+                    g += 4 * p.N;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+#pragma unroll
+                for (int c = 0; c < CB; ++c)
+                    acc[r][c] = make_float2(0.f, 0.f);
+        };
+
+        for (int base = b0; base < b1; base += 32) {
+            // lane q stages slot base + q: tap-row offsets, W V, key
+            const int s = base + lane;
+            int kq = -1;
+            if (s < b1) {
+                const uint64_t r = rec[s];
+                const int i = perm[s];
+                const float wt = weight ? __ldg(weight + i) : 1.0f;
+                const float2 x = __ldg(vis + i);
+                const bool cj = rec_conj(r);
+                const int row = rec_plane(r) * p.OS;
+                kq = ((rec_ly(r) * 64 + rec_lx(r)) << 1) | (cj ? 1 : 0);
+                meta[lane] = make_int4((row + rec_ou(r)) * S, (row + rec_ov(r)) * S,
+                                       __float_as_int(wt * x.x),
+                                       __float_as_int(cj ? -wt * x.y : wt * x.y));
+                keys[lane] = kq;
+            }
+            __syncwarp();
+            const int n = min(32, b1 - base);
+            // runs of equal keys in this batch: bit q set where slot q starts one
+            const int kp = __shfl_up_sync(0xffffffffu, kq, 1);
+            const unsigned starts = __ballot_sync(0xffffffffu, lane < n && (lane == 0 || kq != kp));
+            for (int q = 0; q < n;) {
+                const unsigned later = starts & ~((2u << q) - 1u);
+                const int q1 = later ? __ffs(later) - 1 : n;
+                const int key = keys[q];
+                if (key != cur) {
+                    flush();
+                    cur = key;
+                }
+                for (; q < q1; ++q) {
+                    const int4 m = meta[q];
+                    const float wx = __int_as_float(m.z), wy = __int_as_float(m.w);
+                    const float2 *tu = tcol + m.x;
+                    const float2 *tv = trow + m.y;
+                    float pr[CB], pi[CB], vr[RB], vi[RB];
+#pragma unroll
+                    for (int c = 0; c < CB; ++c) {
+                        float2 a = make_float2(0.f, 0.f);
+                        if (FULL || cg + 8 * c < S)
+                            a = __ldg(tu + 8 * c);
+                        // partial product W V F1(u), Sec. 5
+                        pr[c] = wx * a.x - wy * a.y;
+                        pi[c] = wx * a.y + wy * a.x;
+                    }
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) {
+                        const float2 b = __ldg(tv + 4 * r);
+                        vr[r] = b.x;
+                        vi[r] = b.y;
+                    }
+#pragma unroll
+                    for (int r = 0; r < RB; ++r)
+#pragma unroll
+                        for (int c = 0; c < CB; ++c) {
+                            float2 &a = acc[r][c];
+                            a.x = fmaf(pr[c], vr[r], a.x);
+                            a.x = fmaf(-pi[c], vi[r], a.x);
+                            a.y = fmaf(pr[c], vi[r], a.y);
+                            a.y = fmaf(pi[c], vr[r], a.y);
+                        }
+                }
+            }
+            __syncwarp();
+        }
+        flush();
+    }
+}
+
+
 // Row stride of the shared window: the smallest WP >= W for which the row
 // groups of a warp touch disjoint banks.
 static int window_stride(int W, int S)
@@ -373,9 +723,14 @@ static cudaError_t launch_grid_S(const DevParams &p, const Plan &plan, const flo
     cudaError_t e = cudaMemsetAsync(plan.d_item_counter, 0, sizeof(int32_t), s);
     if (e != cudaSuccess)
         return e;
-    grid_tiled_kernel<S><<<num_sms * kTiledBlocksPerSM, kTiledThreads, 0, s>>>(
-        p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm, vis,
-        weight, taps, grid);
+    if constexpr (Blk2<S>::OK)
+        grid_tiled_block_kernel<S><<<num_sms * kTiledBlocksPerSM, kTiledThreads, 0, s>>>(
+            p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm, vis,
+            weight, taps, grid);
+    else
+        grid_tiled_kernel<S><<<num_sms * kTiledBlocksPerSM, kTiledThreads, 0, s>>>(
+            p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm, vis,
+            weight, taps, grid);
     return cudaGetLastError();
 }
 
@@ -386,14 +741,25 @@ static cudaError_t launch_degrid_S(const DevParams &p, const Plan &plan,
                                    cudaStream_t s)
 {
     const int W = p.T + S - 1;
-    const int WP = window_stride(W, S);
-    const size_t shm = tiled_smem(W, WP);
     cudaError_t e = cudaMemsetAsync(plan.d_item_counter + 1, 0, sizeof(int32_t), s);
     if (e != cudaSuccess)
         return e;
-    degrid_tiled_kernel<S><<<num_sms * kTiledBlocksPerSM, kTiledThreads, shm, s>>>(
-        p, WP, plan.d_items, plan.d_nitems, plan.d_item_counter + 1, plan.d_rec,
-        plan.d_perm, grid, weight, taps, vis);
+    if constexpr (Blk<S>::OK) {
+        // float2 window rows with stride = 4 (mod 8): the 4 x 4 patch read by a
+        // virtual warp covers all 32 banks
+        const int WP = W + ((4 - W % 8) + 8) % 8;
+        const size_t shm = sizeof(float4) * (size_t)((W * WP + 1) / 2) +
+                           (size_t)kTiledWarps * 2 * Blk<S>::MS * (sizeof(int4) + sizeof(int));
+        degrid_tiled_block_kernel<S><<<num_sms * Blk<S>::BPS, kTiledThreads, shm, s>>>(
+            p, WP, plan.d_items, plan.d_nitems, plan.d_item_counter + 1, plan.d_rec,
+            plan.d_perm, grid, weight, taps, vis);
+    } else {
+        const int WP = window_stride(W, S);
+        const size_t shm = tiled_smem(W, WP);
+        degrid_tiled_kernel<S><<<num_sms * kTiledBlocksPerSM, kTiledThreads, shm, s>>>(
+            p, WP, plan.d_items, plan.d_nitems, plan.d_item_counter + 1, plan.d_rec,
+            plan.d_perm, grid, weight, taps, vis);
+    }
     return cudaGetLastError();
 }
 

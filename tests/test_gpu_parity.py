@@ -62,6 +62,11 @@ CASES = {
     "rand_S16": lambda: synth.random_case(3, 8000, 256, 16, 16, 33, edge_fraction=0.1),
     "rand_S16_P1": lambda: synth.random_case(4, 3000, 96, 16, 4, 1, edge_fraction=0.1),
     "rand_S2_OS1": lambda: synth.random_case(5, 3000, 64, 2, 1, 3, edge_fraction=0.1),
+    # supports 4, 8, 12, 16 take the register-block kernels, the others the
+    # column-per-lane kernels
+    "rand_S4": lambda: synth.random_case(6, 3000, 64, 4, 8, 5, edge_fraction=0.1),
+    "rand_S10": lambda: synth.random_case(7, 4000, 128, 10, 8, 9, edge_fraction=0.1),
+    "rand_S20": lambda: synth.random_case(8, 4000, 192, 20, 8, 9, edge_fraction=0.1),
 }
 
 
