@@ -268,7 +268,8 @@ def run_batched(S, torch, args):
            "autotune": tuned}
     tuned_tile = tuned["tile"] if tuned["form"] == "tiled" else 0
     for name, form, tile in (("tiled_fp32", S.FORM_TILED, tuned_tile),
-                             ("tc_fp16", S.FORM_TC_FP16, 0)):
+                             ("tc_fp16", S.FORM_TC_FP16, 0),
+                             ("tc_fp16x2", S.FORM_TC_FP16X2, 0)):
         ctx = S.sepw_create(S.make_params(**wl.params(), tile=tile, form=form))
         taps = S.sepw_make_taps(ctx)
         torch.cuda.synchronize()
@@ -301,6 +302,7 @@ def run_batched(S, torch, args):
                                     "unit": "gridded vis/s", "launches_per_pass": ng}
     out["speedup_tiled_graph_vs_plain"] = pms / out["tiled_fp32"]["graph_grid_ms"]
     out["speedup_tc_fp16_graph_vs_plain"] = pms / out["tc_fp16"]["graph_grid_ms"]
+    out["speedup_tc_fp16x2_graph_vs_plain"] = pms / out["tc_fp16x2"]["graph_grid_ms"]
     ctxp.close()
     del grids, dev
     torch.cuda.empty_cache()
@@ -386,13 +388,16 @@ def run_ours(args):
     # ---- tensor-core contraction forms (grid on tcgen05, degrid tiled FP32) ----
     peaks, peak_src = _peaks()
     if not args.skip_tc:
-        for name, form in (("tc_bf16", S.FORM_TC_BF16), ("tc_fp16", S.FORM_TC_FP16)):
+        for name, form, nprod in (("tc_bf16", S.FORM_TC_BF16, 1),
+                                  ("tc_fp16", S.FORM_TC_FP16, 1),
+                                  ("tc_fp16x2", S.FORM_TC_FP16X2, 3)):
             c2 = S.sepw_create(S.make_params(**wl.params(), form=form))
             fms, fp, fg, fd = _time_form(S, torch, c2, taps, dev, grid, out,
                                          max(3, args.steps // 2), 2, stream)
             # executed dense MMA flops: one M128 x N64 x K16 MMA per 8 visibilities
-            # of a stage, K = 2 real components per visibility
-            mma_flops = 2 * 128 * 64 * 2 * nkept
+            # of a stage (three for the hi + lo form), K = 2 real components per
+            # visibility
+            mma_flops = 2 * 128 * 64 * 2 * nkept * nprod
             forms[name] = {"value": 2.0 * nvis * ws / (fms * 1e-3), "unit": "vis/s",
                            "ms_per_step": fms,
                            "phases_ms": {"plan": fp, "grid": fg, "degrid": fd},
@@ -402,8 +407,9 @@ def run_ours(args):
                                "peak": float(peaks["bf16_tflops"]),
                                "frac": mma_flops / (fg * 1e-3) / 1e12 /
                                float(peaks["bf16_tflops"]),
-                               "note": "dense MMA flops executed (2 x 128 x 64 x 2 per vis) "
-                                       "over the grid kernel; burst bf16 peak (fp16 same)"}}
+                               "note": "dense MMA flops executed (2 x 128 x 64 x 2 per vis "
+                                       "per product) over the grid kernel; burst bf16 peak "
+                                       "(fp16 same)"}}
             c2.close()
 
     # ---- plain FP32 form on the same data (the comparator) ----
@@ -420,7 +426,8 @@ def run_ours(args):
     if rank == 0 and not args.skip_errors:
         fm = {"tiled_fp32": S.FORM_TILED, "plain_fp32": S.FORM_PLAIN}
         if not args.skip_tc:
-            fm.update(tc_bf16=S.FORM_TC_BF16, tc_fp16=S.FORM_TC_FP16)
+            fm.update(tc_bf16=S.FORM_TC_BF16, tc_fp16=S.FORM_TC_FP16,
+                      tc_fp16x2=S.FORM_TC_FP16X2)
         errs, nsub = _form_errors(S, torch, wl, fm)
         for k, e in errs.items():
             if k in forms:
@@ -466,7 +473,7 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     # the tiled form's register-block kernels cover these supports
-    gk = "grid_tiled_block_kernel" if Ssup in (8, 12, 16) else "grid_tiled_kernel"
+    gk = "grid_tiled_block_kernel" if Ssup in (8, 16) else "grid_tiled_kernel"
     dk = "degrid_tiled_block_kernel" if Ssup in (4, 8, 12, 16) else "degrid_tiled_kernel"
     dom, dom_ms = (gk, grid_ms) if grid_ms >= degrid_ms else (dk, degrid_ms)
     achieved = flops_per_vis * nkept / (dom_ms * 1e-3) / 1e12

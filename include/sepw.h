@@ -70,7 +70,11 @@ extern "C" {
 #define SEPW_FORM_TC_BF16 2 /* tile contraction on tensor cores (tcgen05): BF16
                                operands, FP32 accumulation; support <= 16.
                                Degridding uses the tiled FP32 form. */
-#define SEPW_FORM_TC_FP16 3 /* as SEPW_FORM_TC_BF16 with FP16 operands */
+#define SEPW_FORM_TC_FP16 3 /* as SEPW_FORM_TC_BF16 with FP16 operands, scaled per
+                               work item by a power of two (FP16 range) */
+#define SEPW_FORM_TC_FP16X2 4 /* as SEPW_FORM_TC_FP16 with each operand split into
+                                 FP16 hi + lo and three products per step:
+                                 FP32-class accuracy */
 
 /* image directions (sepw_image) */
 #define SEPW_GRID_TO_IMAGE 0

@@ -52,7 +52,15 @@ int cuda_fail(sepw_ctx *ctx, cudaError_t e, const char *where)
             return cuda_fail((ctx), e_, #call);               \
     } while (0)
 
-bool is_tc_form(int form) { return form == SEPW_FORM_TC_BF16 || form == SEPW_FORM_TC_FP16; }
+bool is_tc_form(int form)
+{
+    return form == SEPW_FORM_TC_BF16 || form == SEPW_FORM_TC_FP16 || form == SEPW_FORM_TC_FP16X2;
+}
+
+int tc_prec(int form)
+{
+    return form == SEPW_FORM_TC_BF16 ? 0 : form == SEPW_FORM_TC_FP16 ? 1 : 2;
+}
 
 int effective_tile(const sepw_params *p)
 {
@@ -467,7 +475,7 @@ int sepw_grid_planned(sepw_ctx *ctx, const float *taps, const float *vis,
             return fail(ctx, SEPW_EINVAL, "taps must be 16-byte aligned");
         SEPW_CUDA(ctx, launch_grid_tc(ctx->dp, pl, (const float2 *)vis, weight,
                                       (const float2 *)taps, (float2 *)grid, ctx->num_sms,
-                                      pl.form == SEPW_FORM_TC_FP16, ctx->d_status, s));
+                                      tc_prec(pl.form), ctx->d_status, s));
     } else {
         if (((uintptr_t)taps) & 15)
             return fail(ctx, SEPW_EINVAL, "taps must be 16-byte aligned");

@@ -256,9 +256,10 @@ cudaError_t launch_degrid_tiled(const DevParams &p, const Plan &plan,
 
 // sepw_tc.cu
 int tc_tile_for_support(int S);
+// prec: 0 = BF16, 1 = FP16, 2 = FP16 hi + lo (three products)
 cudaError_t launch_grid_tc(const DevParams &p, const Plan &plan, const float2 *vis,
                            const float *weight, const float2 *taps, float2 *grid,
-                           int num_sms, bool fp16, int32_t *status, cudaStream_t s);
+                           int num_sms, int prec, int32_t *status, cudaStream_t s);
 
 // sepw_image.cu
 cudaError_t launch_image_pre(const DevParams &p, int direction, const float *taper,

@@ -14,18 +14,27 @@
 // which is one tcgen05.mma shape M = 128, N = 64 per K = 16 (8 visibilities).
 // The window is 64 x 64 (tile edge T with T + S - 1 <= 64).
 //
-// Operands: BF16 or FP16 (taps, and W V times the taps), FP32 accumulation in
-// tensor memory.  They are built in shared memory in the no-swizzle K-major
-// canonical layout (8-row x 16-byte core matrices; K-adjacent cores 128 bytes
-// apart, 8-row groups 2048 bytes apart).  Only the non-zero entries of a
-// stage are written, and cleared again once the tensor core has consumed the
-// stage, so the buffers stay zero elsewhere: each of the 512 producer threads
-// owns one (visibility, tap pair) unit of every stage, reads its visibility's
-// record itself, and clears its entries of a buffer when the buffer comes
-// round again.  Two stages of 64 visibilities are in flight.  Producer warps
-// arrive on the stage's "full" mbarrier; a separate warp waits on it, issues
-// the MMAs and commits them to the stage's "empty" mbarrier, so no CTA-wide
-// barrier is needed inside a work item.
+// Operand precisions (FP32 accumulation in tensor memory throughout):
+//   * BF16: one product per K step;
+//   * FP16: one product, with a power-of-two scale 2^-a per work item on B
+//     so that the largest |W V| of the item is below 1 (FP16's range), and
+//     2^a applied to the accumulator when it is read back;
+//   * FP16 hi + lo: each operand x is split into hi = fp16(x) and
+//     lo = fp16(x - hi) (22 significant bits together) and the tile update
+//     takes the three products hi*hi + hi*lo + lo*hi, scaled as for FP16.
+//     The dropped lo*lo term and the two roundings leave about 2^-21 of the
+//     largest operand in each product: FP32-class accuracy.
+//
+// The operands are built in shared memory in the no-swizzle K-major canonical
+// layout.  Only the non-zero entries of a stage are written, and cleared
+// again once the tensor core has consumed the stage, so the buffers stay zero
+// elsewhere.  Eight producer threads share a visibility (taps k = q, q + 8):
+// each reads the record, loads its taps, forms its part of P and writes its
+// entries; the 32 four-byte stores of a warp instruction (four visibilities,
+// eight consecutive rows each) land in 32 distinct banks.  Producer warps arrive on the
+// stage's "full" mbarrier; a separate warp waits on it, issues the MMAs and
+// commits them to the stage's "empty" mbarrier, so no CTA-wide barrier is
+// needed inside a work item.
 //
 // After the last stage of a work item the accumulator is read back with
 // tcgen05.ld, staged in shared memory and added to the HBM grid with float2
@@ -40,17 +49,33 @@
 namespace sepw {
 namespace {
 
-constexpr int kTcThreads = 512;
-constexpr int kStageVis = 64;                 // visibilities per stage (K = 128)
-constexpr int kStages = 3;                    // stages in flight
-constexpr int kWin = 64;                      // padded window edge
-constexpr int kM = 128, kN = 64;              // MMA shape
-constexpr int kKStage = 2 * kStageVis;        // K elements per stage
-constexpr int kSBO = (kKStage / 8) * 128;     // bytes between 8-row core groups
-constexpr int kABytes = kM * kKStage * 2;     // 32 KiB
-constexpr int kBBytes = kN * kKStage * 2;     // 16 KiB
+constexpr int kProducers = 512;                 // 16 warps, 8 threads per visibility
+constexpr int kProducerWarps = kProducers / 32;
+constexpr int kTcBlock = kProducers + 32;       // + one MMA-issuing warp
+constexpr int kStageVis = kProducers / 8;       // 64 visibilities per stage
+constexpr int kWin = 64;                        // padded window edge
+constexpr int kM = 128, kN = 64;                // MMA shape
+constexpr int kKStage = 2 * kStageVis;          // K elements per stage
+constexpr int kSBO = (kKStage / 8) * 128;       // bytes between 8-row core groups
+constexpr int kABytes = kM * kKStage * 2;       // 32 KiB
+constexpr int kBBytes = kN * kKStage * 2;       // 16 KiB
 constexpr uint32_t kTmemCols = 64;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+
+// PREC: 0 = BF16, 1 = FP16, 2 = FP16 hi + lo
+template <int PREC>
+struct Prec {
+    static constexpr int TERMS = PREC == 2 ? 2 : 1;   // operand copies (hi, lo)
+    static constexpr int STAGES = PREC == 2 ? 2 : 3;  // stages in flight
+    static constexpr bool SCALED = PREC != 0;         // per-item power-of-two scale
+};
+
+template <int PREC>
+constexpr size_t tc_smem_bytes_for()
+{
+    return (size_t)Prec<PREC>::STAGES * Prec<PREC>::TERMS * (kABytes + kBBytes) +
+           sizeof(uint64_t) * (2 * Prec<PREC>::STAGES + 1);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -108,7 +133,8 @@ __device__ __forceinline__ void tc_fence_after()
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: no swizzle, K-major canonical layout.
+// Shared-memory matrix descriptor: no swizzle, K-major canonical layout
+// (K-adjacent core matrices 128 bytes apart, 8-row groups kSBO bytes apart).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
 {
     return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) |
@@ -165,95 +191,89 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  : "r"(taddr)                                                               \
                  : "memory")
 
-template <bool FP16>
-__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+// Packs (x, y) for an operand: the rounded pair, and for the split form the
+// rounded remainder.
+template <int PREC>
+__device__ __forceinline__ void split2(float x, float y, uint32_t &hi, uint32_t &lo)
 {
-    if constexpr (FP16) {
-        __half2 h = __floats2half2_rn(lo, hi);
-        return *reinterpret_cast<uint32_t *>(&h);
+    if constexpr (PREC == 0) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+        hi = *reinterpret_cast<uint32_t *>(&h);
+        lo = 0u;
     } else {
-        __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-        return *reinterpret_cast<uint32_t *>(&h);
+        __half2 h = __floats2half2_rn(x, y);
+        hi = *reinterpret_cast<uint32_t *>(&h);
+        if constexpr (PREC == 2) {
+            const float2 f = __half22float2(h);
+            __half2 l = __floats2half2_rn(x - f.x, y - f.y);
+            lo = *reinterpret_cast<uint32_t *>(&l);
+        } else {
+            lo = 0u;
+        }
     }
 }
 
-// byte offset of element pair (row, visibility ii) in a stage operand
+// (a, b) -> (a, -b) and (b, a) on packed 16-bit pairs (sign flip is exact)
+__device__ __forceinline__ uint32_t pair_conj(uint32_t v) { return v ^ 0x80000000u; }
+__device__ __forceinline__ uint32_t pair_swap(uint32_t v) { return (v >> 16) | (v << 16); }
+
+// byte offset of the element pair of visibility ii in operand row `row`
 __device__ __forceinline__ uint32_t op_off(int row, int ii)
 {
     return (uint32_t)((row >> 3) * kSBO + (ii >> 2) * 128 + (row & 7) * 16 + (ii & 3) * 4);
 }
 
-// One producer thread's unit of a stage: visibility ii = 4 * warp + (lane & 3)
-// and the taps k, k + 8 with k = lane >> 2.  The 32 four-byte stores of a
-// warp instruction land in 32 distinct banks (row & 7 differs across k,
-// ii & 3 across the lane quads).  Rows k and k + 8 are one 8-row core group
-// (kSBO bytes) apart, and the second block of A (row + 64) eight groups, so a
-// unit needs two offsets: offA = op_off(ly + k, ii), offB = op_off(lx + k, ii).
-template <int S, bool FP16>
-__device__ __forceinline__ void unit_set(unsigned char *A, unsigned char *B, uint32_t offA,
-                                         uint32_t offB, int k, const float2 *tv,
-                                         const float2 *tu, float wr, float wi, bool cj)
+// What a producer thread holds of one stage: its visibility's value and
+// weight, its taps, and the footprint origin (ly | lx << 8 | conj << 16), or
+// pos = -1 for no visibility.
+template <int NT>
+struct StageData {
+    int pos;
+    float2 x;
+    float wt;
+    float2 tv[NT], tu[NT];
+};
+
+// Byte offsets of the rows r0, r0 + 8 (visibility ii): a step of 8 rows is
+// one core group, kSBO bytes.
+template <int NT>
+__device__ __forceinline__ void row_offsets(int r0, int ii, uint32_t (&o)[NT])
 {
+    const uint32_t o0 = op_off(r0, ii);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int kk = k + 8 * h;
-        if (kk >= S)
-            continue;
-        float2 v = __ldg(tv + kk);
-        float2 u = __ldg(tu + kk);
-        if (cj) {
-            v.y = -v.y;
-            u.y = -u.y;
-        }
-        *reinterpret_cast<uint32_t *>(A + offA + h * kSBO) = pack2<FP16>(v.x, -v.y);
-        *reinterpret_cast<uint32_t *>(A + offA + (8 + h) * kSBO) = pack2<FP16>(v.y, v.x);
-        *reinterpret_cast<uint32_t *>(B + offB + h * kSBO) =
-            pack2<FP16>(wr * u.x - wi * u.y, wr * u.y + wi * u.x);
-    }
+    for (int j = 0; j < NT; ++j)
+        o[j] = o0 + j * kSBO;
 }
 
-template <int S>
-__device__ __forceinline__ void unit_clear(unsigned char *A, unsigned char *B, uint32_t offA,
-                                           uint32_t offB, int k)
-{
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        if (k + 8 * h >= S)
-            continue;
-        *reinterpret_cast<uint32_t *>(A + offA + h * kSBO) = 0u;
-        *reinterpret_cast<uint32_t *>(A + offA + (8 + h) * kSBO) = 0u;
-        *reinterpret_cast<uint32_t *>(B + offB + h * kSBO) = 0u;
-    }
-}
-
-constexpr int kProducerWarps = kTcThreads / 32;  // 16
-constexpr int kTcBlock = kTcThreads + 32;        // + one MMA-issuing warp
-
-template <int S, bool FP16>
+template <int S, int PREC>
 __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
     DevParams p, const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems,
     int32_t *counter, const uint64_t *__restrict__ rec, const int32_t *__restrict__ perm,
     const float2 *__restrict__ vis, const float *__restrict__ weight,
     const float2 *__restrict__ taps, float2 *grid, int32_t *status)
 {
+    constexpr int TERMS = Prec<PREC>::TERMS, STAGES = Prec<PREC>::STAGES;
+    constexpr int NT = (S + 7) / 8;  // taps per producer thread
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *Abuf = smem;                      // kStages x 32 KiB
-    unsigned char *Bbuf = smem + kStages * kABytes;  // kStages x 16 KiB
-    uint64_t *full = reinterpret_cast<uint64_t *>(Bbuf + kStages * kBBytes);
-    uint64_t *empty = full + kStages;
-    uint64_t *accf = empty + kStages;
+    // operand buffers: A[stage][term], then B[stage][term]
+    unsigned char *const Abuf = smem;
+    unsigned char *const Bbuf = smem + STAGES * TERMS * kABytes;
+    uint64_t *full = reinterpret_cast<uint64_t *>(Bbuf + STAGES * TERMS * kBBytes);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accf = empty + STAGES;
     __shared__ uint32_t s_tmem;
     __shared__ int s_item;
     __shared__ volatile int s_abort;
+    __shared__ float s_red[kProducerWarps];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool mma_warp = warp == kProducerWarps;
-    constexpr uint32_t idesc = instr_desc(FP16 ? 0u : 1u);
+    constexpr uint32_t idesc = instr_desc(PREC == 0 ? 1u : 0u);
 
-    for (int e = tid; e < kStages * (kABytes + kBBytes) / 16; e += kTcBlock)
+    for (int e = tid; e < STAGES * TERMS * (kABytes + kBBytes) / 16; e += kTcBlock)
         reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
-        for (int b = 0; b < kStages; ++b) {
+        for (int b = 0; b < STAGES; ++b) {
             mbar_init(full + b, kProducerWarps);
             mbar_init(empty + b, 1);
         }
@@ -275,18 +295,15 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
     const uint32_t tmem = s_tmem;
     const int n_items = *nitems;
 
-    // producer unit of this thread; operand offsets of its last two stages
-    // (0xffffffff: nothing written) for the clears
-    const int ii = 4 * warp + (lane & 3);
-    const int k = lane >> 2;
-    uint32_t oldA[kStages], oldB[kStages];
+    // producer unit: visibility ii of each stage, taps k = q + 8 j
+    const int ii = tid >> 3, q = tid & 7;
+    // footprint origin (ly | lx << 8) this thread wrote into each buffer, or -1
+    int oldpos[STAGES];
 #pragma unroll
-    for (int q = 0; q < kStages; ++q) {
-        oldA[q] = 0xffffffffu;
-        oldB[q] = 0;
-    }
+    for (int b = 0; b < STAGES; ++b)
+        oldpos[b] = -1;
 
-    int t_global = 0;  // stages of this CTA so far (buffer t % kStages)
+    int t_global = 0;  // stages of this CTA so far (buffer t % STAGES)
     int n_done = 0;    // items of this CTA so far (accf parity)
 
     for (;;) {
@@ -298,70 +315,144 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
             break;
         const WorkItem it = items[item];
         const int nst = (it.count + kStageVis - 1) / kStageVis;
+        int a_exp = 0;  // accumulator holds G * 2^-a_exp
 
         if (!mma_warp) {
-            // records of the unit's visibility, one stage ahead
-            uint64_t r_next = 0;
-            int i_next = -1;
-            if (ii < it.count) {
-                r_next = rec[it.start + ii];
-                i_next = perm[it.start + ii];
+            float scale = 1.0f;
+            if constexpr (Prec<PREC>::SCALED) {
+                // largest |W V| component of the item -> power-of-two scale
+                float m = 0.f;
+                for (int e = tid; e < it.count; e += kProducers) {
+                    const int i = perm[it.start + e];
+                    const float2 x = __ldg(vis + i);
+                    const float wt = weight ? __ldg(weight + i) : 1.0f;
+                    m = fmaxf(m, fmaxf(fabsf(wt * x.x), fabsf(wt * x.y)));
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0)
+                    s_red[warp] = m;
+                asm volatile("bar.sync 1, %0;" ::"n"(kProducers) : "memory");
+                m = s_red[0];
+#pragma unroll
+                for (int w = 1; w < kProducerWarps; ++w)
+                    m = fmaxf(m, s_red[w]);
+                if (m > 0.f && m <= 3.0e38f) {
+                    frexpf(m, &a_exp);  // m = f 2^a_exp, f in [0.5, 1)
+                    // 2^-a_exp and 2^a_exp both normal floats
+                    a_exp = max(-126, min(126, a_exp));
+                    scale = ldexpf(1.0f, -a_exp);
+                }
             }
+            // The record is read one stage ahead; the visibility, weight and
+            // taps at the start of the stage, so that their latency overlaps
+            // the wait for the buffer.
+            auto rec_at = [&](int st_, uint64_t &r_, int &i_) {
+                const int e = st_ * kStageVis + ii;
+                i_ = -1;
+                if (st_ < nst && e < it.count) {
+                    r_ = rec[it.start + e];
+                    i_ = perm[it.start + e];
+                }
+            };
+            uint64_t rn = 0;
+            int in = -1;
+            rec_at(0, rn, in);
             for (int st = 0; st < nst; ++st) {
                 const int t = t_global + st;
-                const int b = t % kStages;
-                unsigned char *A = Abuf + b * kABytes;
-                unsigned char *B = Bbuf + b * kBBytes;
-                const uint64_t r = r_next;
-                const int i = i_next;
-                float2 x = make_float2(0.f, 0.f);
-                float wt = 1.0f;
+                const int b = t % STAGES;
+                const uint64_t r = rn;
+                const int i = in;
+                rec_at(st + 1, rn, in);
+                StageData<NT> cur;
+                cur.pos = -1;
                 if (i >= 0) {
-                    x = __ldg(vis + i);
-                    if (weight)
-                        wt = __ldg(weight + i);
-                }
-                const int vn = it.start + (st + 1) * kStageVis + ii;
-                i_next = -1;
-                if (st + 1 < nst && vn < it.start + it.count) {
-                    r_next = rec[vn];
-                    i_next = perm[vn];
-                }
-                uint32_t pa = 0xffffffffu, pb = 0;
+                    cur.x = __ldg(vis + i);
+                    cur.wt = weight ? __ldg(weight + i) : 1.0f;
+                    const int row = rec_plane(r) * p.OS;
+                    const float2 *pv = taps + (row + rec_ov(r)) * S + q;
+                    const float2 *pu = taps + (row + rec_ou(r)) * S + q;
 #pragma unroll
-                for (int q = 0; q < kStages; ++q)
-                    if (q == b) {
-                        pa = oldA[q];
-                        pb = oldB[q];
+                    for (int j = 0; j < NT; ++j) {
+                        cur.tv[j] = make_float2(0.f, 0.f);
+                        cur.tu[j] = make_float2(0.f, 0.f);
+                        if (q + 8 * j < S) {
+                            cur.tv[j] = __ldg(pv + 8 * j);
+                            cur.tu[j] = __ldg(pu + 8 * j);
+                        }
                     }
-                if (t >= kStages) {
-                    // buffer b held stage t - kStages: wait (lane 0) for its
-                    // MMAs, then clear the entries this unit wrote there
+                    cur.pos = rec_ly(r) | (rec_lx(r) << 8) | (rec_conj(r) ? 1 << 16 : 0);
+                }
+                int old = -1;
+#pragma unroll
+                for (int c = 0; c < STAGES; ++c)
+                    if (c == b)
+                        old = oldpos[c];
+                if (t >= STAGES) {
+                    // buffer b held stage t - STAGES: wait (lane 0) for its
+                    // MMAs, then clear the entries this thread wrote there
                     if (lane == 0 && !s_abort &&
-                        !mbar_wait(empty + b, ((t - kStages) / kStages) & 1))
+                        !mbar_wait(empty + b, ((t - STAGES) / STAGES) & 1))
                         s_abort = 1;
                     __syncwarp();
                     tc_fence_after();
-                    if (pa != 0xffffffffu)
-                        unit_clear<S>(A, B, pa, pb, k);
+                    if (old >= 0) {
+                        uint32_t oa[NT], ob[NT];
+                        row_offsets<NT>((old & 255) + q, ii, oa);
+                        row_offsets<NT>(((old >> 8) & 255) + q, ii, ob);
+#pragma unroll
+                        for (int h = 0; h < TERMS; ++h) {
+                            unsigned char *A = Abuf + (b * TERMS + h) * kABytes;
+                            unsigned char *B = Bbuf + (b * TERMS + h) * kBBytes;
+#pragma unroll
+                            for (int j = 0; j < NT; ++j) {
+                                if (q + 8 * j >= S)
+                                    continue;
+                                *reinterpret_cast<uint32_t *>(A + oa[j]) = 0u;
+                                *reinterpret_cast<uint32_t *>(A + oa[j] + 8 * kSBO) = 0u;
+                                *reinterpret_cast<uint32_t *>(B + ob[j]) = 0u;
+                            }
+                        }
+                    }
                 }
-                pa = 0xffffffffu;
-                if (i >= 0) {
-                    const int row = rec_plane(r) * p.OS;
-                    const uint32_t offA = op_off(rec_ly(r) + k, ii);
-                    const uint32_t offB = op_off(rec_lx(r) + k, ii);
-                    unit_set<S, FP16>(A, B, offA, offB, k, taps + (row + rec_ov(r)) * S,
-                                      taps + (row + rec_ou(r)) * S, wt * x.x, wt * x.y,
-                                      rec_conj(r));
-                    pa = offA;
-                    pb = offB;
+                const int pos = cur.pos;
+                if (pos >= 0) {
+                    const bool cj = pos >> 16;
+                    const float wr = (cur.wt * cur.x.x) * scale;  // exact power-of-two scaling
+                    const float wi = (cur.wt * cur.x.y) * scale;
+                    uint32_t oa[NT], ob[NT];
+                    row_offsets<NT>((pos & 255) + q, ii, oa);
+                    row_offsets<NT>(((pos >> 8) & 255) + q, ii, ob);
+                    unsigned char *A0 = Abuf + (b * TERMS) * kABytes;
+                    unsigned char *B0 = Bbuf + (b * TERMS) * kBBytes;
+#pragma unroll
+                    for (int j = 0; j < NT; ++j) {
+                        if (q + 8 * j >= S)
+                            continue;
+                        const float vr = cur.tv[j].x, vi = cj ? -cur.tv[j].y : cur.tv[j].y;
+                        const float ur = cur.tu[j].x, ui = cj ? -cur.tu[j].y : cur.tu[j].y;
+                        const float pr = wr * ur - wi * ui;
+                        const float pi = wr * ui + wi * ur;
+                        uint32_t vh, vl, ph, pl;
+                        split2<PREC>(vr, vi, vh, vl);
+                        split2<PREC>(pr, pi, ph, pl);
+                        // rows y: (Bv_r, -Bv_i); rows 64 + y: (Bv_i, Bv_r)
+                        *reinterpret_cast<uint32_t *>(A0 + oa[j]) = pair_conj(vh);
+                        *reinterpret_cast<uint32_t *>(A0 + oa[j] + 8 * kSBO) = pair_swap(vh);
+                        *reinterpret_cast<uint32_t *>(B0 + ob[j]) = ph;
+                        if constexpr (TERMS == 2) {
+                            *reinterpret_cast<uint32_t *>(A0 + kABytes + oa[j]) = pair_conj(vl);
+                            *reinterpret_cast<uint32_t *>(A0 + kABytes + oa[j] + 8 * kSBO) =
+                                pair_swap(vl);
+                            *reinterpret_cast<uint32_t *>(B0 + kBBytes + ob[j]) = pl;
+                        }
+                    }
                 }
 #pragma unroll
-                for (int q = 0; q < kStages; ++q)
-                    if (q == b) {
-                        oldA[q] = pa;
-                        oldB[q] = pb;
-                    }
+                for (int c = 0; c < STAGES; ++c)
+                    if (c == b)
+                        oldpos[c] = pos;
                 fence_proxy_async();
                 __syncwarp();
                 if (lane == 0)
@@ -372,20 +463,28 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
         } else if (lane == 0) {
             for (int st = 0; st < nst; ++st) {
                 const int t = t_global + st;
-                const int b = t % kStages;
-                if (!s_abort && !mbar_wait(full + b, (t / kStages) & 1))
+                const int b = t % STAGES;
+                if (!s_abort && !mbar_wait(full + b, (t / STAGES) & 1))
                     s_abort = 1;
                 if (s_abort)
                     continue;
                 tc_fence_after();
                 const int v0 = it.start + st * kStageVis;
                 const int nv = min(kStageVis, it.start + it.count - v0);
-                const uint32_t a0 = smem_u32(Abuf + b * kABytes);
-                const uint32_t b0 = smem_u32(Bbuf + b * kBBytes);
+                const uint32_t ah = smem_u32(Abuf + (b * TERMS) * kABytes);
+                const uint32_t bh = smem_u32(Bbuf + (b * TERMS) * kBBytes);
                 const int nk = (nv + 7) / 8;  // K = 16 steps holding visibilities
-                for (int q = 0; q < nk; ++q)
-                    mma_f16(tmem, smem_desc(a0 + 256 * q), smem_desc(b0 + 256 * q), idesc,
-                            (st > 0 || q > 0) ? 1u : 0u);
+                for (int kq = 0; kq < nk; ++kq) {
+                    const uint32_t acc = (st > 0 || kq > 0) ? 1u : 0u;
+                    mma_f16(tmem, smem_desc(ah + 256 * kq), smem_desc(bh + 256 * kq), idesc,
+                            acc);
+                    if constexpr (TERMS == 2) {
+                        mma_f16(tmem, smem_desc(ah + 256 * kq),
+                                smem_desc(bh + kBBytes + 256 * kq), idesc, 1u);
+                        mma_f16(tmem, smem_desc(ah + kABytes + 256 * kq),
+                                smem_desc(bh + 256 * kq), idesc, 1u);
+                    }
+                }
                 mma_commit(empty + b);
             }
             if (!s_abort)
@@ -402,15 +501,16 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
         tc_fence_after();
         float *stg = reinterpret_cast<float *>(Bbuf);  // [128][64], xor-swizzled
         if (!mma_warp && !s_abort) {
-            const int q = warp & 3, h = warp >> 2;  // lane quarter, 16-column group
-            const int m = 32 * q + lane;
-            uint32_t r[16];
-            SEPW_TMEM_LD16(tmem + ((uint32_t)(32 * q) << 16) + 16 * h, r);
+            const int qq = warp & 3, h = warp >> 2;  // lane quarter, 16-column group
+            const int m = 32 * qq + lane;
+            const float back = ldexpf(1.0f, a_exp);
+            uint32_t rr[16];
+            SEPW_TMEM_LD16(tmem + ((uint32_t)(32 * qq) << 16) + 16 * h, rr);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
                 const int x = 16 * h + c;
-                stg[m * kWin + (x ^ (m & 31))] = __uint_as_float(r[c]);
+                stg[m * kWin + (x ^ (m & 31))] = __uint_as_float(rr[c]) * back;
             }
         }
         tc_fence_before();
@@ -430,7 +530,7 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
             }
         }
         __syncthreads();
-        for (int e = tid; e < kStages * kBBytes / 16; e += kTcBlock)
+        for (int e = tid; e < STAGES * TERMS * kBBytes / 16; e += kTcBlock)
             reinterpret_cast<uint4 *>(Bbuf)[e] = make_uint4(0, 0, 0, 0);
         fence_proxy_async();
     }
@@ -451,28 +551,36 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
                      : "memory");
 }
 
-size_t tc_smem_bytes()
-{
-    return (size_t)kStages * (kABytes + kBBytes) + sizeof(uint64_t) * (2 * kStages + 1);
-}
-
-template <int S, bool FP16>
+template <int S, int PREC>
 cudaError_t launch_tc_S(const DevParams &p, const Plan &plan, const float2 *vis,
                         const float *weight, const float2 *taps, float2 *grid, int num_sms,
                         int32_t *status, cudaStream_t s)
 {
-    const size_t shm = tc_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(grid_tc_kernel<S, FP16>,
+    constexpr size_t shm = tc_smem_bytes_for<PREC>();
+    cudaError_t e = cudaFuncSetAttribute(grid_tc_kernel<S, PREC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess)
         return e;
     e = cudaMemsetAsync(plan.d_item_counter, 0, sizeof(int32_t), s);
     if (e != cudaSuccess)
         return e;
-    grid_tc_kernel<S, FP16><<<num_sms, kTcBlock, shm, s>>>(
+    grid_tc_kernel<S, PREC><<<num_sms, kTcBlock, shm, s>>>(
         p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm, vis,
         weight, taps, grid, status);
     return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_tc_prec(int prec, const DevParams &p, const Plan &plan, const float2 *vis,
+                           const float *weight, const float2 *taps, float2 *grid,
+                           int num_sms, int32_t *status, cudaStream_t s)
+{
+    switch (prec) {
+    case 0: return launch_tc_S<S, 0>(p, plan, vis, weight, taps, grid, num_sms, status, s);
+    case 1: return launch_tc_S<S, 1>(p, plan, vis, weight, taps, grid, num_sms, status, s);
+    case 2: return launch_tc_S<S, 2>(p, plan, vis, weight, taps, grid, num_sms, status, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
@@ -485,16 +593,12 @@ int tc_tile_for_support(int S)
 
 cudaError_t launch_grid_tc(const DevParams &p, const Plan &plan, const float2 *vis,
                            const float *weight, const float2 *taps, float2 *grid,
-                           int num_sms, bool fp16, int32_t *status, cudaStream_t s)
+                           int num_sms, int prec, int32_t *status, cudaStream_t s)
 {
     if (p.T + p.S - 1 > kWin)
         return cudaErrorInvalidValue;
-#define SEPW_TC_CASE(SS)                                                                   \
-    case SS:                                                                               \
-        return fp16 ? launch_tc_S<SS, true>(p, plan, vis, weight, taps, grid, num_sms,     \
-                                            status, s)                                     \
-                    : launch_tc_S<SS, false>(p, plan, vis, weight, taps, grid, num_sms,    \
-                                             status, s);
+#define SEPW_TC_CASE(SS) \
+    case SS: return launch_tc_prec<SS>(prec, p, plan, vis, weight, taps, grid, num_sms, status, s);
     switch (p.S) {
         SEPW_TC_CASE(2) SEPW_TC_CASE(4) SEPW_TC_CASE(6) SEPW_TC_CASE(8) SEPW_TC_CASE(10)
         SEPW_TC_CASE(12) SEPW_TC_CASE(14) SEPW_TC_CASE(16)

@@ -18,6 +18,7 @@ FORM_PLAIN = 0
 FORM_TILED = 1
 FORM_TC_BF16 = 2
 FORM_TC_FP16 = 3
+FORM_TC_FP16X2 = 4
 GRID_TO_IMAGE = 0
 IMAGE_TO_GRID = 1
 IMAGE_TO_GRID_ADJOINT = 2
