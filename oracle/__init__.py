@@ -10,8 +10,8 @@ Contents (each function cites the passage it follows):
   * ``sepw_oracle``  taper, 1-D taps (Eq. gt), exact 2-D kernel table, cell /
                      plane location, brute-force dirty image and prediction
                      (Eq. dirty and the prediction integral, Sec. 2), the image
-                     step with grid correction, and the analysis formulas of
-                     Secs. 2-4 and Appendix A;
+                     step with grid correction, hybrid W stacking (Sec. 4.3),
+                     and the analysis formulas of Secs. 2-4 and Appendix A;
   * ``sepw_oracle.c`` plain C FP64 loops: separable gridder (Sec. 5), its
                      adjoint degridder, and the exact 2-D kernel gridder.
 
