@@ -238,6 +238,43 @@ SEPW_API int sepw_device_status(sepw_ctx *ctx, int *status, sepw_stream_t stream
  * Uses cuFFT (FP32 C2C); the plan is created on first use. */
 SEPW_API int sepw_image(sepw_ctx *ctx, int direction, float *buf, sepw_stream_t stream);
 
+/* Hybrid W stacking, Sec. 4.3: visibilities are partitioned by w into
+ * slices; the mean w term of a slice is corrected in image space by the
+ * phase of its centre and the residual w by the separable W-projection kernel
+ * (whose planes span |w - w_c| <= w_max of the context).
+ *
+ * sepw_wstack_plan: w_centres (HOST, nslices doubles, finite, strictly
+ * increasing) are the slice centres.  Visibility i goes to the slice with the
+ * nearest centre (|w_i - w_c| in IEEE double, ties to the lower centre;
+ * non-finite w to slice 0) and its residual is w_i - w_c (IEEE double).  A
+ * batched plan of nslices grids is then built on (u, v, w - w_c) and becomes
+ * the context's plan: sepw_grid_planned / sepw_degrid_planned then take
+ * vis, weight and vis_out in the CALLER'S order and nslices x N x N
+ * complex64 grids [slice][v][u].  Visibilities whose residual falls beyond
+ * w_max or whose footprint leaves the grid are dropped (sepw_plan_dropped).
+ * slice_out (device int32 [nvis]) receives each visibility's slice, or NULL.
+ * Requires a tiled or tensor-core form (SEPW_ENOTSUP for SEPW_FORM_PLAIN);
+ * synchronises `stream` once (slice counts).  The centres are kept for
+ * sepw_wstack_image / sepw_wstack_model_grids until the next call. */
+SEPW_API int sepw_wstack_plan(sepw_ctx *ctx, int32_t nslices, const double *w_centres,
+                              int64_t nvis, const double *u, const double *v, const double *w,
+                              int32_t *slice_out, sepw_stream_t stream);
+
+/* Dirty image of hybrid W stacking from the slice grids (nslices x N x N
+ * complex64, device; transformed IN PLACE, their contents are destroyed):
+ *   image[b][a] = sum_c exp(2 pi i w_c (n_ab - 1)) GRID_TO_IMAGE(grid_c)[b][a]
+ * (GRID_TO_IMAGE as in sepw_image).  image (N x N complex64) is overwritten.
+ * One batched cuFFT over the slices; FP32. */
+SEPW_API int sepw_wstack_image(sepw_ctx *ctx, float *slice_grids, float *image,
+                               sepw_stream_t stream);
+
+/* Prediction direction: slice_grids[c] (overwritten) =
+ *   IMAGE_TO_GRID(image * exp(-2 pi i w_c (n - 1)))   (IMAGE_TO_GRID as in
+ * sepw_image); degridding them with the W-stacking plan predicts the
+ * visibilities of the model image (N x N complex64, device, not modified). */
+SEPW_API int sepw_wstack_model_grids(sepw_ctx *ctx, const float *image, float *slice_grids,
+                                     sepw_stream_t stream);
+
 /* Limits of sepw_grid_noalloc's fixed scratch array. */
 #define SEPW_NOALLOC_MAX_VIS 524288    /* visibilities per call            */
 #define SEPW_NOALLOC_MAX_TILES 65536   /* ((N - S)/T + 1)^2 tiles per grid */

@@ -4,6 +4,7 @@
 #include <cufft.h>
 #include <math.h>
 #include <new>
+#include <vector>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -24,6 +25,19 @@ struct sepw_ctx {
     Plan plan;
     cufftHandle fft = 0;
     bool fft_ready = false;
+    // hybrid W stacking: slice centres of the last sepw_wstack_plan and the
+    // workspace of the slice sort
+    std::vector<double> ws_centres;
+    double *d_ws_c64 = nullptr;
+    float *d_ws_c32 = nullptr;
+    int32_t ws_centres_cap = 0;
+    int32_t *d_ws_count = nullptr;  // per slice: counts, then cursors
+    int32_t *d_ws_slice = nullptr;
+    int32_t *d_ws_part = nullptr;
+    double *d_ws_u = nullptr, *d_ws_v = nullptr, *d_ws_w = nullptr;
+    int64_t ws_cap = 0;
+    cufftHandle fft_batch = 0;
+    int fft_batch_n = 0;  // slices of fft_batch, 0 = none
     char err[512] = {0};
 };
 
@@ -303,6 +317,16 @@ void sepw_destroy(sepw_ctx *ctx)
     cudaDeviceSynchronize();
     if (ctx->fft_ready)
         cufftDestroy(ctx->fft);
+    if (ctx->fft_batch_n)
+        cufftDestroy(ctx->fft_batch);
+    cudaFree(ctx->d_ws_c64);
+    cudaFree(ctx->d_ws_c32);
+    cudaFree(ctx->d_ws_count);
+    cudaFree(ctx->d_ws_slice);
+    cudaFree(ctx->d_ws_part);
+    cudaFree(ctx->d_ws_u);
+    cudaFree(ctx->d_ws_v);
+    cudaFree(ctx->d_ws_w);
     cudaFree(ctx->d_taper64);
     cudaFree(ctx->d_taper32);
     cudaFree(ctx->d_tw);
@@ -618,6 +642,150 @@ int sepw_image(sepw_ctx *ctx, int direction, float *buf, sepw_stream_t stream)
     if (r != CUFFT_SUCCESS)
         return fail(ctx, SEPW_ECUDA, "cufftExecC2C failed (%d)", (int)r);
     SEPW_CUDA(ctx, launch_image_post(ctx->dp, direction, ctx->d_taper32, (float2 *)buf, s));
+    return SEPW_OK;
+}
+
+int sepw_wstack_plan(sepw_ctx *ctx, int32_t nslices, const double *w_centres, int64_t nvis,
+                     const double *u, const double *v, const double *w, int32_t *slice_out,
+                     sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    ctx->ws_centres.clear();
+    ctx->plan.valid = false;
+    if (ctx->p.form == SEPW_FORM_PLAIN)
+        return fail(ctx, SEPW_ENOTSUP, "W stacking needs a tiled or tensor-core form");
+    if (nslices < 1 || !w_centres)
+        return fail(ctx, SEPW_EINVAL, "nslices < 1 or w_centres NULL");
+    for (int c = 0; c < nslices; ++c) {
+        if (!isfinite(w_centres[c]))
+            return fail(ctx, SEPW_EINVAL, "w_centres[%d] not finite", c);
+        if (c > 0 && !(w_centres[c] > w_centres[c - 1]))
+            return fail(ctx, SEPW_EINVAL, "w_centres not strictly increasing at %d", c);
+    }
+    if (nvis < 0 || nvis > (int64_t)INT32_MAX - 1)
+        return fail(ctx, SEPW_EINVAL, "nvis out of range [0, 2^31 - 2]");
+    int rc;
+    if (nvis > 0 && ((rc = check_dev(ctx, u, "u", false)) || (rc = check_dev(ctx, v, "v", false)) ||
+                     (rc = check_dev(ctx, w, "w", false)) ||
+                     (slice_out && (rc = check_dev(ctx, slice_out, "slice_out", false)))))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nslices > ctx->ws_centres_cap) {
+        if ((rc = grow(ctx, &ctx->d_ws_c64, (size_t)nslices)) ||
+            (rc = grow(ctx, &ctx->d_ws_c32, (size_t)nslices)) ||
+            (rc = grow(ctx, &ctx->d_ws_count, (size_t)nslices)))
+            return rc;
+        ctx->ws_centres_cap = nslices;
+    }
+    if (nvis > ctx->ws_cap) {
+        const size_t cap = (size_t)nvis + nvis / 8;
+        if ((rc = grow(ctx, &ctx->d_ws_slice, cap)) || (rc = grow(ctx, &ctx->d_ws_part, cap)) ||
+            (rc = grow(ctx, &ctx->d_ws_u, cap)) || (rc = grow(ctx, &ctx->d_ws_v, cap)) ||
+            (rc = grow(ctx, &ctx->d_ws_w, cap)))
+            return rc;
+        ctx->ws_cap = (int64_t)cap;
+    }
+    std::vector<float> c32(w_centres, w_centres + nslices);
+    SEPW_CUDA(ctx, cudaMemcpyAsync(ctx->d_ws_c64, w_centres, sizeof(double) * nslices,
+                                   cudaMemcpyHostToDevice, s));
+    SEPW_CUDA(ctx, cudaMemcpyAsync(ctx->d_ws_c32, c32.data(), sizeof(float) * nslices,
+                                   cudaMemcpyHostToDevice, s));
+    SEPW_CUDA(ctx, cudaMemsetAsync(ctx->d_ws_count, 0, sizeof(int32_t) * nslices, s));
+    int32_t *slice = slice_out ? slice_out : ctx->d_ws_slice;
+    SEPW_CUDA(ctx, launch_wstack_assign(nvis, w, ctx->d_ws_c64, nslices, slice, ctx->d_ws_count, s));
+    std::vector<int32_t> cnt(nslices);
+    SEPW_CUDA(ctx, cudaMemcpyAsync(cnt.data(), ctx->d_ws_count, sizeof(int32_t) * nslices,
+                                   cudaMemcpyDeviceToHost, s));
+    SEPW_CUDA(ctx, cudaStreamSynchronize(s));
+    std::vector<int64_t> off(nslices + 1, 0);
+    std::vector<int32_t> cur(nslices);
+    for (int c = 0; c < nslices; ++c) {
+        cur[c] = (int32_t)off[c];
+        off[c + 1] = off[c] + cnt[c];
+    }
+    SEPW_CUDA(ctx, cudaMemcpyAsync(ctx->d_ws_count, cur.data(), sizeof(int32_t) * nslices,
+                                   cudaMemcpyHostToDevice, s));
+    SEPW_CUDA(ctx, launch_wstack_scatter(nvis, u, v, w, ctx->d_ws_c64, slice, ctx->d_ws_count,
+                                         ctx->d_ws_part, ctx->d_ws_u, ctx->d_ws_v, ctx->d_ws_w,
+                                         s));
+    if ((rc = plan_impl(ctx, nslices, off.data(), nvis, ctx->d_ws_u, ctx->d_ws_v, ctx->d_ws_w,
+                        s)))
+        return rc;
+    SEPW_CUDA(ctx, launch_wstack_compose(nvis, ctx->plan, ctx->d_ws_part, s));
+    // the host copies above must outlive the asynchronous transfers
+    SEPW_CUDA(ctx, cudaStreamSynchronize(s));
+    ctx->ws_centres.assign(w_centres, w_centres + nslices);
+    return SEPW_OK;
+}
+
+static int ensure_fft_batch(sepw_ctx *ctx, int L)
+{
+    if (ctx->fft_batch_n == L)
+        return SEPW_OK;
+    if (ctx->fft_batch_n)
+        cufftDestroy(ctx->fft_batch);
+    ctx->fft_batch_n = 0;
+    int n[2] = {ctx->p.grid_size, ctx->p.grid_size};
+    const int dist = ctx->p.grid_size * ctx->p.grid_size;
+    cufftResult r = cufftPlanMany(&ctx->fft_batch, 2, n, nullptr, 1, dist, nullptr, 1, dist,
+                                  CUFFT_C2C, L);
+    if (r != CUFFT_SUCCESS)
+        return fail(ctx, SEPW_ECUDA, "cufftPlanMany (%d slices) failed (%d)", L, (int)r);
+    ctx->fft_batch_n = L;
+    return SEPW_OK;
+}
+
+int sepw_wstack_image(sepw_ctx *ctx, float *slice_grids, float *image, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    if (ctx->ws_centres.empty())
+        return fail(ctx, SEPW_ENOPLAN, "no W-stacking plan");
+    int rc;
+    if ((rc = check_dev(ctx, slice_grids, "slice_grids", false)) ||
+        (rc = check_dev(ctx, image, "image", false)))
+        return rc;
+    const int L = (int)ctx->ws_centres.size();
+    if ((rc = ensure_fft_batch(ctx, L)))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cufftSetStream(ctx->fft_batch, s) != CUFFT_SUCCESS)
+        return fail(ctx, SEPW_ECUDA, "cufftSetStream failed");
+    SEPW_CUDA(ctx, launch_wstack_sign(ctx->dp, L, (float2 *)slice_grids, s));
+    cufftResult r = cufftExecC2C(ctx->fft_batch, (cufftComplex *)slice_grids,
+                                 (cufftComplex *)slice_grids, CUFFT_INVERSE);
+    if (r != CUFFT_SUCCESS)
+        return fail(ctx, SEPW_ECUDA, "cufftExecC2C failed (%d)", (int)r);
+    SEPW_CUDA(ctx, launch_wstack_combine(ctx->dp, L, ctx->d_taper32, ctx->d_ws_c32,
+                                         (const float2 *)slice_grids, (float2 *)image, s));
+    return SEPW_OK;
+}
+
+int sepw_wstack_model_grids(sepw_ctx *ctx, const float *image, float *slice_grids,
+                            sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    if (ctx->ws_centres.empty())
+        return fail(ctx, SEPW_ENOPLAN, "no W-stacking plan");
+    int rc;
+    if ((rc = check_dev(ctx, slice_grids, "slice_grids", false)) ||
+        (rc = check_dev(ctx, image, "image", false)))
+        return rc;
+    const int L = (int)ctx->ws_centres.size();
+    if ((rc = ensure_fft_batch(ctx, L)))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cufftSetStream(ctx->fft_batch, s) != CUFFT_SUCCESS)
+        return fail(ctx, SEPW_ECUDA, "cufftSetStream failed");
+    SEPW_CUDA(ctx, launch_wstack_split(ctx->dp, L, ctx->d_taper32, ctx->d_ws_c32,
+                                       (const float2 *)image, (float2 *)slice_grids, s));
+    cufftResult r = cufftExecC2C(ctx->fft_batch, (cufftComplex *)slice_grids,
+                                 (cufftComplex *)slice_grids, CUFFT_FORWARD);
+    if (r != CUFFT_SUCCESS)
+        return fail(ctx, SEPW_ECUDA, "cufftExecC2C failed (%d)", (int)r);
+    SEPW_CUDA(ctx, launch_wstack_sign(ctx->dp, L, (float2 *)slice_grids, s));
     return SEPW_OK;
 }
 

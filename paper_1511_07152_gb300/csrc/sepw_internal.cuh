@@ -261,6 +261,22 @@ cudaError_t launch_grid_tc(const DevParams &p, const Plan &plan, const float2 *v
                            const float *weight, const float2 *taps, float2 *grid,
                            int num_sms, int prec, int32_t *status, cudaStream_t s);
 
+// sepw_wstack.cu
+cudaError_t launch_wstack_assign(int64_t nvis, const double *w, const double *c, int L,
+                                 int32_t *slice, int32_t *count, cudaStream_t s);
+cudaError_t launch_wstack_scatter(int64_t nvis, const double *u, const double *v,
+                                  const double *w, const double *c, const int32_t *slice,
+                                  int32_t *cursor, int32_t *part, double *up, double *vp,
+                                  double *wp, cudaStream_t s);
+cudaError_t launch_wstack_compose(int64_t nvis, const Plan &plan, const int32_t *part,
+                                  cudaStream_t s);
+cudaError_t launch_wstack_sign(const DevParams &p, int L, float2 *g, cudaStream_t s);
+cudaError_t launch_wstack_combine(const DevParams &p, int L, const float *taper,
+                                  const float *wc, const float2 *g, float2 *image,
+                                  cudaStream_t s);
+cudaError_t launch_wstack_split(const DevParams &p, int L, const float *taper, const float *wc,
+                                const float2 *image, float2 *g, cudaStream_t s);
+
 // sepw_image.cu
 cudaError_t launch_image_pre(const DevParams &p, int direction, const float *taper,
                              float2 *buf, cudaStream_t s);

@@ -85,6 +85,9 @@ _SIG = {
                                          _P, _P]),
     "sepw_grid_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _P, _I64, _P, _P, _P, _P,
                                          _P, _P, _P, _P]),
+    "sepw_wstack_plan": (ctypes.c_int, [_P, ctypes.c_int32, _P, _I64, _P, _P, _P, _P, _P]),
+    "sepw_wstack_image": (ctypes.c_int, [_P, _P, _P, _P]),
+    "sepw_wstack_model_grids": (ctypes.c_int, [_P, _P, _P, _P]),
 }
 
 
@@ -148,6 +151,9 @@ class Context:
         if rc != OK:
             raise SepwError(rc, LIB.sepw_strerror(rc).decode())
         self.handle = h
+        self.plan_nvis = 0
+        self.plan_ngrids = 0
+        self.wstack_nslices = 0
 
     def close(self):
         if getattr(self, "handle", None):
@@ -361,6 +367,50 @@ def sepw_image(ctx: Context, direction: int, buf, stream=None):
     ctx.check(LIB.sepw_image(ctx.handle, int(direction),
                              _ptr(buf, torch.complex64, N * N, "buf"), _stream(stream)))
     return buf
+
+
+def sepw_wstack_plan(ctx: Context, w_centres, u, v, w, slice_out=None, stream=None):
+    """Hybrid W-stacking plan (slices at the host centres w_centres); the
+    context's plan then grids / degrids len(w_centres) grids with the
+    visibilities in the caller's order."""
+    import numpy as np
+    import torch
+    c = np.ascontiguousarray(np.asarray(w_centres, np.float64))
+    n = u.numel()
+    ctx.check(LIB.sepw_wstack_plan(ctx.handle, int(c.size), c.ctypes.data, n,
+                                   _ptr(u, torch.float64, n, "u"),
+                                   _ptr(v, torch.float64, n, "v"),
+                                   _ptr(w, torch.float64, n, "w"),
+                                   _ptr(slice_out, torch.int32, n, "slice_out"),
+                                   _stream(stream)))
+    ctx.plan_nvis = n
+    ctx.plan_ngrids = int(c.size)
+    ctx.wstack_nslices = int(c.size)
+
+
+def sepw_wstack_image(ctx: Context, slice_grids, image, stream=None):
+    """Dirty image from the slice grids (transformed in place)."""
+    import torch
+    N = ctx.params.grid_size
+    L = ctx.wstack_nslices
+    ctx.check(LIB.sepw_wstack_image(ctx.handle,
+                                    _ptr(slice_grids, torch.complex64, L * N * N, "slice_grids"),
+                                    _ptr(image, torch.complex64, N * N, "image"),
+                                    _stream(stream)))
+    return image
+
+
+def sepw_wstack_model_grids(ctx: Context, image, slice_grids, stream=None):
+    """Slice grids of a model image for W-stacking prediction."""
+    import torch
+    N = ctx.params.grid_size
+    L = ctx.wstack_nslices
+    ctx.check(LIB.sepw_wstack_model_grids(ctx.handle,
+                                          _ptr(image, torch.complex64, N * N, "image"),
+                                          _ptr(slice_grids, torch.complex64, L * N * N,
+                                               "slice_grids"),
+                                          _stream(stream)))
+    return slice_grids
 
 
 def sepw_grid_noalloc(params: Params, taps, u, v, w, vis, weight, grid, n_dropped=None,
