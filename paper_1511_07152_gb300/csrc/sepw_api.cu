@@ -706,7 +706,8 @@ int sepw_wstack_plan(sepw_ctx *ctx, int32_t nslices, const double *w_centres, in
     }
     SEPW_CUDA(ctx, cudaMemcpyAsync(ctx->d_ws_count, cur.data(), sizeof(int32_t) * nslices,
                                    cudaMemcpyHostToDevice, s));
-    SEPW_CUDA(ctx, launch_wstack_scatter(nvis, u, v, w, ctx->d_ws_c64, slice, ctx->d_ws_count,
+    SEPW_CUDA(ctx, launch_wstack_scatter(nvis, u, v, w, ctx->d_ws_c64, nslices, slice,
+                                         ctx->d_ws_count,
                                          ctx->d_ws_part, ctx->d_ws_u, ctx->d_ws_v, ctx->d_ws_w,
                                          s));
     if ((rc = plan_impl(ctx, nslices, off.data(), nvis, ctx->d_ws_u, ctx->d_ws_v, ctx->d_ws_w,

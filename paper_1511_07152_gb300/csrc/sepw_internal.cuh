@@ -265,7 +265,7 @@ cudaError_t launch_grid_tc(const DevParams &p, const Plan &plan, const float2 *v
 cudaError_t launch_wstack_assign(int64_t nvis, const double *w, const double *c, int L,
                                  int32_t *slice, int32_t *count, cudaStream_t s);
 cudaError_t launch_wstack_scatter(int64_t nvis, const double *u, const double *v,
-                                  const double *w, const double *c, const int32_t *slice,
+                                  const double *w, const double *c, int L, const int32_t *slice,
                                   int32_t *cursor, int32_t *part, double *up, double *vp,
                                   double *wp, cudaStream_t s);
 cudaError_t launch_wstack_compose(int64_t nvis, const Plan &plan, const int32_t *part,

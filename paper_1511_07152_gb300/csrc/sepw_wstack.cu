@@ -43,41 +43,75 @@ __device__ __forceinline__ int nearest_slice(double w, const double *__restrict_
     return k;
 }
 
-__global__ void __launch_bounds__(256) wstack_assign_kernel(
+// Slice of every visibility and the slice histogram.  With L <= kSmemSlices
+// the block counts in shared memory and adds one global atomic per slice it
+// saw (a handful of slices hold most visibilities, so per-visibility global
+// atomics would serialise on a few addresses).
+constexpr int kWsThreads = 1024;
+constexpr int kSmemSlices = 8192;
+
+__global__ void __launch_bounds__(kWsThreads) wstack_assign_kernel(
     int64_t nvis, const double *__restrict__ w, const double *__restrict__ c, int L,
     int32_t *__restrict__ slice, int32_t *count)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i < nvis;
-    int k = 0;
-    if (active) {
-        k = nearest_slice(w[i], c, L);
-        slice[i] = k;
+    extern __shared__ int32_t s_cnt[];
+    const bool smem = L <= kSmemSlices;
+    if (smem) {
+        for (int j = threadIdx.x; j < L; j += blockDim.x)
+            s_cnt[j] = 0;
+        __syncthreads();
     }
-    const unsigned act = __ballot_sync(0xffffffffu, active);
-    if (active) {
-        const unsigned peers = __match_any_sync(act, k);
-        if ((threadIdx.x & 31) == __ffs(peers) - 1)
-            atomicAdd(count + k, __popc(peers));
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nvis) {
+        const int k = nearest_slice(w[i], c, L);
+        slice[i] = k;
+        atomicAdd(smem ? s_cnt + k : count + k, 1);
+    }
+    if (smem) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < L; j += blockDim.x)
+            if (s_cnt[j])
+                atomicAdd(count + j, s_cnt[j]);
     }
 }
 
-// slice-ordered coordinates with the residual w - w_c; part[slot] = i
-__global__ void __launch_bounds__(256) wstack_scatter_kernel(
+// slice-ordered coordinates with the residual w - w_c; part[slot] = i.  The
+// block ranks its visibilities per slice in shared memory and reserves one
+// range per slice with a single global atomic.
+__global__ void __launch_bounds__(kWsThreads) wstack_scatter_kernel(
     int64_t nvis, const double *__restrict__ u, const double *__restrict__ v,
-    const double *__restrict__ w, const double *__restrict__ c,
+    const double *__restrict__ w, const double *__restrict__ c, int L,
     const int32_t *__restrict__ slice, int32_t *cursor, int32_t *__restrict__ part,
     double *__restrict__ up, double *__restrict__ vp, double *__restrict__ wp)
 {
+    extern __shared__ int32_t s_cnt[];  // [L] counts, then [L] bases
+    const bool smem = L <= kSmemSlices;
+    int32_t *s_base = s_cnt + (smem ? L : 0);
+    if (smem) {
+        for (int j = threadIdx.x; j < L; j += blockDim.x)
+            s_cnt[j] = 0;
+        __syncthreads();
+    }
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int k = 0, r = 0;
+    if (i < nvis) {
+        k = slice[i];
+        r = atomicAdd(smem ? s_cnt + k : cursor + k, 1);
+    }
+    if (smem) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < L; j += blockDim.x)
+            if (s_cnt[j])
+                s_base[j] = atomicAdd(cursor + j, s_cnt[j]);
+        __syncthreads();
+        r += s_base[k];
+    }
     if (i >= nvis)
         return;
-    const int k = slice[i];
-    const int s = atomicAdd(cursor + k, 1);
-    part[s] = (int32_t)i;
-    up[s] = u[i];
-    vp[s] = v[i];
-    wp[s] = __dadd_rn(w[i], -c[k]);
+    part[r] = (int32_t)i;
+    up[r] = u[i];
+    vp[r] = v[i];
+    wp[r] = __dadd_rn(w[i], -c[k]);
 }
 
 // plan slots and dropped indices refer to the slice order: map them back to
@@ -99,20 +133,29 @@ cudaError_t launch_wstack_assign(int64_t nvis, const double *w, const double *c,
 {
     if (nvis == 0)
         return cudaSuccess;
-    wstack_assign_kernel<<<(unsigned)((nvis + 255) / 256), 256, 0, s>>>(nvis, w, c, L, slice,
-                                                                        count);
+    const size_t shm = L <= kSmemSlices ? sizeof(int32_t) * L : 0;
+    wstack_assign_kernel<<<(unsigned)((nvis + kWsThreads - 1) / kWsThreads), kWsThreads, shm,
+                           s>>>(nvis, w, c, L, slice, count);
     return cudaGetLastError();
 }
 
 cudaError_t launch_wstack_scatter(int64_t nvis, const double *u, const double *v,
-                                  const double *w, const double *c, const int32_t *slice,
+                                  const double *w, const double *c, int L, const int32_t *slice,
                                   int32_t *cursor, int32_t *part, double *up, double *vp,
                                   double *wp, cudaStream_t s)
 {
     if (nvis == 0)
         return cudaSuccess;
-    wstack_scatter_kernel<<<(unsigned)((nvis + 255) / 256), 256, 0, s>>>(
-        nvis, u, v, w, c, slice, cursor, part, up, vp, wp);
+    const size_t shm = L <= kSmemSlices ? 2 * sizeof(int32_t) * L : 0;
+    if (shm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(wstack_scatter_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)shm);
+        if (e != cudaSuccess)
+            return e;
+    }
+    wstack_scatter_kernel<<<(unsigned)((nvis + kWsThreads - 1) / kWsThreads), kWsThreads, shm,
+                            s>>>(nvis, u, v, w, c, L, slice, cursor, part, up, vp, wp);
     return cudaGetLastError();
 }
 
