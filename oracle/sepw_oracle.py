@@ -548,6 +548,65 @@ def wstack_model_grids(p: Params, image, centres):
 
 
 # --------------------------------------------------------------------------
+# major cycles: weighted least-squares imaging by conjugate gradients
+# --------------------------------------------------------------------------
+
+
+def predict_op(p: Params, loc: dict, T, image):
+    """M x: IMAGE -> GRID (Sec. 2) then separable degridding with unit
+    weights: the visibilities predicted from a model image."""
+    return degrid_separable(p, loc, image_to_grid(p, image), None, T)
+
+
+def predict_adjoint(p: Params, loc: dict, T, vis):
+    """M^H r: separable gridding with unit weights, then the adjoint of
+    IMAGE -> GRID, which is GRID -> IMAGE divided by n^2."""
+    g = grid_separable(p, loc, vis, None, T)
+    l = pixel_l(p.N, p.fov)
+    L, M = np.meshgrid(l, l)
+    return grid_to_image(p, g) / (1.0 - L * L - M * M)
+
+
+def cg_major_cycles(p: Params, loc: dict, T, vis, weight, n_cycles: int, x0=None):
+    """Weighted least-squares imaging, min over real images x of
+    sum_i W_i |(M x)_i - V_i|^2, by conjugate gradients on the normal
+    equations Re(M^H W M) x = Re(M^H W V).  Each cycle predicts the
+    visibilities of a search direction (degridding) and grids them back
+    (gridding): the alternation of major cycles (Sec. 6), with the model
+    update of least squares in place of a CLEAN minor cycle.
+
+    Returns (x, losses, residual images r_k, directions p_k); losses[k] is the
+    weighted chi^2 after k cycles."""
+    vis = np.asarray(vis, np.complex128)
+    wt = np.ones(len(vis)) if weight is None else np.asarray(weight, np.float64)
+    x = np.zeros((p.N, p.N)) if x0 is None else np.array(x0, np.float64)
+
+    def loss(x_):
+        r_ = predict_op(p, loc, T, x_) - vis
+        return float(np.sum(wt * (r_.real ** 2 + r_.imag ** 2)))
+
+    def normal(y):
+        return predict_adjoint(p, loc, T, wt * predict_op(p, loc, T, y)).real
+
+    r = predict_adjoint(p, loc, T, wt * (vis - predict_op(p, loc, T, x))).real
+    d = r.copy()
+    rr = float(np.sum(r * r))
+    losses, rs, ds = [loss(x)], [r.copy()], [d.copy()]
+    for _ in range(n_cycles):
+        q = normal(d)
+        alpha = rr / float(np.sum(d * q))
+        x = x + alpha * d
+        r = r - alpha * q
+        rr_new = float(np.sum(r * r))
+        d = r + (rr_new / rr) * d
+        rr = rr_new
+        losses.append(loss(x))
+        rs.append(r.copy())
+        ds.append(d.copy())
+    return x, losses, rs, ds
+
+
+# --------------------------------------------------------------------------
 # analysis formulas (Secs. 2-4, Appendix A)
 # --------------------------------------------------------------------------
 
