@@ -238,6 +238,11 @@ SEPW_API int sepw_device_status(sepw_ctx *ctx, int *status, sepw_stream_t stream
  * Uses cuFFT (FP32 C2C); the plan is created on first use. */
 SEPW_API int sepw_image(sepw_ctx *ctx, int direction, float *buf, sepw_stream_t stream);
 
+/* Taper of the grid correction: taper[a] = c1(nu_a), nu_a = (a - N/2)/N, the
+ * transform of the antialiasing window normalised to c1(0) = 1 (Sec. 2), as
+ * used by sepw_image (FP32, device, N floats, overwritten). */
+SEPW_API int sepw_taper(sepw_ctx *ctx, float *taper, sepw_stream_t stream);
+
 /* Hybrid W stacking, Sec. 4.3: visibilities are partitioned by w into
  * slices; the mean w term of a slice is corrected in image space by the
  * phase of its centre and the residual w by the separable W-projection kernel

@@ -570,40 +570,51 @@ def predict_adjoint(p: Params, loc: dict, T, vis):
 def cg_major_cycles(p: Params, loc: dict, T, vis, weight, n_cycles: int, x0=None):
     """Weighted least-squares imaging, min over real images x of
     sum_i W_i |(M x)_i - V_i|^2, by conjugate gradients on the normal
-    equations Re(M^H W M) x = Re(M^H W V).  Each cycle predicts the
-    visibilities of a search direction (degridding) and grids them back
-    (gridding): the alternation of major cycles (Sec. 6), with the model
-    update of least squares in place of a CLEAN minor cycle.
+    equations.  Each cycle predicts the visibilities of a search direction
+    (degridding) and grids them back (gridding): the alternation of major
+    cycles (Sec. 6), with the model update of least squares in place of a
+    CLEAN minor cycle.
 
-    Returns (x, losses, residual images r_k, directions p_k); losses[k] is the
-    weighted chi^2 after k cycles."""
+    Reading (the paper gives no solver): CG runs on y with x = D y,
+    D = n c1(nu_a) c1(nu_b) the grid correction, i.e. on the operator M D,
+    which is prediction without the division by n c1 c1.  M itself divides
+    by n c1 c1, up to 1e8 at the image edge for support 16, and unpreconditioned
+    CG loses conjugacy there.
+
+    Returns (x, losses, residuals r_k, directions d_k) with losses[k] the
+    weighted chi^2 after k cycles and r_k, d_k the CG vectors in y."""
     vis = np.asarray(vis, np.complex128)
     wt = np.ones(len(vis)) if weight is None else np.asarray(weight, np.float64)
-    x = np.zeros((p.N, p.N)) if x0 is None else np.array(x0, np.float64)
+    n, cc = _correction(p)
+    D = n * cc
+    y = np.zeros((p.N, p.N)) if x0 is None else np.array(x0, np.float64) / D
 
-    def loss(x_):
-        r_ = predict_op(p, loc, T, x_) - vis
+    def op(y_):  # M D y
+        return predict_op(p, loc, T, D * y_)
+
+    def op_h(r_):  # Re(D M^H r)
+        return D * predict_adjoint(p, loc, T, r_).real
+
+    def loss(y_):
+        r_ = op(y_) - vis
         return float(np.sum(wt * (r_.real ** 2 + r_.imag ** 2)))
 
-    def normal(y):
-        return predict_adjoint(p, loc, T, wt * predict_op(p, loc, T, y)).real
-
-    r = predict_adjoint(p, loc, T, wt * (vis - predict_op(p, loc, T, x))).real
+    r = op_h(wt * (vis - op(y)))
     d = r.copy()
     rr = float(np.sum(r * r))
-    losses, rs, ds = [loss(x)], [r.copy()], [d.copy()]
+    losses, rs, ds = [loss(y)], [r.copy()], [d.copy()]
     for _ in range(n_cycles):
-        q = normal(d)
+        q = op_h(wt * op(d))
         alpha = rr / float(np.sum(d * q))
-        x = x + alpha * d
+        y = y + alpha * d
         r = r - alpha * q
         rr_new = float(np.sum(r * r))
         d = r + (rr_new / rr) * d
         rr = rr_new
-        losses.append(loss(x))
+        losses.append(loss(y))
         rs.append(r.copy())
         ds.append(d.copy())
-    return x, losses, rs, ds
+    return D * y, losses, rs, ds
 
 
 # --------------------------------------------------------------------------

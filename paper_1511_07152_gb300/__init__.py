@@ -11,7 +11,7 @@ raises if it is missing (there is no CPU fallback).  ``build`` compiles it.
 import importlib
 
 
-_SUBMODULES = ("build", "sepw", "autotune")
+_SUBMODULES = ("build", "sepw", "autotune", "autograd", "major_cycle")
 
 
 def __getattr__(name):

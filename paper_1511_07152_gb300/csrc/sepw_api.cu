@@ -645,6 +645,18 @@ int sepw_image(sepw_ctx *ctx, int direction, float *buf, sepw_stream_t stream)
     return SEPW_OK;
 }
 
+int sepw_taper(sepw_ctx *ctx, float *taper, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    int rc = check_dev(ctx, taper, "taper", false);
+    if (rc)
+        return rc;
+    SEPW_CUDA(ctx, cudaMemcpyAsync(taper, ctx->d_taper32, sizeof(float) * ctx->p.grid_size,
+                                   cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return SEPW_OK;
+}
+
 int sepw_wstack_plan(sepw_ctx *ctx, int32_t nslices, const double *w_centres, int64_t nvis,
                      const double *u, const double *v, const double *w, int32_t *slice_out,
                      sepw_stream_t stream)

@@ -85,6 +85,7 @@ _SIG = {
                                          _P, _P]),
     "sepw_grid_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _P, _I64, _P, _P, _P, _P,
                                          _P, _P, _P, _P]),
+    "sepw_taper": (ctypes.c_int, [_P, _P, _P]),
     "sepw_wstack_plan": (ctypes.c_int, [_P, ctypes.c_int32, _P, _I64, _P, _P, _P, _P, _P]),
     "sepw_wstack_image": (ctypes.c_int, [_P, _P, _P, _P]),
     "sepw_wstack_model_grids": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -367,6 +368,16 @@ def sepw_image(ctx: Context, direction: int, buf, stream=None):
     ctx.check(LIB.sepw_image(ctx.handle, int(direction),
                              _ptr(buf, torch.complex64, N * N, "buf"), _stream(stream)))
     return buf
+
+
+def sepw_taper(ctx: Context, out=None, stream=None):
+    """c1(nu_a), a = 0..N-1 (float32, device)."""
+    import torch
+    N = ctx.params.grid_size
+    if out is None:
+        out = torch.empty(N, dtype=torch.float32, device=torch.cuda.current_device())
+    ctx.check(LIB.sepw_taper(ctx.handle, _ptr(out, torch.float32, N, "taper"), _stream(stream)))
+    return out
 
 
 def sepw_wstack_plan(ctx: Context, w_centres, u, v, w, slice_out=None, stream=None):

@@ -1,8 +1,9 @@
 """Pins of the oracle's least-squares major cycles (conjugate gradients on
-the normal equations of prediction): the dot-product test of the prediction
-operator against its adjoint, and the algebraic invariants every CG run has
-to show (non-increasing chi^2, orthogonal residuals, directions conjugate
-under the normal operator).  The operators themselves are pinned by the
+the normal equations of prediction, preconditioned by the grid correction):
+the dot-product test of the prediction operator against its adjoint, and the
+algebraic invariants every CG run has to show (non-increasing chi^2,
+orthogonal residuals, directions conjugate under the normal operator, the
+first step an exact line search).  The operators themselves are pinned by the
 pipeline tests (prediction integral, adjointness of the gridder)."""
 import math
 
@@ -43,8 +44,14 @@ def test_cg_invariants():
     nrm = np.sqrt(np.diag(G))
     assert np.max(np.abs(G / np.outer(nrm, nrm) - np.eye(len(rs)))) < 1e-8
 
+    # CG runs on y, x = Dg y, with Dg = n c1 c1 (the grid correction)
+    l = O.pixel_l(p.N, p.fov)
+    L, M = np.meshgrid(l, l)
+    c1 = O.kb_taper(O.pixel_nu(p.N), p.S, p.kb_beta)
+    Dg = np.sqrt(1 - L * L - M * M) * c1[None, :] * c1[:, None]
+
     def normal(y):
-        return O.predict_adjoint(p, loc, T, wt * O.predict_op(p, loc, T, y)).real
+        return Dg * O.predict_adjoint(p, loc, T, wt * O.predict_op(p, loc, T, Dg * y)).real
 
     D = np.array([d.ravel() for d in ds[:6]])
     Q = np.array([normal(d).ravel() for d in ds[:6]])
@@ -52,8 +59,10 @@ def test_cg_invariants():
     dn = np.sqrt(np.abs(np.diag(C)))
     off = np.abs(C / np.outer(dn, dn) - np.eye(6))
     assert np.max(off) < 1e-8
-    # the first step is the exact line search along the negative gradient
+    # the first step is the exact line search along the negative gradient in y
     r0 = rs[0]
+    assert np.max(np.abs(r0 - Dg * O.predict_adjoint(p, loc, T, wt * vis).real)) < \
+        1e-12 * np.max(np.abs(r0))
     a0 = float(np.sum(r0 * r0)) / float(np.sum(r0 * normal(r0)))
     x1, _, _, _ = O.cg_major_cycles(p, loc, T, vis, wt, 1)
-    assert np.max(np.abs(x1 - a0 * r0)) < 1e-12 * np.max(np.abs(x1))
+    assert np.max(np.abs(x1 - Dg * a0 * r0)) < 1e-12 * np.max(np.abs(x1))
