@@ -13,7 +13,9 @@
  *     and plane p touches the S x S cells (cv - S/2 + 1 + k, cu - S/2 + 1 + j),
  *     j, k = 0..S-1;
  *   - taps[p][o][j] (complex) is the 1-D kernel value for footprint column j
- *     at oversample offset o of plane p;
+ *     at oversample offset o of plane p; the separable functions take the
+ *     v-direction values from taps_v when it is not NULL (the facet screens
+ *     of Sec. 4.1 differ between l and m), else from taps;
  *   - conj[i] != 0 means w_i < 0: the kernel used is the complex conjugate of
  *     the |w| plane's kernel;
  *   - keep[i] == 0 means the visibility was dropped (footprint off the grid or
@@ -42,7 +44,7 @@ void oracle_grid_separable(int64_t nvis, int32_t N, int32_t S, int32_t OS,
                            const int32_t *plane, const uint8_t *conj,
                            const uint8_t *keep, const double *vis,
                            const double *weight, const double *taps,
-                           int32_t wrap, double *grid)
+                           const double *taps_v, int32_t wrap, double *grid)
 {
     double pu_re[1024], pu_im[1024];
     for (int64_t i = 0; i < nvis; ++i) {
@@ -52,7 +54,7 @@ void oracle_grid_separable(int64_t nvis, int32_t N, int32_t S, int32_t OS,
         double vr = wgt * vis[2 * i], vi = wgt * vis[2 * i + 1];
         double sgn = conj[i] ? -1.0 : 1.0;
         const double *tu = taps + 2 * (((int64_t)plane[i] * OS + ou[i]) * S);
-        const double *tv = taps + 2 * (((int64_t)plane[i] * OS + ov[i]) * S);
+        const double *tv = (taps_v ? taps_v : taps) + 2 * (((int64_t)plane[i] * OS + ov[i]) * S);
         for (int j = 0; j < S; ++j) {
             double tr = tu[2 * j], ti = sgn * tu[2 * j + 1];
             pu_re[j] = vr * tr - vi * ti;
@@ -86,7 +88,7 @@ void oracle_degrid_separable(int64_t nvis, int32_t N, int32_t S, int32_t OS,
                              const int32_t *plane, const uint8_t *conj,
                              const uint8_t *keep, const double *grid,
                              const double *weight, const double *taps,
-                             int32_t wrap, double *vis_out)
+                             const double *taps_v, int32_t wrap, double *vis_out)
 {
     for (int64_t i = 0; i < nvis; ++i) {
         vis_out[2 * i] = 0.0;
@@ -95,7 +97,7 @@ void oracle_degrid_separable(int64_t nvis, int32_t N, int32_t S, int32_t OS,
             continue;
         double sgn = conj[i] ? -1.0 : 1.0;
         const double *tu = taps + 2 * (((int64_t)plane[i] * OS + ou[i]) * S);
-        const double *tv = taps + 2 * (((int64_t)plane[i] * OS + ov[i]) * S);
+        const double *tv = (taps_v ? taps_v : taps) + 2 * (((int64_t)plane[i] * OS + ov[i]) * S);
         double acc_re = 0.0, acc_im = 0.0;
         for (int k = 0; k < S; ++k) {
             int64_t y = (int64_t)cv[i] - S / 2 + 1 + k;

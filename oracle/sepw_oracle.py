@@ -280,9 +280,9 @@ def _clib():
         common = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                   _I32, _I32, _I32, _I32, _I32, _U8, _U8]
         lib.oracle_grid_separable.argtypes = common + [_F64, ctypes.c_void_p, _F64,
-                                                       ctypes.c_int32, _F64]
+                                                       ctypes.c_void_p, ctypes.c_int32, _F64]
         lib.oracle_degrid_separable.argtypes = common + [_F64, ctypes.c_void_p, _F64,
-                                                         ctypes.c_int32, _F64]
+                                                         ctypes.c_void_p, ctypes.c_int32, _F64]
         lib.oracle_grid_exact2d.argtypes = common + [_F64, ctypes.c_void_p, _F64,
                                                      ctypes.c_int32, _F64]
         for f in (lib.oracle_grid_separable, lib.oracle_degrid_separable,
@@ -311,8 +311,16 @@ def _weight_arg(weight, n):
     return wt, wt.ctypes.data
 
 
-def grid_separable(p: Params, loc: dict, vis, weight, T, wrap=False, grid=None):
-    """Separable gridder (Sec. 5), FP64: returns the N x N complex128 grid."""
+def _tv_arg(Tv):
+    if Tv is None:
+        return None, None
+    tv = _c128(Tv).reshape(-1)
+    return tv, tv.ctypes.data
+
+
+def grid_separable(p: Params, loc: dict, vis, weight, T, wrap=False, grid=None, Tv=None):
+    """Separable gridder (Sec. 5), FP64: returns the N x N complex128 grid.
+    Tv: separate v-direction table (facet screens, Sec. 4.1), default T."""
     n = len(loc["keep"])
     if p.S > 1024:
         raise ValueError("support > 1024")
@@ -320,20 +328,22 @@ def grid_separable(p: Params, loc: dict, vis, weight, T, wrap=False, grid=None):
         grid = np.zeros((p.N, p.N), np.complex128)
     visd = _c128(vis)
     wt, wptr = _weight_arg(weight, n)
+    tv, tvptr = _tv_arg(Tv)
     gflat = grid.view(np.float64).reshape(-1)
     _clib().oracle_grid_separable(n, p.N, p.S, p.OS, *_loc_args(loc), visd, wptr,
-                                  _c128(T).reshape(-1), int(wrap), gflat)
+                                  _c128(T).reshape(-1), tvptr, int(wrap), gflat)
     return grid
 
 
-def degrid_separable(p: Params, loc: dict, grid, weight, T, wrap=False):
+def degrid_separable(p: Params, loc: dict, grid, weight, T, wrap=False, Tv=None):
     """Separable degridder (the adjoint of grid_separable), FP64."""
     n = len(loc["keep"])
     out = np.zeros(n, np.complex128)
     wt, wptr = _weight_arg(weight, n)
+    tv, tvptr = _tv_arg(Tv)
     _clib().oracle_degrid_separable(n, p.N, p.S, p.OS, *_loc_args(loc),
                                     _c128(grid).reshape(-1), wptr,
-                                    _c128(T).reshape(-1), int(wrap),
+                                    _c128(T).reshape(-1), tvptr, int(wrap),
                                     out.view(np.float64))
     return out
 
@@ -422,10 +432,12 @@ def _shift_dft_matrix(N, sign):
     return np.exp(sign * 2j * np.pi * m / N)
 
 
-def _correction(p: Params):
+def _correction(p: Params, l0: float = 0.0, m0: float = 0.0):
+    """n at the pixels (offset by a facet centre (l0, m0), Sec. 4.1) and the
+    taper product c1(nu_a) c1(nu_b)."""
     nu = pixel_nu(p.N)
     l = nu * p.fov
-    L, M = np.meshgrid(l, l)
+    L, M = np.meshgrid(l + l0, l + m0)
     n = np.sqrt(1.0 - L * L - M * M)
     c = kb_taper(nu, p.S, p.kb_beta)
     return n, c[None, :] * c[:, None]
@@ -440,10 +452,11 @@ def grid_to_image_direct(p: Params, grid):
     return n / cc * (E @ np.asarray(grid, np.complex128) @ E.T)
 
 
-def grid_to_image(p: Params, grid):
-    """GRID -> IMAGE with numpy.fft as the DFT primitive (same sum)."""
+def grid_to_image(p: Params, grid, l0: float = 0.0, m0: float = 0.0):
+    """GRID -> IMAGE with numpy.fft as the DFT primitive (same sum); for a
+    facet centred at (l0, m0) the factor n is taken at l0 + l, m0 + m."""
     N = p.N
-    n, cc = _correction(p)
+    n, cc = _correction(p, l0, m0)
     s = np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(np.asarray(grid, np.complex128))))
     return n / cc * (N * N) * s
 
@@ -462,6 +475,76 @@ def image_to_grid(p: Params, image):
     n, cc = _correction(p)
     x = np.asarray(image, np.complex128) / (n * cc)
     return np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(x)))
+
+
+# --------------------------------------------------------------------------
+# image-plane faceting (Sec. 4.1, Eq. gt-facet)
+# --------------------------------------------------------------------------
+
+
+def facet_coeffs(l0: float, m0: float):
+    """Quadratic coefficients of the facet screens of Eq. gt-facet:
+    a_l = -(1/n0 + l0^2/n0^3)/2, a_m = -(1/n0 + m0^2/n0^3)/2, n0 = h(l0, m0).
+    g^l_w(l) = exp(2 pi i w a_l l^2), g^m_w(m) = exp(2 pi i w a_m m^2)."""
+    n0 = math.sqrt(1.0 - l0 * l0 - m0 * m0)
+    return -0.5 * (1.0 / n0 + l0 * l0 / n0 ** 3), -0.5 * (1.0 / n0 + m0 * m0 / n0 ** 3)
+
+
+def taps_facet(p: Params, l0: float, m0: float):
+    """(Tu, Tv): the 1-D tables of a facet centred at (l0, m0), built as taps()
+    with the screens g^l_w (u table) and g^m_w (v table) of Eq. gt-facet over
+    the facet's pixels (l, m relative to the facet centre)."""
+    N, S, OS = p.N, p.S, p.OS
+    wp = plane_w(p.P, p.w_max)
+    nu = pixel_nu(N)
+    l = nu * p.fov
+    c = kb_taper(nu, S, p.kb_beta)
+    E = _dft_rows(S, OS, N)
+    out = []
+    for a in facet_coeffs(l0, m0):
+        h = c[None, :] * np.exp(2j * np.pi * wp[:, None] * a * (l * l)[None, :])
+        out.append(((h @ E.T) / N).reshape(len(wp), OS, S))
+    return out[0], out[1]
+
+
+def facet_shift(u, v, w, vis, l0: float, m0: float):
+    """Visibilities of a facet (Sec. 4.1): the linear term of the Taylor
+    expansion of h about (l0, m0) is absorbed by u' = u - w l0 / n0,
+    v' = v - w m0 / n0, and the phase centre moves to the facet centre,
+    V' = V exp(2 pi i (u l0 + v m0 + w (n0 - 1)))."""
+    n0 = math.sqrt(1.0 - l0 * l0 - m0 * m0)
+    u = np.asarray(u, np.float64)
+    v = np.asarray(v, np.float64)
+    w = np.asarray(w, np.float64)
+    ph = u * l0 + v * m0 + w * (n0 - 1.0)
+    return u - w * l0 / n0, v - w * m0 / n0, np.asarray(vis) * np.exp(2j * np.pi * ph)
+
+
+def facet_image(p: Params, l0: float, m0: float, u, v, w, vis, weight, wrap=False):
+    """Dirty image of one facet: shifted visibilities gridded with the facet
+    tables (separable, Sec. 5), image step with n at l0 + l, m0 + m."""
+    up, vp, visp = facet_shift(u, v, w, vis, l0, m0)
+    loc = locate(p, up, vp, w, wrap=wrap)
+    Tu, Tv = taps_facet(p, l0, m0)
+    g = grid_separable(p, loc, visp, weight, Tu, wrap=wrap, Tv=Tv)
+    return grid_to_image(p, g, l0, m0)
+
+
+def dirty_direct_facet(p: Params, l0: float, m0: float, u, v, w, vis, weight=None):
+    """Eq. dirty over a facet's pixels (l0 + l, m0 + m) with the w term
+    exp(2 pi i w (n - 1)) replaced by its facet approximation
+    exp(2 pi i w (n0 - 1)) exp(-2 pi i w (l0 l + m0 m) / n0) g^l_w(l) g^m_w(m)."""
+    l = pixel_l(p.N, p.fov)
+    L, M = np.meshgrid(l, l)
+    n = np.sqrt(1.0 - (L + l0) ** 2 - (M + m0) ** 2)
+    al, am = facet_coeffs(l0, m0)
+    up, vp, visp = facet_shift(u, v, w, vis, l0, m0)
+    wt = np.ones(len(up)) if weight is None else np.asarray(weight, np.float64)
+    img = np.zeros((p.N, p.N), np.complex128)
+    for i in range(len(up)):
+        ph = up[i] * L + vp[i] * M + w[i] * (al * L * L + am * M * M)
+        img += wt[i] * complex(visp[i]) * np.exp(2j * np.pi * ph)
+    return n * img
 
 
 # --------------------------------------------------------------------------
