@@ -243,6 +243,37 @@ SEPW_API int sepw_image(sepw_ctx *ctx, int direction, float *buf, sepw_stream_t 
  * used by sepw_image (FP32, device, N floats, overwritten). */
 SEPW_API int sepw_taper(sepw_ctx *ctx, float *taper, sepw_stream_t stream);
 
+/* Image-plane faceting, Sec. 4.1 (Eq. gt-facet).  sepw_set_facet puts the
+ * context in facet mode for the facet centred at (l0, m0) (direction cosines
+ * of the original image plane, l0^2 + m0^2 < 1; the context's grid_size and
+ * fov are the facet's).  In facet mode:
+ *   - sepw_make_taps / _f64 write TWO tables, [2][P][OS][S]: the u-direction
+ *     table of the screen g^l_w(l) = exp(2 pi i w a_l l^2) and then the
+ *     v-direction table of g^m_w(m) = exp(2 pi i w a_m m^2), with
+ *     a_l = -(1/n0 + l0^2/n0^3)/2, a_m = -(1/n0 + m0^2/n0^3)/2, n0 = h(l0, m0),
+ *     l, m relative to the facet centre (no quartic term);
+ *   - gridding and degridding take the v-direction taps from the second table;
+ *   - the image steps (sepw_image, W stacking) take n at l0 + l, m0 + m.
+ * sepw_set_facet(ctx, 0, 0, 0) (enable = 0) returns to the one-table screen of
+ * Eq. gt.  The plan is unaffected; regenerate the taps after a change. */
+SEPW_API int sepw_set_facet(sepw_ctx *ctx, int enable, double l0, double m0);
+
+/* Visibilities of the context's facet (Sec. 4.1).  SEPW_FACET_IN:
+ *   u_out = u - w l0 / n0,  v_out = v - w m0 / n0   (IEEE double, this order)
+ *   vis_out = vis exp(2 pi i (u l0 + v m0 + w (n0 - 1)))
+ * (plan and grid with u_out, v_out, w and vis_out).  SEPW_FACET_OUT:
+ *   vis_out = vis exp(-2 pi i (u l0 + v m0 + w (n0 - 1)))
+ * (predictions of the facet back to the original phase centre).  u_out,
+ * v_out (device doubles) may be NULL to skip the shift, vis / vis_out
+ * (device complex64) may be NULL to skip the rotation; vis_out may equal vis.
+ * Requires facet mode (SEPW_ENOTSUP otherwise). */
+#define SEPW_FACET_IN 0
+#define SEPW_FACET_OUT 1
+SEPW_API int sepw_facet_shift(sepw_ctx *ctx, int direction, int64_t nvis, const double *u,
+                              const double *v, const double *w, const float *vis,
+                              double *u_out, double *v_out, float *vis_out,
+                              sepw_stream_t stream);
+
 /* Hybrid W stacking, Sec. 4.3: visibilities are partitioned by w into
  * slices; the mean w term of a slice is corrected in image space by the
  * phase of its centre and the residual w by the separable W-projection kernel

@@ -58,7 +58,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    # host arithmetic that must match the FP64 oracle bit for bit (facet
+    # centre n0) is not contracted into fused multiply-adds
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-ffp-contract=off",
+                    "-Xcompiler", "-fPIC",
                     "-Xcompiler", "-fvisibility=hidden", f"-I{INCLUDE}"]
     objs = []
 

@@ -657,6 +657,61 @@ int sepw_taper(sepw_ctx *ctx, float *taper, sepw_stream_t stream)
     return SEPW_OK;
 }
 
+int sepw_set_facet(sepw_ctx *ctx, int enable, double l0, double m0)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    if (!enable) {
+        ctx->dp.facet = 0;
+        ctx->dp.voff = 0;
+        ctx->dp.l0 = ctx->dp.m0 = 0.0;
+        ctx->dp.a2u = ctx->dp.a2v = -0.5;
+        return SEPW_OK;
+    }
+    if (!isfinite(l0) || !isfinite(m0) || !(l0 * l0 + m0 * m0 < 1.0))
+        return fail(ctx, SEPW_EINVAL, "facet centre (%g, %g) not inside the unit circle", l0,
+                    m0);
+    const double n0 = sqrt(1.0 - l0 * l0 - m0 * m0);
+    ctx->dp.facet = 1;
+    ctx->dp.voff = (int64_t)ctx->p.n_wplanes * ctx->p.oversample * ctx->p.support;
+    ctx->dp.l0 = l0;
+    ctx->dp.m0 = m0;
+    ctx->dp.a2u = -0.5 * (1.0 / n0 + l0 * l0 / (n0 * n0 * n0));
+    ctx->dp.a2v = -0.5 * (1.0 / n0 + m0 * m0 / (n0 * n0 * n0));
+    return SEPW_OK;
+}
+
+int sepw_facet_shift(sepw_ctx *ctx, int direction, int64_t nvis, const double *u,
+                     const double *v, const double *w, const float *vis, double *u_out,
+                     double *v_out, float *vis_out, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    if (!ctx->dp.facet)
+        return fail(ctx, SEPW_ENOTSUP, "context not in facet mode");
+    if (direction != SEPW_FACET_IN && direction != SEPW_FACET_OUT)
+        return fail(ctx, SEPW_EINVAL, "bad facet direction %d", direction);
+    if (nvis < 0)
+        return fail(ctx, SEPW_EINVAL, "nvis < 0");
+    if (nvis == 0)
+        return SEPW_OK;
+    if ((u_out == nullptr) != (v_out == nullptr))
+        return fail(ctx, SEPW_EINVAL, "u_out and v_out must both be given or both NULL");
+    if ((vis == nullptr) != (vis_out == nullptr))
+        return fail(ctx, SEPW_EINVAL, "vis and vis_out must both be given or both NULL");
+    int rc;
+    if ((rc = check_dev(ctx, u, "u", false)) || (rc = check_dev(ctx, v, "v", false)) ||
+        (rc = check_dev(ctx, w, "w", false)) || (rc = check_dev(ctx, vis, "vis", true)) ||
+        (rc = check_dev(ctx, vis_out, "vis_out", true)) ||
+        (rc = check_dev(ctx, u_out, "u_out", true)) ||
+        (rc = check_dev(ctx, v_out, "v_out", true)))
+        return rc;
+    SEPW_CUDA(ctx, launch_facet_shift(nvis, ctx->dp.l0, ctx->dp.m0, direction, u, v, w,
+                                      (const float2 *)vis, u_out, v_out, (float2 *)vis_out,
+                                      (cudaStream_t)stream));
+    return SEPW_OK;
+}
+
 int sepw_wstack_plan(sepw_ctx *ctx, int32_t nslices, const double *w_centres, int64_t nvis,
                      const double *u, const double *v, const double *w, int32_t *slice_out,
                      sepw_stream_t stream)

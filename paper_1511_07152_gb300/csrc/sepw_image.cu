@@ -15,8 +15,10 @@
 namespace sepw {
 
 // mode: 0 = sign only, 1 = sign * n / (c_a c_b), 2 = sign / (n c_a c_b)
-__global__ void image_scale_kernel(int N, float fov_over_n, const float *__restrict__ taper,
-                                   float2 *buf, int mode)
+// (l0, m0): facet centre (Sec. 4.1), n is taken at the pixel's position
+// l0 + l, m0 + m in the original image plane
+__global__ void image_scale_kernel(int N, float fov_over_n, float l0, float m0,
+                                   const float *__restrict__ taper, float2 *buf, int mode)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
@@ -24,8 +26,8 @@ __global__ void image_scale_kernel(int N, float fov_over_n, const float *__restr
         return;
     float s = ((a + b) & 1) ? -1.f : 1.f;
     if (mode != 0) {
-        const float l = (float)(a - N / 2) * fov_over_n;
-        const float m = (float)(b - N / 2) * fov_over_n;
+        const float l = (float)(a - N / 2) * fov_over_n + l0;
+        const float m = (float)(b - N / 2) * fov_over_n + m0;
         const float n = sqrtf(1.f - (l * l + m * m));
         const float cc = taper[a] * taper[b];
         s = mode == 1 ? s * n / cc : s / (n * cc);
@@ -39,7 +41,8 @@ static cudaError_t scale(const DevParams &p, int mode, const float *taper, float
                          cudaStream_t s)
 {
     dim3 grid((p.N + 255) / 256, p.N);
-    image_scale_kernel<<<grid, 256, 0, s>>>(p.N, (float)(p.fov / p.N), taper, buf, mode);
+    image_scale_kernel<<<grid, 256, 0, s>>>(p.N, (float)(p.fov / p.N), (float)p.l0,
+                                            (float)p.m0, taper, buf, mode);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,14 @@ struct DevParams {
     double w_max;
     double gamma;
     double beta;
+    // image-plane faceting (Sec. 4.1): the v-direction taps sit voff elements
+    // after the u-direction ones (0: one table for both); the image step takes
+    // n at the facet's pixels (l0 + l, m0 + m); the facet tables use the
+    // screens exp(2 pi i w a2 l^2) with a2 = a2u (u table), a2v (v table)
+    int64_t voff = 0;
+    int32_t facet = 0;
+    double l0 = 0.0, m0 = 0.0;
+    double a2u = -0.5, a2v = -0.5;
 };
 
 // Result of locating one visibility.
@@ -276,6 +284,12 @@ cudaError_t launch_wstack_combine(const DevParams &p, int L, const float *taper,
                                   cudaStream_t s);
 cudaError_t launch_wstack_split(const DevParams &p, int L, const float *taper, const float *wc,
                                 const float2 *image, float2 *g, cudaStream_t s);
+
+// sepw_facet.cu (direction 0: into the facet, 1: back out)
+cudaError_t launch_facet_shift(int64_t nvis, double l0, double m0, int direction,
+                               const double *u, const double *v, const double *w,
+                               const float2 *vin, double *uo, double *vo, float2 *vout,
+                               cudaStream_t s);
 
 // sepw_image.cu
 cudaError_t launch_image_pre(const DevParams &p, int direction, const float *taper,

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) grid_plain_kernel(
     if (!L.keep)
         return;
     const float2 *tu = taps + ((int64_t)L.plane * p.OS + L.ou) * S;
-    const float2 *tv = taps + ((int64_t)L.plane * p.OS + L.ov) * S;
+    const float2 *tv = taps + p.voff + ((int64_t)L.plane * p.OS + L.ov) * S;
     float sg = L.conj ? -1.f : 1.f;
     float2 a = __ldg(tu + j);
     a.y *= sg;
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256) degrid_plain_kernel(
         Loc L = sloc[vs];
         if (L.keep) {
             const float2 *tu = taps + ((int64_t)L.plane * p.OS + L.ou) * S;
-            const float2 *tv = taps + ((int64_t)L.plane * p.OS + L.ov) * S;
+            const float2 *tv = taps + p.voff + ((int64_t)L.plane * p.OS + L.ov) * S;
             // conj of the gridding kernel: conj(tap) if w >= 0, tap if w < 0
             float sg = L.conj ? 1.f : -1.f;
             int64_t x = L.cu - S / 2 + 1 + j;

@@ -7,8 +7,9 @@
 // The DFT phase d*nu_a = k (a - N/2) / (N OS) with the integer k = d*OS, so it
 // is reduced exactly in integers and looked up in a table of N*OS twiddles
 // exp(-2 pi i m / (N OS)), each computed once with sincospi.  The screen
-// g1_w(l) = exp(2 pi i w (-l^2/2 - gamma l^4)) is evaluated once per pixel and
-// plane.  Off the hot path.
+// g1_w(l) = exp(2 pi i w (-l^2/2 - gamma l^4)) (or a facet screen of Eq.
+// gt-facet, Sec. 4.1) is evaluated once per pixel and plane.  Off the hot
+// path.
 #include "sepw_internal.cuh"
 
 namespace sepw {
@@ -59,13 +60,19 @@ constexpr int kTapsPerWarp = 4;
 constexpr int kTapsPerBlock = kTapWarps * kTapsPerWarp;
 constexpr int kPixChunk = 1024;
 
-// grid = (ceil(OS*S / 32), P); block = 256 threads.
+// grid = (ceil(OS*S / 32), P, tables); block = 256 threads.  Table 0 is the
+// u-direction table (the only one unless p.facet), table 1 the v-direction
+// table of a facet; the screen is exp(2 pi i w (a2 l^2 + a4 l^4)) with
+// (a2, a4) = (-1/2, -gamma) (Eq. gt) or (a2u or a2v, 0) (Eq. gt-facet).
 __global__ void __launch_bounds__(256) taps_kernel(DevParams p, const double *taper64,
                                                    const double2 *tw, double2 *out64,
                                                    float2 *out32)
 {
     __shared__ double2 h[kPixChunk];
     const int plane = blockIdx.y;
+    const int table = blockIdx.z;
+    const double a2 = p.facet ? (table ? p.a2v : p.a2u) : -0.5;
+    const double a4 = p.facet ? 0.0 : -p.gamma;
     const int ntap = p.OS * p.S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t M = (int64_t)p.N * p.OS;
@@ -93,7 +100,7 @@ __global__ void __launch_bounds__(256) taps_kernel(DevParams p, const double *ta
                 double nu = (double)(a - p.N / 2) / (double)p.N;
                 double l = nu * p.fov;
                 double l2 = l * l;
-                double turns = wp * (-0.5 * l2 - p.gamma * l2 * l2);
+                double turns = wp * (a2 * l2 + a4 * l2 * l2);
                 double s, c;
                 sincospi(2.0 * turns, &s, &c);
                 double t = taper64[a];
@@ -127,7 +134,7 @@ __global__ void __launch_bounds__(256) taps_kernel(DevParams p, const double *ta
         }
         if (lane == 0 && valid[q]) {
             int t = blockIdx.x * kTapsPerBlock + warp * kTapsPerWarp + q;
-            int64_t idx = (int64_t)plane * ntap + t;
+            int64_t idx = ((int64_t)table * p.P + plane) * ntap + t;
             double2 v = make_double2(re / (double)p.N, im / (double)p.N);
             if (out64)
                 out64[idx] = v;
@@ -154,7 +161,7 @@ cudaError_t launch_twiddles(const DevParams &p, double2 *tw, cudaStream_t s)
 cudaError_t launch_taps(const DevParams &p, const double *taper64, const double2 *tw,
                         double2 *out64, float2 *out32, cudaStream_t s)
 {
-    dim3 grid((p.OS * p.S + kTapsPerBlock - 1) / kTapsPerBlock, p.P);
+    dim3 grid((p.OS * p.S + kTapsPerBlock - 1) / kTapsPerBlock, p.P, p.facet ? 2 : 1);
     taps_kernel<<<grid, 256, 0, s>>>(p, taper64, tw, out64, out32);
     return cudaGetLastError();
 }

@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kTcBlock, 1) grid_tc_kernel(
                     cur.x = __ldg(vis + i);
                     cur.wt = weight ? __ldg(weight + i) : 1.0f;
                     const int row = rec_plane(r) * p.OS;
-                    const float2 *pv = taps + (row + rec_ov(r)) * S + q;
+                    const float2 *pv = taps + p.voff + (row + rec_ov(r)) * S + q;
                     const float2 *pu = taps + (row + rec_ou(r)) * S + q;
 #pragma unroll
                     for (int j = 0; j < NT; ++j) {

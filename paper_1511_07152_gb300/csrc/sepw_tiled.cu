@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_k
                     const float pr = wx * a.x - wy * a.y;
                     const float pi = wx * a.y + wy * a.x;
                     float tr[RPL], ti[RPL];
-                    load_vtaps<S>(tu + meta_dv(m.y), rg, tr, ti);
+                    load_vtaps<S>(tu + p.voff + meta_dv(m.y), rg, tr, ti);
 #pragma unroll
                     for (int k = 0; k < RPL; ++k) {
                         ar[k] = fmaf(pr, tr[k], ar[k]);
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) degrid_tiled
                         if (lane_ok) {
                             const float2 *tu = taps + m.x;
                             float tr[RPL], ti[RPL];
-                            load_vtaps<S>(tu + meta_dv(m.y), rg, tr, ti);
+                            load_vtaps<S>(tu + p.voff + meta_dv(m.y), rg, tr, ti);
                             float sr = 0.f, si = 0.f;
 #pragma unroll
                             for (int k = 0; k < RPL; ++k) {
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(kTiledThreads, Blk<S>::BPS) degrid_tiled_block
     int *const keys = reinterpret_cast<int *>(meta - (warp * 2 + vw) * MS + kTiledWarps * 2 * MS) +
                       (warp * 2 + vw) * MS;
     const float2 *const tcol = taps + cg;
-    const float2 *const trow = taps + rg;
+    const float2 *const trow = taps + p.voff + rg;
     const int n_items = *nitems;
     // this lane's first window cell relative to the footprint origin
     const float2 *const lwin = win + rg * WP + cg;
@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_b
     int *const keys = s_key + warp * 32;
     // this lane's u-tap column and v-tap row within a table row
     const float2 *const tcol = taps + cg;
-    const float2 *const trow = taps + rg;
+    const float2 *const trow = taps + p.voff + rg;
     const int n_items = *nitems;
 
     for (;;) {

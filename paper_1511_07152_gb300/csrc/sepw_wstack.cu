@@ -170,11 +170,13 @@ cudaError_t launch_wstack_compose(int64_t nvis, const Plan &plan, const int32_t 
 }
 
 // n - 1 without cancellation, and the grid correction factors of pixel (a, b)
-__device__ __forceinline__ void pixel_terms(int N, float fov_over_n, const float *taper, int a,
-                                            int b, float &nm1, float &n, float &cc)
+// (at l0 + l, m0 + m for a facet centred at (l0, m0))
+__device__ __forceinline__ void pixel_terms(int N, float fov_over_n, float l0, float m0,
+                                            const float *taper, int a, int b, float &nm1,
+                                            float &n, float &cc)
 {
-    const float l = (float)(a - N / 2) * fov_over_n;
-    const float m = (float)(b - N / 2) * fov_over_n;
+    const float l = (float)(a - N / 2) * fov_over_n + l0;
+    const float m = (float)(b - N / 2) * fov_over_n + m0;
     const float r2 = l * l + m * m;
     n = sqrtf(1.f - r2);
     nm1 = -r2 / (1.f + n);
@@ -209,7 +211,8 @@ __global__ void wstack_sign_kernel(int N, int L, float2 *g)
 }
 
 // image = sum_c sign n / (c c) exp(2 pi i w_c (n - 1)) IDFT(grid_c)
-__global__ void wstack_combine_kernel(int N, int L, float fov_over_n, const float *taper,
+__global__ void wstack_combine_kernel(int N, int L, float fov_over_n, float l0, float m0,
+                                      const float *taper,
                                       const float *__restrict__ wc, const float2 *__restrict__ g,
                                       float2 *__restrict__ image)
 {
@@ -218,7 +221,7 @@ __global__ void wstack_combine_kernel(int N, int L, float fov_over_n, const floa
     if (a >= N)
         return;
     float nm1, n, cc;
-    pixel_terms(N, fov_over_n, taper, a, b, nm1, n, cc);
+    pixel_terms(N, fov_over_n, l0, m0, taper, a, b, nm1, n, cc);
     const float s = (((a + b) & 1) ? -1.f : 1.f) * n / cc;
     const int64_t n2 = (int64_t)N * N, idx = (int64_t)b * N + a;
     float re = 0.f, im = 0.f;
@@ -232,7 +235,8 @@ __global__ void wstack_combine_kernel(int N, int L, float fov_over_n, const floa
 }
 
 // grid_c (before the forward DFT) = sign / (n c c) exp(-2 pi i w_c (n - 1)) image
-__global__ void wstack_split_kernel(int N, int L, float fov_over_n, const float *taper,
+__global__ void wstack_split_kernel(int N, int L, float fov_over_n, float l0, float m0,
+                                    const float *taper,
                                     const float *__restrict__ wc,
                                     const float2 *__restrict__ image, float2 *__restrict__ g)
 {
@@ -241,7 +245,7 @@ __global__ void wstack_split_kernel(int N, int L, float fov_over_n, const float 
     if (a >= N)
         return;
     float nm1, n, cc;
-    pixel_terms(N, fov_over_n, taper, a, b, nm1, n, cc);
+    pixel_terms(N, fov_over_n, l0, m0, taper, a, b, nm1, n, cc);
     const float s = (((a + b) & 1) ? -1.f : 1.f) / (n * cc);
     const int64_t n2 = (int64_t)N * N, idx = (int64_t)b * N + a;
     const float2 x = image[idx];
@@ -263,8 +267,8 @@ cudaError_t launch_wstack_combine(const DevParams &p, int L, const float *taper,
                                   cudaStream_t s)
 {
     dim3 grid((p.N + 255) / 256, p.N);
-    wstack_combine_kernel<<<grid, 256, 0, s>>>(p.N, L, (float)(p.fov / p.N), taper, wc, g,
-                                               image);
+    wstack_combine_kernel<<<grid, 256, 0, s>>>(p.N, L, (float)(p.fov / p.N), (float)p.l0,
+                                               (float)p.m0, taper, wc, g, image);
     return cudaGetLastError();
 }
 
@@ -272,8 +276,8 @@ cudaError_t launch_wstack_split(const DevParams &p, int L, const float *taper, c
                                 const float2 *image, float2 *g, cudaStream_t s)
 {
     dim3 grid((p.N + 255) / 256, p.N);
-    wstack_split_kernel<<<grid, 256, 0, s>>>(p.N, L, (float)(p.fov / p.N), taper, wc, image,
-                                             g);
+    wstack_split_kernel<<<grid, 256, 0, s>>>(p.N, L, (float)(p.fov / p.N), (float)p.l0,
+                                             (float)p.m0, taper, wc, image, g);
     return cudaGetLastError();
 }
 

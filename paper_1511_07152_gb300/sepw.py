@@ -86,6 +86,9 @@ _SIG = {
     "sepw_grid_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _P, _I64, _P, _P, _P, _P,
                                          _P, _P, _P, _P]),
     "sepw_taper": (ctypes.c_int, [_P, _P, _P]),
+    "sepw_set_facet": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+    "sepw_facet_shift": (ctypes.c_int, [_P, ctypes.c_int, _I64, _P, _P, _P, _P, _P, _P, _P,
+                                        _P]),
     "sepw_wstack_plan": (ctypes.c_int, [_P, ctypes.c_int32, _P, _I64, _P, _P, _P, _P, _P]),
     "sepw_wstack_image": (ctypes.c_int, [_P, _P, _P, _P]),
     "sepw_wstack_model_grids": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -155,6 +158,7 @@ class Context:
         self.plan_nvis = 0
         self.plan_ngrids = 0
         self.wstack_nslices = 0
+        self.facet = None  # (l0, m0) in facet mode
 
     def close(self):
         if getattr(self, "handle", None):
@@ -174,12 +178,14 @@ class Context:
 
     @property
     def ntaps(self) -> int:
-        return int(LIB.sepw_taps_count(ctypes.byref(self.params)))
+        n = int(LIB.sepw_taps_count(ctypes.byref(self.params)))
+        return 2 * n if getattr(self, "facet", None) else n
 
     @property
     def taps_shape(self):
         p = self.params
-        return (p.n_wplanes, p.oversample, p.support)
+        shape = (p.n_wplanes, p.oversample, p.support)
+        return (2,) + shape if getattr(self, "facet", None) else shape
 
 
 # ---- entry points (same names as the C ABI) ---------------------------------
@@ -368,6 +374,36 @@ def sepw_image(ctx: Context, direction: int, buf, stream=None):
     ctx.check(LIB.sepw_image(ctx.handle, int(direction),
                              _ptr(buf, torch.complex64, N * N, "buf"), _stream(stream)))
     return buf
+
+
+FACET_IN, FACET_OUT = 0, 1
+
+
+def sepw_set_facet(ctx: Context, l0=None, m0=None):
+    """Facet mode for the facet centred at (l0, m0) (Sec. 4.1); None leaves
+    it.  In facet mode the taps are two tables [2, P, OS, S]."""
+    if l0 is None:
+        ctx.check(LIB.sepw_set_facet(ctx.handle, 0, 0.0, 0.0))
+        ctx.facet = None
+    else:
+        ctx.check(LIB.sepw_set_facet(ctx.handle, 1, float(l0), float(m0)))
+        ctx.facet = (float(l0), float(m0))
+
+
+def sepw_facet_shift(ctx: Context, direction, u, v, w, vis=None, u_out=None, v_out=None,
+                     vis_out=None, stream=None):
+    """Visibilities into (FACET_IN) or out of (FACET_OUT) the context's facet."""
+    import torch
+    n = u.numel()
+    ctx.check(LIB.sepw_facet_shift(ctx.handle, int(direction), n,
+                                   _ptr(u, torch.float64, n, "u"),
+                                   _ptr(v, torch.float64, n, "v"),
+                                   _ptr(w, torch.float64, n, "w"),
+                                   _ptr(vis, torch.complex64, n, "vis"),
+                                   _ptr(u_out, torch.float64, n, "u_out"),
+                                   _ptr(v_out, torch.float64, n, "v_out"),
+                                   _ptr(vis_out, torch.complex64, n, "vis_out"),
+                                   _stream(stream)))
 
 
 def sepw_taper(ctx: Context, out=None, stream=None):
