@@ -161,3 +161,71 @@ void oracle_grid_exact2d(int64_t nvis, int32_t N, int32_t S, int32_t OS,
         }
     }
 }
+
+/*
+ * Correction pass with the stored correction F_w - F~_w (Sec. 7: the exact
+ * kernel minus the separable one, kept in a full 2-D table).  The table holds
+ * Sr x Sr values for the central footprint cells (first one at column / row
+ * k0 = (S - Sr) / 2 of the S x S footprint) at OSr oversample offsets per
+ * axis: fine offset o uses the coarse entry o / (OS / OSr).  Layout
+ * res[plane][ov][ou][k][j].  Gridding adds W V R (conj(R) for w < 0);
+ * degridding is its exact adjoint and ADDS W sum conj(kernel) X to vis_out.
+ */
+void oracle_grid_residual(int64_t nvis, int32_t N, int32_t S, int32_t OS, int32_t Sr,
+                          int32_t OSr, const int32_t *cu, const int32_t *cv,
+                          const int32_t *ou, const int32_t *ov, const int32_t *plane,
+                          const uint8_t *conj, const uint8_t *keep, const double *vis,
+                          const double *weight, const double *res, double *grid)
+{
+    const int32_t step = OS / OSr, k0 = (S - Sr) / 2;
+    for (int64_t i = 0; i < nvis; ++i) {
+        if (!keep[i])
+            continue;
+        double wgt = weight ? weight[i] : 1.0;
+        double vr = wgt * vis[2 * i], vi = wgt * vis[2 * i + 1];
+        double sgn = conj[i] ? -1.0 : 1.0;
+        const double *R = res + 2 * ((((int64_t)plane[i] * OSr + ov[i] / step) * OSr +
+                                      ou[i] / step) * Sr * Sr);
+        for (int k = 0; k < Sr; ++k) {
+            int64_t y = (int64_t)cv[i] - S / 2 + 1 + k0 + k;
+            for (int j = 0; j < Sr; ++j) {
+                int64_t x = (int64_t)cu[i] - S / 2 + 1 + k0 + j;
+                double rr = R[2 * (k * Sr + j)], ri = sgn * R[2 * (k * Sr + j) + 1];
+                double *g = grid + 2 * (y * N + x);
+                g[0] += vr * rr - vi * ri;
+                g[1] += vr * ri + vi * rr;
+            }
+        }
+    }
+}
+
+void oracle_degrid_residual(int64_t nvis, int32_t N, int32_t S, int32_t OS, int32_t Sr,
+                            int32_t OSr, const int32_t *cu, const int32_t *cv,
+                            const int32_t *ou, const int32_t *ov, const int32_t *plane,
+                            const uint8_t *conj, const uint8_t *keep, const double *grid,
+                            const double *weight, const double *res, double *vis_out)
+{
+    const int32_t step = OS / OSr, k0 = (S - Sr) / 2;
+    for (int64_t i = 0; i < nvis; ++i) {
+        if (!keep[i])
+            continue;
+        double sgn = conj[i] ? -1.0 : 1.0;
+        const double *R = res + 2 * ((((int64_t)plane[i] * OSr + ov[i] / step) * OSr +
+                                      ou[i] / step) * Sr * Sr);
+        double ar = 0.0, ai = 0.0;
+        for (int k = 0; k < Sr; ++k) {
+            int64_t y = (int64_t)cv[i] - S / 2 + 1 + k0 + k;
+            for (int j = 0; j < Sr; ++j) {
+                int64_t x = (int64_t)cu[i] - S / 2 + 1 + k0 + j;
+                /* conj of the kernel used for gridding */
+                double rr = R[2 * (k * Sr + j)], ri = -sgn * R[2 * (k * Sr + j) + 1];
+                const double *g = grid + 2 * (y * N + x);
+                ar += rr * g[0] - ri * g[1];
+                ai += rr * g[1] + ri * g[0];
+            }
+        }
+        double wgt = weight ? weight[i] : 1.0;
+        vis_out[2 * i] += wgt * ar;
+        vis_out[2 * i + 1] += wgt * ai;
+    }
+}

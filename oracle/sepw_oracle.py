@@ -285,8 +285,13 @@ def _clib():
                                                          ctypes.c_void_p, ctypes.c_int32, _F64]
         lib.oracle_grid_exact2d.argtypes = common + [_F64, ctypes.c_void_p, _F64,
                                                      ctypes.c_int32, _F64]
+        rcommon = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                   ctypes.c_int32, ctypes.c_int32, _I32, _I32, _I32, _I32, _I32, _U8, _U8]
+        lib.oracle_grid_residual.argtypes = rcommon + [_F64, ctypes.c_void_p, _F64, _F64]
+        lib.oracle_degrid_residual.argtypes = rcommon + [_F64, ctypes.c_void_p, _F64, _F64]
         for f in (lib.oracle_grid_separable, lib.oracle_degrid_separable,
-                  lib.oracle_grid_exact2d):
+                  lib.oracle_grid_exact2d, lib.oracle_grid_residual,
+                  lib.oracle_degrid_residual):
             f.restype = None
         _LIB = lib
     return _LIB
@@ -357,6 +362,60 @@ def grid_exact2d(p: Params, loc: dict, vis, weight, K, wrap=False):
                                 _c128(K).reshape(-1), int(wrap),
                                 grid.view(np.float64).reshape(-1))
     return grid
+
+
+def residual_table(p: Params, Sr: int = None, OSr: int = None, K=None, T=None):
+    """Stored correction of the separable kernel (Sec. 7: store and apply
+    F_w - F~_w in a small full-dimension table):
+        R[p][ov][ou][k][j] = F_w(d_u, d_v) - F1_w(d_u) F1_w(d_v)
+    with F_w the exact 2-D kernel of exact_table and F1 the taps, on the Sr x Sr
+    central footprint cells (first at k0 = (S - Sr)/2) and every
+    (OS / OSr)-th oversample offset per axis.
+
+    Reading (the paper leaves the table's support and sampling open): the
+    truncated table keeps the central cells, and a visibility at fine offset o
+    uses the coarse entry floor(o / (OS / OSr)).  Sr = S, OSr = OS gives the
+    exact kernel back when added to the separable one."""
+    S, OS = p.S, p.OS
+    Sr = S if Sr is None else Sr
+    OSr = OS if OSr is None else OSr
+    if Sr < 1 or Sr > S or (S - Sr) % 2 or OSr < 1 or OS % OSr:
+        raise ValueError("need 1 <= Sr <= S, S - Sr even, OSr dividing OS")
+    K = exact_table(p) if K is None else K
+    T = taps(p) if T is None else T
+    full = K - T[:, :, None, :, None] * T[:, None, :, None, :]
+    step, k0 = OS // OSr, (S - Sr) // 2
+    return np.ascontiguousarray(full[:, ::step, ::step, k0:k0 + Sr, k0:k0 + Sr])
+
+
+def _res_dims(p: Params, R):
+    return int(R.shape[3]), int(R.shape[1])
+
+
+def grid_residual(p: Params, loc: dict, vis, weight, R, grid=None):
+    """Correction pass of residual_table's correction, FP64: adds to grid."""
+    n = len(loc["keep"])
+    Sr, OSr = _res_dims(p, R)
+    if grid is None:
+        grid = np.zeros((p.N, p.N), np.complex128)
+    wt, wptr = _weight_arg(weight, n)
+    _clib().oracle_grid_residual(n, p.N, p.S, p.OS, Sr, OSr, *_loc_args(loc), _c128(vis),
+                                 wptr, _c128(R).reshape(-1),
+                                 grid.view(np.float64).reshape(-1))
+    return grid
+
+
+def degrid_residual(p: Params, loc: dict, grid, weight, R, out=None):
+    """Adjoint of grid_residual, FP64: adds to out (zeros if None)."""
+    n = len(loc["keep"])
+    Sr, OSr = _res_dims(p, R)
+    if out is None:
+        out = np.zeros(n, np.complex128)
+    wt, wptr = _weight_arg(weight, n)
+    _clib().oracle_degrid_residual(n, p.N, p.S, p.OS, Sr, OSr, *_loc_args(loc),
+                                   _c128(grid).reshape(-1), wptr, _c128(R).reshape(-1),
+                                   out.view(np.float64))
+    return out
 
 
 def grid(p: Params, u, v, w, vis, weight=None, T=None):
