@@ -428,6 +428,49 @@ def run_major_cycles(S, torch, args):
                     "initial prediction and adjoint (one extra half cycle)"}
 
 
+def run_correction(S, torch, args):
+    """Stored correction F_w - F~_w (Sec. 7) on workload 4 (2048^2, ~4M
+    visibilities, support 16, oversampling 16, 64 planes): table build (once,
+    float64) and the correction pass after the separable gridding, for the
+    full table and for an 8 x 8, 8-offset one."""
+    import synth
+    _, wl = synth.point_source_model()
+    ctx = S.sepw_create(S.make_params(**wl.params(), form=S.FORM_TILED))
+    taps = S.sepw_make_taps(ctx)
+    d = {k: torch.from_numpy(getattr(wl, k)).cuda() for k in ("u", "v", "w", "vis", "weight")}
+    S.sepw_plan(ctx, d["u"], d["v"], d["w"])
+    N = wl.grid_size
+    grid = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    out = {"workload": wl.name, "nvis": wl.nvis, "grid": N, "support": wl.support}
+    for Sr, OSr in ((wl.support, wl.oversample), (8, 8)):
+        t0 = time.perf_counter()
+        table = S.sepw_make_residual(ctx, Sr, OSr)
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        sep, cor = [], []
+        for k in range(max(3, args.steps // 2) + 2):
+            e = [E() for _ in range(3)]
+            grid.zero_()
+            e[0].record()
+            S.sepw_grid_planned(ctx, taps, d["vis"], d["weight"], grid)
+            e[1].record()
+            S.sepw_grid_residual_planned(ctx, table, d["vis"], d["weight"], grid)
+            e[2].record()
+            torch.cuda.synchronize()
+            if k >= 2:
+                sep.append(e[0].elapsed_time(e[1]))
+                cor.append(e[1].elapsed_time(e[2]))
+        out[f"table_{Sr}x{Sr}_os{OSr}"] = {
+            "build_s": build_s, "table_mib": table.numel() * 8 / 2 ** 20,
+            "separable_grid_ms": statistics.median(sep),
+            "correction_pass_ms": statistics.median(cor)}
+        del table
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -588,6 +631,9 @@ def run_ours(args):
     cycles = None
     if rank == 0 and not args.skip_autograd:
         cycles = run_major_cycles(S, torch, args)
+    correction = None
+    if rank == 0 and not args.skip_correction:
+        correction = run_correction(S, torch, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
@@ -612,7 +658,7 @@ def run_ours(args):
             "grid_updates_per_s": nkept * Ssup * Ssup * 2 * ws / (ms * 1e-3),
             "speedup_vs_plain_fp32": (plain["ms_per_step"] / ms) if plain else None,
             "forms": forms, "batched": batched, "predict_autograd": predict,
-            "wstack": wstack, "major_cycles": cycles,
+            "wstack": wstack, "major_cycles": cycles, "correction": correction,
             "roofline": roofline, "roofline_hbm": roofline_hbm, "peak_source": peak_src,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "wall_s_timed": time.perf_counter() - t_start,
@@ -646,6 +692,7 @@ def main():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-autograd", action="store_true")
     ap.add_argument("--skip-wstack", action="store_true")
+    ap.add_argument("--skip-correction", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -243,6 +243,43 @@ SEPW_API int sepw_image(sepw_ctx *ctx, int direction, float *buf, sepw_stream_t 
  * used by sepw_image (FP32, device, N floats, overwritten). */
 SEPW_API int sepw_taper(sepw_ctx *ctx, float *taper, sepw_stream_t stream);
 
+/* Stored correction of the separable kernel, Sec. 7 (store and apply
+ * F_w - F~_w in a small full-dimension table).  The table holds
+ *   res[p][ovr][our][k][j] = F_w(d_u, d_v) - F1_w(d_u) F1_w(d_v)
+ * (F_w the exact 2-D W-projection kernel, the transform of
+ * c1 c1 exp(2 pi i w (n - 1)) over the N x N pixels; F1 the taps of
+ * sepw_make_taps) for the support_r x support_r central cells of the S x S
+ * footprint (first at (S - support_r)/2) and oversample_r offsets per axis
+ * (entry c stands for the fine offset c * OS / oversample_r; a visibility at
+ * fine offset o uses entry floor(o / (OS / oversample_r))).  Constraints:
+ * 1 <= support_r <= S, S - support_r even, oversample_r divides OS.
+ * sepw_residual_count: number of complex entries,
+ *   P * oversample_r^2 * support_r^2 (0 for invalid sizes).
+ * sepw_make_residual / _f64: build it in float64 on the GPU (complex64 /
+ * complex128 output, device).  Not in facet mode (SEPW_ENOTSUP).  Allocates
+ * and frees a temporary of P * oversample_r * support_r * N complex128 and
+ * synchronises `stream`: a set-up step, not for the hot loop.
+ * sepw_grid_residual_planned: the correction pass, ADDS to grid the
+ * W_i V_i res (conj(res) for w_i < 0) of every planned visibility; after
+ * sepw_grid_planned with the full table (support_r = S, oversample_r = OS)
+ * the grid is that of exact 2-D W projection.
+ * sepw_degrid_residual_planned: its adjoint, ADDS to vis_out (after
+ * sepw_degrid_planned).  Both need a tiled or tensor-core plan (SEPW_ENOTSUP
+ * for SEPW_FORM_PLAIN), including batched and W-stacking plans. */
+SEPW_API size_t sepw_residual_count(const sepw_params *p, int32_t support_r,
+                                    int32_t oversample_r);
+SEPW_API int sepw_make_residual(sepw_ctx *ctx, int32_t support_r, int32_t oversample_r,
+                                float *table, sepw_stream_t stream);
+SEPW_API int sepw_make_residual_f64(sepw_ctx *ctx, int32_t support_r, int32_t oversample_r,
+                                    double *table, sepw_stream_t stream);
+SEPW_API int sepw_grid_residual_planned(sepw_ctx *ctx, int32_t support_r, int32_t oversample_r,
+                                        const float *table, const float *vis,
+                                        const float *weight, float *grid, sepw_stream_t stream);
+SEPW_API int sepw_degrid_residual_planned(sepw_ctx *ctx, int32_t support_r,
+                                          int32_t oversample_r, const float *table,
+                                          const float *grid, const float *weight,
+                                          float *vis_out, sepw_stream_t stream);
+
 /* Image-plane faceting, Sec. 4.1 (Eq. gt-facet).  sepw_set_facet puts the
  * context in facet mode for the facet centred at (l0, m0) (direction cosines
  * of the original image plane, l0^2 + m0^2 < 1; the context's grid_size and

@@ -657,6 +657,127 @@ int sepw_taper(sepw_ctx *ctx, float *taper, sepw_stream_t stream)
     return SEPW_OK;
 }
 
+static bool residual_sizes_ok(const sepw_params *p, int32_t Sr, int32_t OSr)
+{
+    return Sr >= 1 && Sr <= p->support && (p->support - Sr) % 2 == 0 && OSr >= 1 &&
+           p->oversample % OSr == 0;
+}
+
+size_t sepw_residual_count(const sepw_params *p, int32_t support_r, int32_t oversample_r)
+{
+    if (!p || sepw_check_params(p) != SEPW_OK || !residual_sizes_ok(p, support_r, oversample_r))
+        return 0;
+    return (size_t)p->n_wplanes * oversample_r * oversample_r * support_r * support_r;
+}
+
+static int make_residual(sepw_ctx *ctx, int32_t Sr, int32_t OSr, double2 *out64,
+                         float2 *out32, cudaStream_t s)
+{
+    if (!residual_sizes_ok(&ctx->p, Sr, OSr))
+        return fail(ctx, SEPW_EINVAL, "need 1 <= support_r <= S, S - support_r even, "
+                                      "oversample_r dividing OS");
+    if (ctx->dp.facet)
+        return fail(ctx, SEPW_ENOTSUP, "correction table not available in facet mode");
+    const DevParams &p = ctx->dp;
+    double2 *X = nullptr, *t64 = nullptr;
+    const size_t nx = (size_t)p.P * OSr * Sr * p.N, nt = (size_t)p.P * p.OS * p.S;
+    int rc;
+    if ((rc = grow(ctx, &X, nx)) || (rc = grow(ctx, &t64, nt))) {
+        cudaFree(X);
+        cudaFree(t64);
+        return rc;
+    }
+    cudaError_t e = launch_taps(p, ctx->d_taper64, ctx->d_tw, t64, nullptr, s);
+    if (e == cudaSuccess)
+        e = launch_residual_table(p, Sr, OSr, ctx->d_taper64, ctx->d_tw, t64, X, out64, out32,
+                                  s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    cudaFree(X);
+    cudaFree(t64);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "correction table");
+    return SEPW_OK;
+}
+
+int sepw_make_residual(sepw_ctx *ctx, int32_t support_r, int32_t oversample_r, float *table,
+                       sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    int rc = check_dev(ctx, table, "table", false);
+    if (rc)
+        return rc;
+    return make_residual(ctx, support_r, oversample_r, nullptr, (float2 *)table,
+                         (cudaStream_t)stream);
+}
+
+int sepw_make_residual_f64(sepw_ctx *ctx, int32_t support_r, int32_t oversample_r,
+                           double *table, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    int rc = check_dev(ctx, table, "table", false);
+    if (rc)
+        return rc;
+    return make_residual(ctx, support_r, oversample_r, (double2 *)table, nullptr,
+                         (cudaStream_t)stream);
+}
+
+static int residual_pass_check(sepw_ctx *ctx, int32_t Sr, int32_t OSr, const float *table)
+{
+    if (!ctx->plan.valid)
+        return fail(ctx, SEPW_ENOPLAN, "no plan");
+    if (ctx->plan.form == SEPW_FORM_PLAIN)
+        return fail(ctx, SEPW_ENOTSUP, "the correction pass needs a tiled or tensor-core plan");
+    if (!residual_sizes_ok(&ctx->p, Sr, OSr))
+        return fail(ctx, SEPW_EINVAL, "need 1 <= support_r <= S, S - support_r even, "
+                                      "oversample_r dividing OS");
+    return check_dev(ctx, table, "table", false);
+}
+
+int sepw_grid_residual_planned(sepw_ctx *ctx, int32_t support_r, int32_t oversample_r,
+                               const float *table, const float *vis, const float *weight,
+                               float *grid, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    int rc;
+    if ((rc = residual_pass_check(ctx, support_r, oversample_r, table)) ||
+        (rc = check_dev(ctx, grid, "grid", false)))
+        return rc;
+    if (ctx->plan.nvis == 0)
+        return SEPW_OK;
+    if ((rc = check_dev(ctx, vis, "vis", false)) || (rc = check_dev(ctx, weight, "weight", true)))
+        return rc;
+    SEPW_CUDA(ctx, launch_grid_residual(ctx->dp, support_r, oversample_r, ctx->plan,
+                                        (const float2 *)vis, weight, (const float2 *)table,
+                                        (float2 *)grid, ctx->num_sms, (cudaStream_t)stream));
+    return SEPW_OK;
+}
+
+int sepw_degrid_residual_planned(sepw_ctx *ctx, int32_t support_r, int32_t oversample_r,
+                                 const float *table, const float *grid, const float *weight,
+                                 float *vis_out, sepw_stream_t stream)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    int rc;
+    if ((rc = residual_pass_check(ctx, support_r, oversample_r, table)) ||
+        (rc = check_dev(ctx, grid, "grid", false)))
+        return rc;
+    if (ctx->plan.nvis == 0)
+        return SEPW_OK;
+    if ((rc = check_dev(ctx, vis_out, "vis_out", false)) ||
+        (rc = check_dev(ctx, weight, "weight", true)))
+        return rc;
+    SEPW_CUDA(ctx, launch_degrid_residual(ctx->dp, support_r, oversample_r, ctx->plan,
+                                          (const float2 *)grid, weight, (const float2 *)table,
+                                          (float2 *)vis_out, ctx->num_sms,
+                                          (cudaStream_t)stream));
+    return SEPW_OK;
+}
+
 int sepw_set_facet(sepw_ctx *ctx, int enable, double l0, double m0)
 {
     if (!ctx)

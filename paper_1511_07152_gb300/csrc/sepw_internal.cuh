@@ -291,6 +291,17 @@ cudaError_t launch_facet_shift(int64_t nvis, double l0, double m0, int direction
                                const float2 *vin, double *uo, double *vo, float2 *vout,
                                cudaStream_t s);
 
+// sepw_residual.cu (stored correction F_w - F~_w)
+cudaError_t launch_residual_table(const DevParams &p, int Sr, int OSr, const double *taper64,
+                                  const double2 *tw, const double2 *taps64, double2 *X,
+                                  double2 *out64, float2 *out32, cudaStream_t s);
+cudaError_t launch_grid_residual(const DevParams &p, int Sr, int OSr, const Plan &plan,
+                                 const float2 *vis, const float *weight, const float2 *res,
+                                 float2 *grid, int num_sms, cudaStream_t s);
+cudaError_t launch_degrid_residual(const DevParams &p, int Sr, int OSr, const Plan &plan,
+                                   const float2 *grid, const float *weight, const float2 *res,
+                                   float2 *vis_out, int num_sms, cudaStream_t s);
+
 // sepw_image.cu
 cudaError_t launch_image_pre(const DevParams &p, int direction, const float *taper,
                              float2 *buf, cudaStream_t s);

@@ -86,6 +86,14 @@ _SIG = {
     "sepw_grid_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _P, _I64, _P, _P, _P, _P,
                                          _P, _P, _P, _P]),
     "sepw_taper": (ctypes.c_int, [_P, _P, _P]),
+    "sepw_residual_count": (ctypes.c_size_t, [ctypes.POINTER(Params), ctypes.c_int32,
+                                              ctypes.c_int32]),
+    "sepw_make_residual": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "sepw_make_residual_f64": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "sepw_grid_residual_planned": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                                  _P, _P, _P]),
+    "sepw_degrid_residual_planned": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P,
+                                                    _P, _P, _P, _P]),
     "sepw_set_facet": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
     "sepw_facet_shift": (ctypes.c_int, [_P, ctypes.c_int, _I64, _P, _P, _P, _P, _P, _P, _P,
                                         _P]),
@@ -374,6 +382,63 @@ def sepw_image(ctx: Context, direction: int, buf, stream=None):
     ctx.check(LIB.sepw_image(ctx.handle, int(direction),
                              _ptr(buf, torch.complex64, N * N, "buf"), _stream(stream)))
     return buf
+
+
+def _residual_shape(ctx: Context, support_r, oversample_r):
+    p = ctx.params
+    n = int(LIB.sepw_residual_count(ctypes.byref(p), int(support_r), int(oversample_r)))
+    if n == 0:
+        raise SepwError(EINVAL, "invalid correction table sizes")
+    return (p.n_wplanes, oversample_r, oversample_r, support_r, support_r), n
+
+
+def sepw_make_residual(ctx: Context, support_r, oversample_r, table=None, stream=None):
+    """Correction table F_w - F~_w, complex64 [P, OSr, OSr, Sr, Sr] (Sec. 7)."""
+    import torch
+    shape, n = _residual_shape(ctx, support_r, oversample_r)
+    if table is None:
+        table = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    ctx.check(LIB.sepw_make_residual(ctx.handle, int(support_r), int(oversample_r),
+                                     _ptr(table, torch.complex64, n, "table"), _stream(stream)))
+    return table
+
+
+def sepw_make_residual_f64(ctx: Context, support_r, oversample_r, table=None, stream=None):
+    import torch
+    shape, n = _residual_shape(ctx, support_r, oversample_r)
+    if table is None:
+        table = torch.empty(shape, dtype=torch.complex128, device="cuda")
+    ctx.check(LIB.sepw_make_residual_f64(ctx.handle, int(support_r), int(oversample_r),
+                                         _ptr(table, torch.complex128, n, "table"),
+                                         _stream(stream)))
+    return table
+
+
+def sepw_grid_residual_planned(ctx: Context, table, vis, weight, grid, stream=None):
+    """Correction pass: adds the correction table's update to grid."""
+    import torch
+    Sr, OSr = int(table.shape[-1]), int(table.shape[1])
+    N = ctx.params.grid_size
+    n = ctx.plan_nvis
+    ctx.check(LIB.sepw_grid_residual_planned(
+        ctx.handle, Sr, OSr, _ptr(table, torch.complex64, table.numel(), "table"),
+        _ptr(vis, torch.complex64, n, "vis"), _ptr(weight, torch.float32, n, "weight"),
+        _ptr(grid, torch.complex64, ctx.plan_ngrids * N * N, "grid"), _stream(stream)))
+    return grid
+
+
+def sepw_degrid_residual_planned(ctx: Context, table, grid, weight, vis_out, stream=None):
+    """Adjoint of the correction pass: adds to vis_out."""
+    import torch
+    Sr, OSr = int(table.shape[-1]), int(table.shape[1])
+    N = ctx.params.grid_size
+    n = ctx.plan_nvis
+    ctx.check(LIB.sepw_degrid_residual_planned(
+        ctx.handle, Sr, OSr, _ptr(table, torch.complex64, table.numel(), "table"),
+        _ptr(grid, torch.complex64, ctx.plan_ngrids * N * N, "grid"),
+        _ptr(weight, torch.float32, n, "weight"), _ptr(vis_out, torch.complex64, n, "vis_out"),
+        _stream(stream)))
+    return vis_out
 
 
 FACET_IN, FACET_OUT = 0, 1
