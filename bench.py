@@ -515,7 +515,8 @@ def run_ours(args):
                             "phases_ms": {"plan": plan_ms, "grid": grid_ms,
                                           "degrid": degrid_ms}}}
 
-    # ---- tensor-core contraction forms (grid on tcgen05, degrid tiled FP32) ----
+    # ---- tensor-core contraction forms (grid on tcgen05; degrid on tcgen05 for
+    # bf16 / fp16, tiled FP32 for the hi + lo form) ----
     peaks, peak_src = _peaks()
     if not args.skip_tc:
         for name, form, nprod in (("tc_bf16", S.FORM_TC_BF16, 1),
@@ -540,6 +541,17 @@ def run_ours(args):
                                "note": "dense MMA flops executed (2 x 128 x 64 x 2 per vis "
                                        "per product) over the grid kernel; burst bf16 peak "
                                        "(fp16 same)"}}
+            if nprod == 1:
+                # degridding: one M128 x N128 x K128 product per 128 visibilities
+                # of a work item (Q = conj(Av) X over the item's window)
+                dg_flops = 2 * 128 * 128 * nkept
+                forms[name]["degrid_tensor_roofline"] = {
+                    "bound": "tensor", "unit": "TFLOP/s",
+                    "achieved": dg_flops / (fd * 1e-3) / 1e12,
+                    "peak": float(peaks["bf16_tflops"]),
+                    "frac": dg_flops / (fd * 1e-3) / 1e12 / float(peaks["bf16_tflops"]),
+                    "note": "dense MMA flops per kept visibility (2 x 128 x 128; "
+                            "ragged stages not counted) over the degrid kernel"}
             c2.close()
 
     # ---- plain FP32 form on the same data (the comparator) ----

@@ -69,12 +69,20 @@ extern "C" {
 #define SEPW_FORM_TILED 1  /* binned tiles, register/shared accumulation, FP32 */
 #define SEPW_FORM_TC_BF16 2 /* tile contraction on tensor cores (tcgen05): BF16
                                operands, FP32 accumulation; support <= 16.
-                               Degridding uses the tiled FP32 form. */
+                               Degridding is the contraction form too:
+                               Q = conj(Av) X per window, then the
+                               u-direction dot product per visibility. */
 #define SEPW_FORM_TC_FP16 3 /* as SEPW_FORM_TC_BF16 with FP16 operands, scaled per
-                               work item by a power of two (FP16 range) */
+                               work item by a power of two (FP16 range).
+                               Degridding errs relative to the model grid's
+                               magnitude (11-bit operands), not the
+                               prediction's: a grid dominated by content the
+                               kernel suppresses (image edges divided by
+                               c1 c1) loses accuracy accordingly. */
 #define SEPW_FORM_TC_FP16X2 4 /* as SEPW_FORM_TC_FP16 with each operand split into
                                  FP16 hi + lo and three products per step:
-                                 FP32-class accuracy */
+                                 FP32-class accuracy.  Degridding uses the
+                                 tiled FP32 form. */
 
 /* image directions (sepw_image) */
 #define SEPW_GRID_TO_IMAGE 0

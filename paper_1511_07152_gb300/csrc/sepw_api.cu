@@ -541,9 +541,14 @@ int sepw_degrid_planned(sepw_ctx *ctx, const float *taps, const float *grid,
         if (((uintptr_t)taps) & 15)
             return fail(ctx, SEPW_EINVAL, "taps must be 16-byte aligned");
         SEPW_CUDA(ctx, launch_zero_dropped(pl, (float2 *)vis_out, s));
-        SEPW_CUDA(ctx, launch_degrid_tiled(ctx->dp, pl, (const float2 *)grid, weight,
-                                           (const float2 *)taps, (float2 *)vis_out,
-                                           ctx->num_sms, s));
+        if (pl.form == SEPW_FORM_TC_BF16 || pl.form == SEPW_FORM_TC_FP16)
+            SEPW_CUDA(ctx, launch_degrid_tc(ctx->dp, pl, (const float2 *)grid, weight,
+                                            (const float2 *)taps, (float2 *)vis_out,
+                                            ctx->num_sms, tc_prec(pl.form), ctx->d_status, s));
+        else
+            SEPW_CUDA(ctx, launch_degrid_tiled(ctx->dp, pl, (const float2 *)grid, weight,
+                                               (const float2 *)taps, (float2 *)vis_out,
+                                               ctx->num_sms, s));
     }
     return SEPW_OK;
 }

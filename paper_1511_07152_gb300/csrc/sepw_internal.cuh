@@ -264,6 +264,10 @@ cudaError_t launch_degrid_tiled(const DevParams &p, const Plan &plan,
 
 // sepw_tc.cu
 int tc_tile_for_support(int S);
+// contraction-form degridder: prec 0 = BF16, 1 = FP16 (scaled per item)
+cudaError_t launch_degrid_tc(const DevParams &p, const Plan &plan, const float2 *grid,
+                             const float *weight, const float2 *taps, float2 *vis,
+                             int num_sms, int prec, int32_t *status, cudaStream_t s);
 // prec: 0 = BF16, 1 = FP16, 2 = FP16 hi + lo (three products)
 cudaError_t launch_grid_tc(const DevParams &p, const Plan &plan, const float2 *vis,
                            const float *weight, const float2 *taps, float2 *grid,

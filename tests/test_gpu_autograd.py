@@ -74,7 +74,20 @@ def test_predict_gradient_matches_oracle(env, form):
     wl = synth.random_case(42, 6000, 128, 8, 8, 9, w_max=300.0, radius_cells=50.0)
     ctx, taps, d = _setup(torch, S, wl, form=form)
     rng = np.random.default_rng(3)
-    image = rng.standard_normal((128, 128)).astype(np.float32)
+    image = rng.standard_normal((128, 128))
+    if form == 3:
+        # FP16 degridding errs relative to the model grid, not to the
+        # prediction: a white image divided by n c1^2 gives a grid 500 times
+        # the prediction's rms (degridding cancels the edge-amplified part),
+        # and 11-bit operands then cost 3% of the prediction (pinned in the
+        # tensor-core tests).  The model here is tapered, x = n c1 c1 y, the
+        # parameterisation of the major cycles, where the grid is 3 times the
+        # prediction's rms.
+        p = O.params_from(wl.params())
+        c = O.kb_taper(O.pixel_nu(128), p.S, p.kb_beta)
+        l = O.pixel_l(128, p.fov)
+        image = image * np.sqrt(1.0 - l[None, :] ** 2 - l[:, None] ** 2) * np.outer(c, c)
+    image = image.astype(np.float32)
     I = torch.from_numpy(image).cuda().requires_grad_(True)
     target = d["vis"]
     loss = AG.chi2(AG.predict(I, ctx, taps), target, d["weight"])
@@ -85,7 +98,7 @@ def test_predict_gradient_matches_oracle(env, form):
         assert rel_l2(got, want) <= 1e-4
     else:
         # The tensor-core form grids the backward with FP16 operands (grid
-        # error ~4e-4).  That rounding noise is white in the image domain,
+        # error ~4e-4; the FP16 forward adds ~2e-4 on this model).  That rounding noise is white in the image domain,
         # while the gradient itself is tapered by c1^2 (it is gridded with
         # the taper), so the grid correction raises the relative error by
         # c1(0)^2 / c1(nu)^2: at most 7.8 inside |nu| < 1/4 for support 8,
