@@ -131,6 +131,7 @@ void free_plan(Plan &pl)
     cudaFree(pl.d_rec);
     cudaFree(pl.d_perm);
     cudaFree(pl.d_drop_list);
+    cudaFree(pl.d_bin);
     cudaFree(pl.d_tile_count);
     cudaFree(pl.d_tile_cursor);
     cudaFree(pl.d_items);
@@ -167,7 +168,7 @@ int ensure_plan_capacity(sepw_ctx *ctx, int64_t nvis, int ngrids)
     Plan &pl = ctx->plan;
     int rc;
     const int64_t ntiles64 = (int64_t)ctx->dp.ntx * ctx->dp.ntx * ngrids;
-    if (ntiles64 > (1ll << 30))
+    if (ntiles64 > (1ll << 26))  // bin ids (tile * kSubBins + sub) stay in int32
         return fail(ctx, SEPW_EINVAL, "too many tiles (%lld)", (long long)ntiles64);
     const int ntiles = (int)ntiles64;
     if (!pl.d_nitems) {
@@ -177,7 +178,8 @@ int ensure_plan_capacity(sepw_ctx *ctx, int64_t nvis, int ngrids)
     }
     if (pl.tiles_capacity < ntiles) {
         if ((rc = grow(ctx, &pl.d_tile_count, ntiles)) ||
-            (rc = grow(ctx, &pl.d_tile_cursor, ntiles)))
+            (rc = grow(ctx, &pl.d_tile_cursor, ntiles)) ||
+            (rc = grow(ctx, &pl.d_bin, (size_t)ntiles * kSubBins)))
             return rc;
         pl.tiles_capacity = ntiles;
     }

@@ -1,9 +1,10 @@
 // Plan construction for the tiled forms: locate every visibility, bin it by
-// the T x T tile that holds its footprint origin (counting sort with
-// warp-aggregated atomics), cut each tile into work items of at most kChunk
-// visibilities, and sort each item by (footprint origin, conj) so that
-// consecutive visibilities with the same origin and kernel conjugation can be
-// accumulated in one register block.
+// the T x T tile that holds its footprint origin and, inside the tile, by the
+// 4 x 4 sub-block of the origin and conj (counting sort with warp-aggregated
+// atomics), cut each tile into work items of at most kChunk visibilities, and
+// sort each item by (footprint origin, conj) so that consecutive visibilities
+// with the same origin and kernel conjugation can be accumulated in one
+// register block.
 //
 // The update structure this serves is Sec. 5: every visibility adds a
 // separable S x S block at its own offset; visibilities that share a tile
@@ -20,16 +21,16 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
-// Pass 1: locate, record, tile histogram, dropped count.
+// Pass 1: locate, record, bin histogram, dropped count.
 __global__ void __launch_bounds__(256) locate_bin_kernel(
     DevParams p, int64_t nvis, const double *__restrict__ u, const double *__restrict__ v,
-    const double *__restrict__ w, int32_t *__restrict__ tile_of,
-    uint64_t *__restrict__ rec0, int32_t *tile_count, unsigned long long *dropped,
+    const double *__restrict__ w, int32_t *__restrict__ bin_of,
+    uint64_t *__restrict__ rec0, int32_t *bin_count, unsigned long long *dropped,
     int32_t *__restrict__ drop_list, int ngrids, const int64_t *__restrict__ offsets)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool active = i < nvis;
-    int tile = -1;
+    int bin = -1;
     if (active) {
         Loc L = locate(u[i], v[i], w[i], p);
         if (L.keep) {
@@ -47,13 +48,14 @@ __global__ void __launch_bounds__(256) locate_bin_kernel(
                 }
                 g = lo;
             }
-            tile = (g * p.ntx + ty) * p.ntx + tx;
-            rec0[i] = pack_rec(fx - tx * p.T, fy - ty * p.T, L.ou, L.ov, L.plane, L.conj);
+            const int lx = fx - tx * p.T, ly = fy - ty * p.T;
+            bin = ((g * p.ntx + ty) * p.ntx + tx) * kSubBins + sub_bin(lx, ly, L.conj, p.T);
+            rec0[i] = pack_rec(lx, ly, L.ou, L.ov, L.plane, L.conj);
         }
-        tile_of[i] = tile;
+        bin_of[i] = bin;
     }
-    unsigned act = __ballot_sync(0xffffffffu, active && tile >= 0);
-    unsigned drop = __ballot_sync(0xffffffffu, active && tile < 0);
+    unsigned act = __ballot_sync(0xffffffffu, active && bin >= 0);
+    unsigned drop = __ballot_sync(0xffffffffu, active && bin < 0);
     int lane = threadIdx.x & 31;
     if (drop) {
         // append the dropped indices (degridding writes 0 there)
@@ -62,14 +64,38 @@ __global__ void __launch_bounds__(256) locate_bin_kernel(
         if (lane == leader)
             base = atomicAdd(dropped, (unsigned long long)__popc(drop));
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (active && tile < 0)
+        if (active && bin < 0)
             drop_list[base + __popc(drop & lanemask_lt())] = (int32_t)i;
     }
-    if (active && tile >= 0) {
-        unsigned peers = __match_any_sync(act, tile);
+    if (active && bin >= 0) {
+        unsigned peers = __match_any_sync(act, bin);
         if (lane == __ffs(peers) - 1)
-            atomicAdd(tile_count + tile, __popc(peers));
+            atomicAdd(bin_count + bin, __popc(peers));
     }
+}
+
+// Pass 1b (one warp per tile): the tile's visibility count, and each bin's
+// count replaced by its offset inside the tile (exclusive scan of the 32).
+__global__ void __launch_bounds__(256) bin_scan_kernel(int32_t ntiles,
+                                                       int32_t *__restrict__ bin,
+                                                       int32_t *__restrict__ tile_count)
+{
+    static_assert(kSubBins == 32, "one lane per bin");
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= ntiles)
+        return;
+    const int c = bin[t * kSubBins + lane];
+    int incl = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off)
+            incl += y;
+    }
+    bin[t * kSubBins + lane] = incl - c;
+    if (lane == 31)
+        tile_count[t] = incl;
 }
 
 // Pass 2 (one block of 1024 threads): exclusive scans of the tile counts
@@ -141,22 +167,24 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
         *nitems = total_full + s_part[t];
 }
 
-// Pass 3: scatter visibility ids and records to their tile's slots.
+// Pass 3: scatter visibility ids and records to their bin's slots (tile
+// start + offset of the bin inside the tile + rank inside the bin).
 __global__ void __launch_bounds__(256) scatter_kernel(
-    int64_t nvis, const int32_t *__restrict__ tile_of, const uint64_t *__restrict__ rec0,
-    int32_t *cursor, int32_t *__restrict__ perm, uint64_t *__restrict__ rec)
+    int64_t nvis, const int32_t *__restrict__ bin_of, const uint64_t *__restrict__ rec0,
+    const int32_t *__restrict__ tile_start, int32_t *bin_cursor,
+    int32_t *__restrict__ perm, uint64_t *__restrict__ rec)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int tile = i < nvis ? tile_of[i] : -1;
-    unsigned act = __ballot_sync(0xffffffffu, tile >= 0);
-    if (tile < 0)
+    int b = i < nvis ? bin_of[i] : -1;
+    unsigned act = __ballot_sync(0xffffffffu, b >= 0);
+    if (b < 0)
         return;
     int lane = threadIdx.x & 31;
-    unsigned peers = __match_any_sync(act, tile);
+    unsigned peers = __match_any_sync(act, b);
     int leader = __ffs(peers) - 1;
     int base = 0;
     if (lane == leader)
-        base = atomicAdd(cursor + tile, __popc(peers));
+        base = __ldg(tile_start + b / kSubBins) + atomicAdd(bin_cursor + b, __popc(peers));
     base = __shfl_sync(peers, base, leader);
     int slot = base + __popc(peers & lanemask_lt());
     perm[slot] = (int32_t)i;
@@ -273,7 +301,7 @@ cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
                         const double *v, const double *w, Plan &plan, cudaStream_t s)
 {
     cudaError_t e;
-    e = cudaMemsetAsync(plan.d_tile_count, 0, sizeof(int32_t) * plan.ntiles, s);
+    e = cudaMemsetAsync(plan.d_bin, 0, sizeof(int32_t) * kSubBins * (size_t)plan.ntiles, s);
     if (e != cudaSuccess)
         return e;
     e = cudaMemsetAsync(plan.d_dropped, 0, sizeof(unsigned long long), s);
@@ -281,18 +309,23 @@ cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
         return e;
     if (nvis > 0) {
         locate_bin_kernel<<<(unsigned)((nvis + 255) / 256), 256, 0, s>>>(
-            p, nvis, u, v, w, plan.d_tile, plan.d_rec0, plan.d_tile_count, plan.d_dropped,
+            p, nvis, u, v, w, plan.d_tile, plan.d_rec0, plan.d_bin, plan.d_dropped,
             plan.d_drop_list, plan.ngrids, plan.d_offsets);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
     }
+    bin_scan_kernel<<<(unsigned)(((int64_t)plan.ntiles * 32 + 255) / 256), 256, 0, s>>>(
+        plan.ntiles, plan.d_bin, plan.d_tile_count);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
     scan_kernel<<<1, kScanThreads, 0, s>>>(plan.ntiles, plan.d_tile_count,
                                            plan.d_tile_cursor, plan.d_items, plan.d_nitems);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     if (nvis > 0) {
         scatter_kernel<<<(unsigned)((nvis + 255) / 256), 256, 0, s>>>(
-            nvis, plan.d_tile, plan.d_rec0, plan.d_tile_cursor, plan.d_perm, plan.d_rec);
+            nvis, plan.d_tile, plan.d_rec0, plan.d_tile_cursor, plan.d_bin, plan.d_perm,
+            plan.d_rec);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
         const int nb = 2 * p.T * p.T;

@@ -193,6 +193,18 @@ constexpr int kChunk = 2048;      // visibilities per work item (tiled forms)
 constexpr int kMaxWindow = 64;    // T + S - 1 <= kMaxWindow
 
 // Plan workspace (owned by the context).
+// Binning below the tile: each tile's visibilities are grouped by the 4 x 4
+// sub-block of the tile that holds their footprint origin and by conj, 32
+// bins per tile, before the tile is cut into work items.  An item then spans
+// few sub-blocks, so after the per-item sort its runs of one origin are long
+// (one register block accumulates a whole run).
+constexpr int kSubBins = 32;
+
+__host__ __device__ __forceinline__ int sub_bin(int lx, int ly, bool conj, int T)
+{
+    return ((((ly * 4) / T) * 4 + (lx * 4) / T) << 1) | (conj ? 1 : 0);
+}
+
 struct Plan {
     int64_t nvis = 0;
     int64_t capacity = 0;       // allocated visibility slots
@@ -202,7 +214,8 @@ struct Plan {
     bool valid = false;
     int form = 0;
     // tiled forms
-    int32_t *d_tile = nullptr;      // [nvis] tile id per visibility (-1 dropped)
+    int32_t *d_tile = nullptr;      // [nvis] bin id per visibility (-1 dropped)
+    int32_t *d_bin = nullptr;       // [ntiles * kSubBins] bin counts, then cursors
     uint64_t *d_rec0 = nullptr;     // [nvis] record, input order
     uint64_t *d_rec = nullptr;      // [nvis] record, slot order
     int32_t *d_perm = nullptr;      // [nvis] slot -> visibility index

@@ -7,14 +7,14 @@
 // raw allocations from plugins.  This entry point serves them: instead of a
 // context's workspace it uses one fixed scratch array compiled into the
 // library as a file-scope __device__ variable, so every GPU that loads the
-// library holds that array (kNoallocBytes, about 16 MB) until the process
+// library holds that array (kNoallocBytes, about 24 MB) until the process
 // exits.
 //
-// The scratch holds the same plan as the context path (tile ids, packed
+// The scratch holds the same plan as the context path (bin ids, packed
 // records, slot permutation, dropped-index list, per-tile counts and cursors,
-// work items and counters), and the existing plan and tiled-gridder launchers
-// run on it unchanged.  Every call reuses the array: the plan launcher clears
-// the tile counts and the dropped counter at the start of each call, the
+// per-bin counts, work items and counters), and the existing plan and
+// tiled-gridder launchers run on it unchanged.  Every call reuses the array: the plan launcher clears
+// the bin counts and the dropped counter at the start of each call, the
 // gridder clears its work counter, and everything else is overwritten before
 // it is read.  Calls whose work overlaps on the GPU (other streams, other host
 // threads) race on the array.
@@ -39,7 +39,8 @@ constexpr size_t kOffPerm = align256(kOffRec + sizeof(uint64_t) * kMaxVis);
 constexpr size_t kOffDrop = align256(kOffPerm + sizeof(int32_t) * kMaxVis);
 constexpr size_t kOffCount = align256(kOffDrop + sizeof(int32_t) * kMaxVis);
 constexpr size_t kOffCursor = align256(kOffCount + sizeof(int32_t) * kMaxTiles);
-constexpr size_t kOffItems = align256(kOffCursor + sizeof(int32_t) * kMaxTiles);
+constexpr size_t kOffBin = align256(kOffCursor + sizeof(int32_t) * kMaxTiles);
+constexpr size_t kOffItems = align256(kOffBin + sizeof(int32_t) * kSubBins * kMaxTiles);
 constexpr size_t kOffNitems = align256(kOffItems + sizeof(WorkItem) * kMaxItems);
 constexpr size_t kOffCounter = align256(kOffNitems + sizeof(int32_t));
 constexpr size_t kOffDropped = align256(kOffCounter + 2 * sizeof(int32_t));
@@ -165,6 +166,7 @@ extern "C" int sepw_grid_noalloc(const sepw_params *prm, const float *taps, int6
     pl.d_drop_list = (int32_t *)(b + kOffDrop);
     pl.d_tile_count = (int32_t *)(b + kOffCount);
     pl.d_tile_cursor = (int32_t *)(b + kOffCursor);
+    pl.d_bin = (int32_t *)(b + kOffBin);
     pl.d_items = (WorkItem *)(b + kOffItems);
     pl.d_nitems = (int32_t *)(b + kOffNitems);
     pl.d_item_counter = (int32_t *)(b + kOffCounter);
