@@ -706,7 +706,9 @@ def run_ours(args):
             "roofline": roofline, "roofline_hbm": roofline_hbm, "peak_source": peak_src,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "wall_s_timed": time.perf_counter() - t_start,
-            "gpu_launches": 7 * args.steps,
+            # per step: plan (locate_bin, bin_scan, scan, scatter, item_sort),
+            # grid (planar tap copy, gridder), degrid (zero_dropped, degridder)
+            "gpu_launches": 9 * args.steps,
         }
         print(json.dumps(line))
     if ws > 1:

@@ -22,6 +22,9 @@ struct sepw_ctx {
     float *d_taper32 = nullptr;
     double2 *d_tw = nullptr;
     int32_t *d_status = nullptr;  // SEPW_ETIMEOUT recorded by a kernel
+    // workspace of the tiled gridder's planar copy of the caller's tap
+    // table(s) (two tables: facet mode)
+    float *d_planar = nullptr;
     Plan plan;
     cufftHandle fft = 0;
     bool fft_ready = false;
@@ -289,7 +292,8 @@ int sepw_create(sepw_ctx **out, const sepw_params *p)
     const int N = p->grid_size;
     if ((rc = grow(ctx, &ctx->d_taper64, N)) || (rc = grow(ctx, &ctx->d_taper32, N)) ||
         (rc = grow(ctx, &ctx->d_tw, (size_t)N * p->oversample)) ||
-        (rc = grow(ctx, &ctx->d_status, 1))) {
+        (rc = grow(ctx, &ctx->d_status, 1)) ||
+        (rc = grow(ctx, &ctx->d_planar, 2 * 2 * sepw_taps_count(p)))) {
         sepw_destroy(ctx);
         return rc;
     }
@@ -333,6 +337,7 @@ void sepw_destroy(sepw_ctx *ctx)
     cudaFree(ctx->d_taper32);
     cudaFree(ctx->d_tw);
     cudaFree(ctx->d_status);
+    cudaFree(ctx->d_planar);
     free_plan(ctx->plan);
     cudaSetDevice(cur);
     delete ctx;
@@ -506,7 +511,7 @@ int sepw_grid_planned(sepw_ctx *ctx, const float *taps, const float *vis,
         if (((uintptr_t)taps) & 15)
             return fail(ctx, SEPW_EINVAL, "taps must be 16-byte aligned");
         SEPW_CUDA(ctx, launch_grid_tiled(ctx->dp, pl, (const float2 *)vis, weight,
-                                         (const float2 *)taps, (float2 *)grid,
+                                         (const float2 *)taps, ctx->d_planar, (float2 *)grid,
                                          ctx->num_sms, s));
     }
     return SEPW_OK;

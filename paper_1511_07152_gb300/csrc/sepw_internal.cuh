@@ -267,9 +267,12 @@ cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
 cudaError_t launch_zero_dropped(const Plan &plan, float2 *vis, cudaStream_t s);
 
 // sepw_tiled.cu
+// planar: workspace of 2 x (taps of both tables) floats for the lane-ordered
+// planar copy of the tap table that the block gridder (S = 8, 16) builds and
+// reads its v-taps from; null: the interleaved table is read directly
 cudaError_t launch_grid_tiled(const DevParams &p, const Plan &plan, const float2 *vis,
-                              const float *weight, const float2 *taps, float2 *grid,
-                              int num_sms, cudaStream_t s);
+                              const float *weight, const float2 *taps, float *planar,
+                              float2 *grid, int num_sms, cudaStream_t s);
 cudaError_t launch_degrid_tiled(const DevParams &p, const Plan &plan,
                                 const float2 *grid, const float *weight,
                                 const float2 *taps, float2 *vis, int num_sms,

@@ -178,7 +178,7 @@ extern "C" int sepw_grid_noalloc(const sepw_params *prm, const float *taps, int6
         return SEPW_ECUDA;
     }
     if (nvis > 0 && launch_grid_tiled(dp, pl, (const float2 *)vis, weight,
-                                      (const float2 *)taps, (float2 *)grid, num_sms,
+                                      (const float2 *)taps, nullptr, (float2 *)grid, num_sms,
                                       s) != cudaSuccess) {
         cudaGetLastError();
         return SEPW_ECUDA;

@@ -536,9 +536,20 @@ __global__ void __launch_bounds__(kTiledThreads, Blk<S>::BPS) degrid_tiled_block
 // ---------------------------------------------------------------------------
 // Gridding with a 4 x 8 lane grid, S = 8, 16.  Lane (rg, cg) =
 // (lane >> 3, lane & 7) owns the cells at footprint rows rg + 4 r
-// (r < S / 4) and columns cg + 8 c (c < ceil(S / 8), column < S).  The inner
-// loop runs over runs of equal keys found with one ballot per batch, so the
-// flush and its branch sit outside it.
+// (r < RB = S / 4) and columns cg + 8 c (c < ceil(S / 8), column < S).  The
+// inner loop runs over runs of equal keys found with one ballot per batch, so
+// the flush and its branch sit outside it.
+//
+// The accumulators of the lane's rows 2q and 2q + 1 in one column form a
+// pair, (re, re) and (im, im), so that the complex multiply-adds of the
+// outer product run as paired FP32 FMAs (two FMAs per instruction): per row
+// pair and column
+//     re += (vr_2q, vr_2q+1) pr - (vi_2q, vi_2q+1) pi
+//     im += (vi_2q, vi_2q+1) pr + (vr_2q, vr_2q+1) pi
+// with the same rounding sequence per cell as scalar FMAs.  The v-tap pairs
+// come straight from the lane-ordered planar copy of the table (see
+// planar_taps_kernel: a lane's RB taps are adjacent); without it (PLANAR
+// false) they are rearranged from the interleaved table in registers.
 // ---------------------------------------------------------------------------
 template <int S>
 struct Blk2 {
@@ -546,28 +557,32 @@ struct Blk2 {
     // kernel was faster there (sparse batched grids, 11.1 vs 13.0 ms)
     static constexpr bool OK = S == 8 || S == 16;
     static constexpr int RB = S / 4;        // rows per lane
+    static constexpr int RP = RB / 2;       // row pairs per lane
     static constexpr int CB = (S + 7) / 8;  // columns per lane
     static constexpr bool FULL = S % 8 == 0;
 };
 
-template <int S>
+template <int S, bool PLANAR>
 __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_block_kernel(
     DevParams p, const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems,
     int32_t *counter, const uint64_t *__restrict__ rec, const int32_t *__restrict__ perm,
     const float2 *__restrict__ vis, const float *__restrict__ weight,
-    const float2 *__restrict__ taps, float2 *grid)
+    const float2 *__restrict__ taps, const float *__restrict__ planar, float2 *grid)
 {
-    constexpr int RB = Blk2<S>::RB, CB = Blk2<S>::CB;
+    constexpr int RB = Blk2<S>::RB, RP = Blk2<S>::RP, CB = Blk2<S>::CB;
     constexpr bool FULL = Blk2<S>::FULL;
+    static_assert(RB % 2 == 0, "rows come in pairs");
     __shared__ int4 s_meta[kTiledWarps * 32];
     __shared__ int s_key[kTiledWarps * 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rg = lane >> 3, cg = lane & 7;
     int4 *const meta = s_meta + warp * 32;
     int *const keys = s_key + warp * 32;
-    // this lane's u-tap column and v-tap row within a table row
+    // this lane's u-tap column and first v-tap row within a table row; in
+    // the planar copy its RB v-taps sit at RB rg .. RB rg + RB - 1
     const float2 *const tcol = taps + cg;
     const float2 *const trow = taps + p.voff + rg;
+    const float *const prow = PLANAR ? planar + 2 * p.voff + RB * rg : nullptr;
     const int n_items = *nitems;
 
     for (;;) {
@@ -582,40 +597,39 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_b
         float2 *const tgrid = grid + o.base + (o.gy0 + rg) * p.N + o.gx0 + cg;
         const int b0 = it.start, b1 = it.start + it.count;
 
-        float2 acc[RB][CB];
+        // ar[q][c] = (re of rows 2q, 2q + 1) of column c (footprint rows
+        // rg + 8 q, rg + 8 q + 4); ai likewise
+        float2 ar[RP][CB], ai[RP][CB];
 #pragma unroll
-        for (int r = 0; r < RB; ++r)
+        for (int q = 0; q < RP; ++q)
 #pragma unroll
             for (int c = 0; c < CB; ++c)
-                acc[r][c] = make_float2(0.f, 0.f);
+                ar[q][c] = ai[q][c] = make_float2(0.f, 0.f);
         int cur = -1;
 
         // adds the register block of key `cur` to the grid and clears it;
         // conj groups accumulated conj(W V) F1 F1 and are conjugated here
         auto flush = [&]() {
             if (cur >= 0) {
-                if (cur & 1) {
-#pragma unroll
-                    for (int r = 0; r < RB; ++r)
-#pragma unroll
-                        for (int c = 0; c < CB; ++c)
-                            acc[r][c].y = -acc[r][c].y;
-                }
+                const float sg = (cur & 1) ? -1.f : 1.f;
                 float2 *g = tgrid + key_ly(cur) * p.N + key_lx(cur);
 #pragma unroll
-                for (int r = 0; r < RB; ++r) {
+                for (int q = 0; q < RP; ++q) {
 #pragma unroll
                     for (int c = 0; c < CB; ++c)
-                        if (FULL || cg + 8 * c < S)
-                            atomicAdd(g + 8 * c, acc[r][c]);
-                    g += 4 * p.N;
+                        if (FULL || cg + 8 * c < S) {
+                            atomicAdd(g + 8 * c, make_float2(ar[q][c].x, sg * ai[q][c].x));
+                            atomicAdd(g + 4 * p.N + 8 * c,
+                                      make_float2(ar[q][c].y, sg * ai[q][c].y));
+                        }
+                    g += 8 * p.N;
                 }
             }
 #pragma unroll
-            for (int r = 0; r < RB; ++r)
+            for (int q = 0; q < RP; ++q)
 #pragma unroll
                 for (int c = 0; c < CB; ++c)
-                    acc[r][c] = make_float2(0.f, 0.f);
+                    ar[q][c] = ai[q][c] = make_float2(0.f, 0.f);
         };
 
         for (int base = b0; base < b1; base += 32) {
@@ -652,8 +666,7 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_b
                     const int4 m = meta[q];
                     const float wx = __int_as_float(m.z), wy = __int_as_float(m.w);
                     const float2 *tu = tcol + m.x;
-                    const float2 *tv = trow + m.y;
-                    float pr[CB], pi[CB], vr[RB], vi[RB];
+                    float pr[CB], pi[CB];
 #pragma unroll
                     for (int c = 0; c < CB; ++c) {
                         float2 a = make_float2(0.f, 0.f);
@@ -663,22 +676,46 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_b
                         pr[c] = wx * a.x - wy * a.y;
                         pi[c] = wx * a.y + wy * a.x;
                     }
+                    // v-tap pairs of this lane's rows: (vr_2q, vr_2q+1), (vi_2q, vi_2q+1)
+                    float2 vr[RP], vi[RP];
+                    if constexpr (PLANAR) {
+                        const float *pv = prow + 2 * m.y;
+                        if constexpr (RP == 2) {
+                            const float4 re = __ldg(reinterpret_cast<const float4 *>(pv));
+                            const float4 im = __ldg(reinterpret_cast<const float4 *>(pv + S));
+                            vr[0] = make_float2(re.x, re.y);
+                            vr[1] = make_float2(re.z, re.w);
+                            vi[0] = make_float2(im.x, im.y);
+                            vi[1] = make_float2(im.z, im.w);
+                        } else {
 #pragma unroll
-                    for (int r = 0; r < RB; ++r) {
-                        const float2 b = __ldg(tv + 4 * r);
-                        vr[r] = b.x;
-                        vi[r] = b.y;
+                            for (int q2 = 0; q2 < RP; ++q2) {
+                                vr[q2] = __ldg(reinterpret_cast<const float2 *>(pv) + q2);
+                                vi[q2] = __ldg(reinterpret_cast<const float2 *>(pv + S) + q2);
+                            }
+                        }
+                    } else {
+                        const float2 *tv = trow + m.y;
+#pragma unroll
+                        for (int q2 = 0; q2 < RP; ++q2) {
+                            const float2 t0 = __ldg(tv + 8 * q2), t1 = __ldg(tv + 8 * q2 + 4);
+                            vr[q2] = make_float2(t0.x, t1.x);
+                            vi[q2] = make_float2(t0.y, t1.y);
+                        }
                     }
 #pragma unroll
-                    for (int r = 0; r < RB; ++r)
+                    for (int c = 0; c < CB; ++c) {
+                        const float2 prr = make_float2(pr[c], pr[c]);
+                        const float2 pii = make_float2(pi[c], pi[c]);
+                        const float2 npi = make_float2(-pi[c], -pi[c]);
 #pragma unroll
-                        for (int c = 0; c < CB; ++c) {
-                            float2 &a = acc[r][c];
-                            a.x = fmaf(pr[c], vr[r], a.x);
-                            a.x = fmaf(-pi[c], vi[r], a.x);
-                            a.y = fmaf(pr[c], vi[r], a.y);
-                            a.y = fmaf(pi[c], vr[r], a.y);
+                        for (int q2 = 0; q2 < RP; ++q2) {
+                            ar[q2][c] = __ffma2_rn(vr[q2], prr, ar[q2][c]);
+                            ar[q2][c] = __ffma2_rn(vi[q2], npi, ar[q2][c]);
+                            ai[q2][c] = __ffma2_rn(vi[q2], prr, ai[q2][c]);
+                            ai[q2][c] = __ffma2_rn(vr[q2], pii, ai[q2][c]);
                         }
+                    }
                 }
             }
             __syncwarp();
@@ -686,7 +723,6 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) grid_tiled_b
         flush();
     }
 }
-
 
 // Row stride of the shared window: the smallest WP >= W for which the row
 // groups of a warp touch disjoint banks.
@@ -717,19 +753,59 @@ static size_t tiled_smem(int W, int WP)
            (size_t)kTiledWarps * 32 * sizeof(int4);
 }
 
+// Lane-ordered planar copy of a tap table: row j of S complex taps becomes
+// S real parts followed by S imaginary parts (same bytes per row, same row
+// order), with tap k at position (k mod 4) S/4 + floor(k / 4) when 4 divides
+// S.  A lane of the block gridder owns rows g, g + 4, g + 8, ... (g = k mod 4),
+// whose taps are then adjacent: one vector load gives its FP32 pairs.
+__global__ void planar_taps_kernel(const float2 *__restrict__ taps, float *__restrict__ out,
+                                   int64_t n, int S)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e / S;
+        const int k = (int)(e - row * S);
+        const int pos = S % 4 == 0 ? (k & 3) * (S >> 2) + (k >> 2) : k;
+        const float2 t = taps[e];
+        out[row * 2 * S + pos] = t.x;
+        out[row * 2 * S + S + pos] = t.y;
+    }
+}
+
+static cudaError_t launch_planar_taps(const float2 *taps, float *out, int64_t n, int S,
+                               cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    const int64_t blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    planar_taps_kernel<<<(unsigned)blocks, 256, 0, s>>>(taps, out, n, S);
+    return cudaGetLastError();
+}
+
 template <int S>
 static cudaError_t launch_grid_S(const DevParams &p, const Plan &plan, const float2 *vis,
-                                 const float *weight, const float2 *taps, float2 *grid,
-                                 int num_sms, cudaStream_t s)
+                                 const float *weight, const float2 *taps, float *planar,
+                                 float2 *grid, int num_sms, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(plan.d_item_counter, 0, sizeof(int32_t), s);
     if (e != cudaSuccess)
         return e;
-    if constexpr (Blk2<S>::OK)
-        grid_tiled_block_kernel<S><<<num_sms * kTiledBlocksPerSM, kTiledThreads, 0, s>>>(
-            p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm, vis,
-            weight, taps, grid);
-    else
+    if constexpr (Blk2<S>::OK) {
+        const unsigned nb = (unsigned)(num_sms * kTiledBlocksPerSM);
+        if (planar) {  // rebuilt per call: the caller's table may have changed
+            const int64_t n = (p.facet ? 2 : 1) * (int64_t)p.P * p.OS * S;
+            if ((e = launch_planar_taps(taps, planar, n, S, s)) != cudaSuccess)
+                return e;
+        }
+        if (planar)
+            grid_tiled_block_kernel<S, true><<<nb, kTiledThreads, 0, s>>>(
+                p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm,
+                vis, weight, taps, planar, grid);
+        else
+            grid_tiled_block_kernel<S, false><<<nb, kTiledThreads, 0, s>>>(
+                p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm,
+                vis, weight, taps, nullptr, grid);
+    } else
         grid_tiled_kernel<S><<<num_sms * kTiledBlocksPerSM, kTiledThreads, 0, s>>>(
             p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm, vis,
             weight, taps, grid);
@@ -769,12 +845,12 @@ static cudaError_t launch_degrid_S(const DevParams &p, const Plan &plan,
     X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24) X(26) X(28) X(30) X(32)
 
 cudaError_t launch_grid_tiled(const DevParams &p, const Plan &plan, const float2 *vis,
-                              const float *weight, const float2 *taps, float2 *grid,
-                              int num_sms, cudaStream_t s)
+                              const float *weight, const float2 *taps, float *planar,
+                              float2 *grid, int num_sms, cudaStream_t s)
 {
     switch (p.S) {
 #define X(SS) \
-    case SS: return launch_grid_S<SS>(p, plan, vis, weight, taps, grid, num_sms, s);
+    case SS: return launch_grid_S<SS>(p, plan, vis, weight, taps, planar, grid, num_sms, s);
         SEPW_FOR_EACH_S(X)
 #undef X
     default:
