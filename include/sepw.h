@@ -368,7 +368,7 @@ SEPW_API int sepw_wstack_model_grids(sepw_ctx *ctx, const float *image, float *s
  *
  * Same result as sepw_grid with the tiled FP32 form (p->form is ignored), but
  * no context is needed and nothing is allocated: the binning workspace is one
- * file-scope device array of about 24 MB compiled into the library, which
+ * file-scope device array of about 26 MB compiled into the library, which
  * every GPU that loads the library keeps until the process exits.  The call
  * makes no cudaMalloc / cudaFree and no allocating library call.
  *   - p, taps, u, v, w, vis, weight (NULL = 1), grid (accumulated, +=):

@@ -130,6 +130,7 @@ int grow(sepw_ctx *ctx, T **ptr, size_t count)
 void free_plan(Plan &pl)
 {
     cudaFree(pl.d_tile);
+    cudaFree(pl.d_rank);
     cudaFree(pl.d_rec0);
     cudaFree(pl.d_rec);
     cudaFree(pl.d_perm);
@@ -191,7 +192,8 @@ int ensure_plan_capacity(sepw_ctx *ctx, int64_t nvis, int ngrids)
         return SEPW_OK;  // the plain form keeps no per-visibility state
     if (pl.capacity < nvis) {
         int64_t cap = nvis;
-        if ((rc = grow(ctx, &pl.d_tile, cap)) || (rc = grow(ctx, &pl.d_rec0, cap)) ||
+        if ((rc = grow(ctx, &pl.d_tile, cap)) || (rc = grow(ctx, &pl.d_rank, cap)) ||
+            (rc = grow(ctx, &pl.d_rec0, cap)) ||
             (rc = grow(ctx, &pl.d_rec, cap)) || (rc = grow(ctx, &pl.d_perm, cap)) ||
             (rc = grow(ctx, &pl.d_drop_list, cap)))
             return rc;

@@ -21,12 +21,14 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
-// Pass 1: locate, record, bin histogram, dropped count.
+// Pass 1: locate, record, bin histogram with each visibility's rank inside
+// its bin (the order of arrival at the bin's counter), dropped count.
 __global__ void __launch_bounds__(256) locate_bin_kernel(
     DevParams p, int64_t nvis, const double *__restrict__ u, const double *__restrict__ v,
     const double *__restrict__ w, int32_t *__restrict__ bin_of,
-    uint64_t *__restrict__ rec0, int32_t *bin_count, unsigned long long *dropped,
-    int32_t *__restrict__ drop_list, int ngrids, const int64_t *__restrict__ offsets)
+    int32_t *__restrict__ rank_of, uint64_t *__restrict__ rec0, int32_t *bin_count,
+    unsigned long long *dropped, int32_t *__restrict__ drop_list, int ngrids,
+    const int64_t *__restrict__ offsets)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool active = i < nvis;
@@ -68,9 +70,13 @@ __global__ void __launch_bounds__(256) locate_bin_kernel(
             drop_list[base + __popc(drop & lanemask_lt())] = (int32_t)i;
     }
     if (active && bin >= 0) {
-        unsigned peers = __match_any_sync(act, bin);
-        if (lane == __ffs(peers) - 1)
-            atomicAdd(bin_count + bin, __popc(peers));
+        const unsigned peers = __match_any_sync(act, bin);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader)
+            base = atomicAdd(bin_count + bin, __popc(peers));
+        base = __shfl_sync(act, base, leader);
+        rank_of[i] = base + __popc(peers & lanemask_lt());
     }
 }
 
@@ -167,26 +173,21 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
         *nitems = total_full + s_part[t];
 }
 
-// Pass 3: scatter visibility ids and records to their bin's slots (tile
-// start + offset of the bin inside the tile + rank inside the bin).
+// Pass 3: scatter visibility ids and records to their slots: tile start +
+// offset of the bin inside the tile + rank inside the bin.
 __global__ void __launch_bounds__(256) scatter_kernel(
-    int64_t nvis, const int32_t *__restrict__ bin_of, const uint64_t *__restrict__ rec0,
-    const int32_t *__restrict__ tile_start, int32_t *bin_cursor,
-    int32_t *__restrict__ perm, uint64_t *__restrict__ rec)
+    int64_t nvis, const int32_t *__restrict__ bin_of, const int32_t *__restrict__ rank_of,
+    const uint64_t *__restrict__ rec0, const int32_t *__restrict__ tile_start,
+    const int32_t *__restrict__ bin_off, int32_t *__restrict__ perm,
+    uint64_t *__restrict__ rec)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int b = i < nvis ? bin_of[i] : -1;
-    unsigned act = __ballot_sync(0xffffffffu, b >= 0);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nvis)
+        return;
+    const int b = bin_of[i];
     if (b < 0)
         return;
-    int lane = threadIdx.x & 31;
-    unsigned peers = __match_any_sync(act, b);
-    int leader = __ffs(peers) - 1;
-    int base = 0;
-    if (lane == leader)
-        base = __ldg(tile_start + b / kSubBins) + atomicAdd(bin_cursor + b, __popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    int slot = base + __popc(peers & lanemask_lt());
+    const int slot = __ldg(tile_start + b / kSubBins) + __ldg(bin_off + b) + rank_of[i];
     perm[slot] = (int32_t)i;
     rec[slot] = rec0[i];
 }
@@ -223,11 +224,22 @@ __global__ void __launch_bounds__(kSortThreads) item_sort_kernel(
     for (int b = threadIdx.x; b < per * kSortThreads; b += kSortThreads)
         hist[b] = 0;
     __syncthreads();
-    for (int q = threadIdx.x; q < n; q += kSortThreads) {
-        const uint64_t r = rec[it.start + q];
-        s_rec[q] = r;
-        s_perm[q] = perm[it.start + q];
-        atomicAdd(hist + sort_key(r, T), 1);
+    // a warp's lanes hold consecutive slots, where runs of one key are
+    // common: one shared-memory atomic per distinct key per warp
+    const int lane_id = threadIdx.x & 31;
+    for (int q0 = 0; q0 < n; q0 += kSortThreads) {
+        const int q = q0 + (int)threadIdx.x;
+        const bool act = q < n;
+        int key = -1;
+        if (act) {
+            const uint64_t r = rec[it.start + q];
+            s_rec[q] = r;
+            s_perm[q] = perm[it.start + q];
+            key = sort_key(r, T);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (act && lane_id == __ffs(peers) - 1)
+            atomicAdd(hist + key, __popc(peers));
     }
     __syncthreads();
     // exclusive scan: thread t owns bins [t*per, t*per + per)
@@ -272,11 +284,26 @@ __global__ void __launch_bounds__(kSortThreads) item_sort_kernel(
         run += local[q];
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < n; q += kSortThreads) {
-        const uint64_t r = s_rec[q];
-        const int dst = atomicAdd(hist + sort_key(r, T), 1);
-        rec[it.start + dst] = r;
-        perm[it.start + dst] = s_perm[q];
+    for (int q0 = 0; q0 < n; q0 += kSortThreads) {
+        const int q = q0 + (int)threadIdx.x;
+        const bool act = q < n;
+        uint64_t r = 0;
+        int key = -1;
+        if (act) {
+            r = s_rec[q];
+            key = sort_key(r, T);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (act && lane_id == leader)
+            base = atomicAdd(hist + key, __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (act) {
+            const int dst = base + __popc(peers & lanemask_lt());
+            rec[it.start + dst] = r;
+            perm[it.start + dst] = s_perm[q];
+        }
     }
 }
 
@@ -309,8 +336,8 @@ cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
         return e;
     if (nvis > 0) {
         locate_bin_kernel<<<(unsigned)((nvis + 255) / 256), 256, 0, s>>>(
-            p, nvis, u, v, w, plan.d_tile, plan.d_rec0, plan.d_bin, plan.d_dropped,
-            plan.d_drop_list, plan.ngrids, plan.d_offsets);
+            p, nvis, u, v, w, plan.d_tile, plan.d_rank, plan.d_rec0, plan.d_bin,
+            plan.d_dropped, plan.d_drop_list, plan.ngrids, plan.d_offsets);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
     }
@@ -324,8 +351,8 @@ cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
         return e;
     if (nvis > 0) {
         scatter_kernel<<<(unsigned)((nvis + 255) / 256), 256, 0, s>>>(
-            nvis, plan.d_tile, plan.d_rec0, plan.d_tile_cursor, plan.d_bin, plan.d_perm,
-            plan.d_rec);
+            nvis, plan.d_tile, plan.d_rank, plan.d_rec0, plan.d_tile_cursor, plan.d_bin,
+            plan.d_perm, plan.d_rec);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
         const int nb = 2 * p.T * p.T;

@@ -215,6 +215,7 @@ struct Plan {
     int form = 0;
     // tiled forms
     int32_t *d_tile = nullptr;      // [nvis] bin id per visibility (-1 dropped)
+    int32_t *d_rank = nullptr;      // [nvis] rank of the visibility inside its bin
     int32_t *d_bin = nullptr;       // [ntiles * kSubBins] bin counts, then cursors
     uint64_t *d_rec0 = nullptr;     // [nvis] record, input order
     uint64_t *d_rec = nullptr;      // [nvis] record, slot order

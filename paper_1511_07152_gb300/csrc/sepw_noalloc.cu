@@ -7,17 +7,17 @@
 // raw allocations from plugins.  This entry point serves them: instead of a
 // context's workspace it uses one fixed scratch array compiled into the
 // library as a file-scope __device__ variable, so every GPU that loads the
-// library holds that array (kNoallocBytes, about 24 MB) until the process
+// library holds that array (kNoallocBytes, about 26 MB) until the process
 // exits.
 //
-// The scratch holds the same plan as the context path (bin ids, packed
-// records, slot permutation, dropped-index list, per-tile counts and cursors,
-// per-bin counts, work items and counters), and the existing plan and
-// tiled-gridder launchers run on it unchanged.  Every call reuses the array: the plan launcher clears
-// the bin counts and the dropped counter at the start of each call, the
-// gridder clears its work counter, and everything else is overwritten before
-// it is read.  Calls whose work overlaps on the GPU (other streams, other host
-// threads) race on the array.
+// The scratch holds the same plan as the context path (bin ids and ranks,
+// packed records, slot permutation, dropped-index list, per-tile counts and
+// cursors, per-bin counts, work items and counters), and the existing plan
+// and tiled-gridder launchers run on it unchanged.  Every call reuses the
+// array: the plan launcher clears the bin counts and the dropped counter at
+// the start of each call, the gridder clears its work counter, and
+// everything else is overwritten before it is read.  Calls whose work
+// overlaps on the GPU (other streams, other host threads) race on the array.
 #include <mutex>
 
 #include "sepw_internal.cuh"
@@ -33,7 +33,8 @@ constexpr int64_t kMaxItems = kMaxTiles + kMaxVis / kChunk + 1;
 
 // byte offsets of the plan arrays inside the scratch
 constexpr size_t kOffTile = 0;
-constexpr size_t kOffRec0 = align256(kOffTile + sizeof(int32_t) * kMaxVis);
+constexpr size_t kOffRank = align256(kOffTile + sizeof(int32_t) * kMaxVis);
+constexpr size_t kOffRec0 = align256(kOffRank + sizeof(int32_t) * kMaxVis);
 constexpr size_t kOffRec = align256(kOffRec0 + sizeof(uint64_t) * kMaxVis);
 constexpr size_t kOffPerm = align256(kOffRec + sizeof(uint64_t) * kMaxVis);
 constexpr size_t kOffDrop = align256(kOffPerm + sizeof(int32_t) * kMaxVis);
@@ -160,6 +161,7 @@ extern "C" int sepw_grid_noalloc(const sepw_params *prm, const float *taps, int6
     pl.valid = true;
     pl.form = SEPW_FORM_TILED;
     pl.d_tile = (int32_t *)(b + kOffTile);
+    pl.d_rank = (int32_t *)(b + kOffRank);
     pl.d_rec0 = (uint64_t *)(b + kOffRec0);
     pl.d_rec = (uint64_t *)(b + kOffRec);
     pl.d_perm = (int32_t *)(b + kOffPerm);
