@@ -163,7 +163,8 @@ SEPW_API int sepw_locate(sepw_ctx *ctx, int64_t nvis, const double *u, const dou
                 sepw_stream_t stream);
 
 /* Locate and bin nvis visibilities into the context's plan (tiled forms:
- * counting sort by tile, then by footprint origin inside each tile).  The
+ * counting sort by tile and by 4 x 4 sub-block of the footprint origin
+ * inside the tile, cut into work items, each sorted by origin).  The
  * plan is reused by sepw_grid_planned / sepw_degrid_planned until the next
  * sepw_plan; u, v, w need not stay alive.  Binning is amortisable over the
  * gridding/degridding calls of a major cycle (Sec. 6).  For the plain form
