@@ -95,6 +95,7 @@ DevParams make_dev(const sepw_params *p)
     d.P = p->n_wplanes;
     d.T = effective_tile(p);
     d.ntx = (d.N - d.S) / d.T + 1;
+    d.t_inv = tile_reciprocal(d.T);
     d.fov = p->fov;
     d.half = (double)(d.N / 2);
     d.os_d = (double)d.OS;
@@ -102,6 +103,7 @@ DevParams make_dev(const sepw_params *p)
     for (int k = 0; k < 31; ++k)
         if ((1 << k) == d.OS)
             d.os_log2 = k;
+    locate_fast_bounds(d.N, d.os_log2, d.fast_elim, d.fast_near);
     d.plane_r = d.P > 1 ? (double)(d.P - 1) / p->w_max : 0.0;
     d.w_max = p->w_max;
     d.gamma = p->gamma;

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) locate_bin_kernel(
         Loc L = locate(u[i], v[i], w[i], p);
         if (L.keep) {
             int fx = L.cu - p.S / 2 + 1, fy = L.cv - p.S / 2 + 1;
-            int tx = fx / p.T, ty = fy / p.T;
+            const int tx = div_tile(fx, p), ty = div_tile(fy, p);
             int g = 0;
             if (ngrids > 1) {  // grid of visibility i: offsets[g] <= i < offsets[g+1]
                 int lo = 0, hi = ngrids - 1;
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256) locate_bin_kernel(
                 g = lo;
             }
             const int lx = fx - tx * p.T, ly = fy - ty * p.T;
-            bin = ((g * p.ntx + ty) * p.ntx + tx) * kSubBins + sub_bin(lx, ly, L.conj, p.T);
+            bin = ((g * p.ntx + ty) * p.ntx + tx) * kSubBins + sub_bin(lx, ly, L.conj, p);
             rec0[i] = pack_rec(lx, ly, L.ou, L.ov, L.plane, L.conj);
         }
         bin_of[i] = bin;

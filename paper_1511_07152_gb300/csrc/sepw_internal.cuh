@@ -15,10 +15,13 @@ namespace sepw {
 struct DevParams {
     int32_t N, S, OS, P, T;
     int32_t ntx;      // tiles per axis for the tiled forms
+    uint32_t t_inv;   // ceil(2^32 / T), see div_tile
     double fov;       // inverse cell size: x = u * fov + N/2
     double half;      // N/2 as a double
     double os_d;      // OS as a double
     int32_t os_log2;  // log2(OS) if OS is a power of two, else -1
+    int32_t fast_elim;  // locate_axis: exponent bound of its integer path (-1: off)
+    int32_t fast_near;  // locate_axis: its fall-back margin, in units of 2^-40
     double plane_r;   // (P-1)/w_max (0 if P == 1)
     double w_max;
     double gamma;
@@ -82,11 +85,72 @@ __device__ __forceinline__ double scale_pow2(double x, int k, double os_d)
 // Only u*fov and + N/2 use the FP64 pipe; the power-of-two scaling, the
 // rounded + 0.5 with its floor, and the range checks are exact integer
 // operations on the bits.
+//
+// Integer path (OS a power of two): with y = fl(coord*fov) the IEEE product,
+// t = floor(fl(y + N/2) OS + 1/2).  The exact value floor((y + N/2) OS + 1/2)
+// = (N/2) OS + floor(y OS + 1/2) follows from the bits of y (y OS is exact),
+// and differs from t only if fl(y + N/2) moves (y + N/2) OS + 1/2 across an
+// integer: fl rounds by at most half an ulp of a sum below N, so that needs
+// y OS + 1/2 within N OS 2^-53 of an integer.  Those cases (and |y OS| at or
+// beyond 2^fast_elim, which bounds the sum and the fixed-point range) take
+// the FP64 path below.
+__device__ __forceinline__ bool locate_axis_int(double y, const DevParams &p, long long &ti,
+                                                bool &done)
+{
+    done = false;
+    const long long b = __double_as_longlong(y);
+    const int eb = (int)((b >> 52) & 0x7FF);
+    if (eb == 0x7FF)
+        return false;  // non-finite
+    long long z;       // floor((y OS + 1/2) 2^40), then split
+    if (eb == 0) {
+        z = (b < 0 ? -1ll : 0ll) + (1ll << 39);  // zero or subnormal: |y OS| < 2^-40
+    } else {
+        const int ey = eb - 1023 + p.os_log2;  // exponent of y OS
+        if (ey >= p.fast_elim)
+            return true;  // FP64 path
+        const long long m = (b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll;
+        const int sh = ey - 12;  // y OS 2^40 = m 2^(ey - 12)
+        long long a;
+        if (sh >= 0) {
+            a = m << sh;  // ey < fast_elim <= 21: below 2^62
+            a = b < 0 ? -a : a;
+        } else if (sh > -53) {
+            const long long q = m >> (-sh);
+            const bool rem = (m & ((1ll << (-sh)) - 1)) != 0;
+            a = b < 0 ? -q - (rem ? 1 : 0) : q;  // floor
+        } else {
+            a = b < 0 ? -1 : 0;
+        }
+        z = a + (1ll << 39);
+    }
+    const long long fr = z & ((1ll << 40) - 1);
+    if (fr <= p.fast_near || fr >= (1ll << 40) - p.fast_near)
+        return true;  // within the rounding margin of an integer: FP64 path
+    ti = ((long long)(p.N / 2) << p.os_log2) + (z >> 40);
+    done = true;
+    return true;
+}
+
 __device__ __forceinline__ bool locate_axis(double coord, const DevParams &p,
                                             int32_t &c, int32_t &o)
 {
-    const double x = __dadd_rn(__dmul_rn(coord, p.fov), p.half);
+    const double y = __dmul_rn(coord, p.fov);
     long long ti, cc, oo;
+    bool done = false;
+    if (p.fast_elim >= 0 && !locate_axis_int(y, p, ti, done))
+        return false;
+    if (done) {
+        cc = ti >> p.os_log2;
+        oo = ti - (cc << p.os_log2);
+        const long long f = cc - p.S / 2 + 1;
+        if (f < 0 || f + p.S - 1 > p.N - 1)
+            return false;
+        c = (int32_t)cc;
+        o = (int32_t)oo;
+        return true;
+    }
+    const double x = __dadd_rn(y, p.half);
     if (p.os_log2 >= 0) {
         if (!floor_add_half_bits(scale_pow2(x, p.os_log2, p.os_d), ti))
             return false;
@@ -200,9 +264,41 @@ constexpr int kMaxWindow = 64;    // T + S - 1 <= kMaxWindow
 // (one register block accumulates a whole run).
 constexpr int kSubBins = 32;
 
-__host__ __device__ __forceinline__ int sub_bin(int lx, int ly, bool conj, int T)
+// ceil(2^32 / T) for the tile edge T (8 <= T <= 64)
+// Bounds of locate_axis's integer path for grid size N and OS = 2^os_log2
+// (os_log2 < 0: path off): |y OS| < 2^elim with 2^elim <= N OS / 2 and
+// elim <= 21; margin (N OS) 2^-53 in units of 2^-40, rounded up, plus 2.
+inline void locate_fast_bounds(int N, int os_log2, int32_t &elim, int32_t &near)
 {
-    return ((((ly * 4) / T) * 4 + (lx * 4) / T) << 1) | (conj ? 1 : 0);
+    elim = -1;
+    near = 0;
+    if (os_log2 < 0)
+        return;
+    const long long half_span = ((long long)N << os_log2) / 2;  // N OS / 2
+    int e = 0;
+    while (e < 21 && (1ll << (e + 1)) <= half_span)
+        ++e;
+    elim = (1ll << e) <= half_span ? e : -1;
+    near = (int32_t)((((long long)N << os_log2) >> 13) + 2);
+}
+
+inline uint32_t tile_reciprocal(int T)
+{
+    return (uint32_t)((0x100000000ull + (uint64_t)T - 1) / (uint64_t)T);
+}
+
+// floor(n / T) for 0 <= n < 2^26 as one multiply-high.  With
+// M = ceil(2^32 / T) = (2^32 + e) / T, 0 <= e < T, and n = q T + r
+// (0 <= r <= T - 1): n M / 2^32 = q + (r + n e / 2^32) / T, whose fraction
+// stays below 1 while n e < 2^32, true for n < 2^26 and T <= 64.
+__device__ __forceinline__ int div_tile(int n, const DevParams &p)
+{
+    return (int)__umulhi((unsigned)n, p.t_inv);
+}
+
+__device__ __forceinline__ int sub_bin(int lx, int ly, bool conj, const DevParams &p)
+{
+    return ((div_tile(ly * 4, p) * 4 + div_tile(lx * 4, p)) << 1) | (conj ? 1 : 0);
 }
 
 struct Plan {

@@ -118,6 +118,7 @@ extern "C" int sepw_grid_noalloc(const sepw_params *prm, const float *taps, int6
     dp.P = prm->n_wplanes;
     dp.T = prm->tile == 0 ? 32 : prm->tile;
     dp.ntx = (dp.N - dp.S) / dp.T + 1;
+    dp.t_inv = tile_reciprocal(dp.T);
     dp.fov = prm->fov;
     dp.half = (double)(dp.N / 2);
     dp.os_d = (double)dp.OS;
@@ -125,6 +126,7 @@ extern "C" int sepw_grid_noalloc(const sepw_params *prm, const float *taps, int6
     for (int k = 0; k < 31; ++k)
         if ((1 << k) == dp.OS)
             dp.os_log2 = k;
+    locate_fast_bounds(dp.N, dp.os_log2, dp.fast_elim, dp.fast_near);
     dp.plane_r = dp.P > 1 ? (double)(dp.P - 1) / prm->w_max : 0.0;
     dp.w_max = prm->w_max;
     dp.gamma = prm->gamma;

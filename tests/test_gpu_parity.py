@@ -129,6 +129,46 @@ def test_locate_bit_exact(torch_cuda, S_, name):
     assert 0 < want["keep"].sum() < len(u) or name == "small_disk"
 
 
+@pytest.mark.parametrize("N,OS", [(4096, 16), (256, 8), (1000, 4), (96, 16)])
+def test_locate_rounding_boundaries(torch_cuda, S_, N, OS):
+    """Coordinates whose scaled position y OS + 1/2 (y = u fov) lies within a
+    few ulps of an integer, both sides, or whose sum y + N/2 rounds at its
+    last bit, over the whole grid and beyond its edges: every result, whether
+    the locate takes its integer path or falls back to FP64 arithmetic,
+    equals the oracle's bit for bit."""
+    torch = torch_cuda
+    rng = np.random.default_rng(17)
+    fov = math.radians(1.0)
+    H = N // 2
+    ys = []
+    for k in rng.integers(-H * OS - 4 * OS, H * OS + 4 * OS, 3000):
+        y = (float(k) - 0.5) / OS
+        up = dn = y
+        ys.append(y)
+        for _ in range(4):
+            up = float(np.nextafter(up, np.inf))
+            dn = float(np.nextafter(dn, -np.inf))
+            ys += [up, dn]
+    for k in rng.integers(1, 1 << 40, 3000):
+        ys.append(float(k) * 2.0 ** (int(rng.integers(-20, 12)) - 40) - H)
+    ys += list(rng.uniform(-H - 8, H + 8, 20000))
+    ys += [0.0, -0.0, 5e-324, -5e-324, float(H), -float(H), 0.5 / OS, -0.5 / OS]
+    y = np.array(ys)
+    n = len(y)
+    u = y / fov
+    v = rng.permutation(y) / fov
+    w = rng.uniform(-300.0, 300.0, n)
+    p = dict(grid_size=N, fov=fov, support=8, oversample=OS, n_wplanes=9, w_max=300.0)
+    ctx = S_.sepw_create(S_.make_params(**p, form=S_.FORM_TILED))
+    out = S_.sepw_locate(ctx, torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(),
+                         torch.from_numpy(w).cuda())
+    want = O.locate(O.Params(**p), u, v, w)
+    for k in ("cu", "cv", "ou", "ov", "plane"):
+        assert np.array_equal(out[k].cpu().numpy(), want[k]), k
+    assert np.array_equal(out["keep"].cpu().numpy().astype(bool), want["keep"])
+    assert 0 < want["keep"].sum() < n
+
+
 def test_locate_meerkat_full_bit_exact(torch_cuda, S_):
     """All 32,256,000 visibilities of the full-size workload."""
     torch = torch_cuda
