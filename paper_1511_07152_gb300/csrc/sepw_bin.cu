@@ -114,39 +114,77 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
     int32_t ntiles, const int32_t *__restrict__ tile_count, int32_t *__restrict__ cursor,
     WorkItem *__restrict__ items, int32_t *nitems)
 {
-    __shared__ int64_t s_cnt[kScanThreads];
-    __shared__ int32_t s_full[kScanThreads];
-    __shared__ int32_t s_part[kScanThreads];
-    const int t = threadIdx.x;
+    __shared__ int64_t s_cnt[kScanThreads / 32];
+    __shared__ int32_t s_tot_full, s_tot_part;
+    __shared__ int32_t s_full[kScanThreads / 32];
+    __shared__ int32_t s_part[kScanThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int per = (ntiles + kScanThreads - 1) / kScanThreads;
     const int lo = min(ntiles, t * per), hi = min(ntiles, lo + per);
     int64_t c = 0;
     int32_t nf = 0, np = 0;
-    for (int i = lo; i < hi; ++i) {
-        const int n = tile_count[i];
-        c += n;
-        nf += n / kChunk;
-        np += (n % kChunk) != 0;
+    // this thread's tiles, eight loads in flight at a time
+    for (int i0 = lo; i0 < hi; i0 += 8) {
+        int n[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            n[k] = i0 + k < hi ? tile_count[i0 + k] : 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            c += n[k];
+            nf += n[k] / kChunk;
+            np += (n[k] % kChunk) != 0;
+        }
     }
-    s_cnt[t] = c;
-    s_full[t] = nf;
-    s_part[t] = np;
+    // exclusive scans over the threads: warp shuffles, then the warp totals
+    int64_t ic = c;
+    int32_t ifl = nf, ip = np;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t x = __shfl_up_sync(0xffffffffu, ic, off);
+        const int32_t y = __shfl_up_sync(0xffffffffu, ifl, off);
+        const int32_t z = __shfl_up_sync(0xffffffffu, ip, off);
+        if (lane >= off) {
+            ic += x;
+            ifl += y;
+            ip += z;
+        }
+    }
+    if (lane == 31) {
+        s_cnt[warp] = ic;
+        s_full[warp] = ifl;
+        s_part[warp] = ip;
+    }
     __syncthreads();
-    // Hillis-Steele inclusive scans over the 1024 partials
-    for (int off = 1; off < kScanThreads; off <<= 1) {
-        const int64_t a = t >= off ? s_cnt[t - off] : 0;
-        const int32_t b = t >= off ? s_full[t - off] : 0;
-        const int32_t d = t >= off ? s_part[t - off] : 0;
-        __syncthreads();
-        s_cnt[t] += a;
-        s_full[t] += b;
-        s_part[t] += d;
-        __syncthreads();
+    if (warp == 0) {
+        int64_t wc = s_cnt[lane];
+        int32_t wf = s_full[lane], wp = s_part[lane];
+        const int64_t c0 = wc;
+        const int32_t f0 = wf, p0 = wp;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t x = __shfl_up_sync(0xffffffffu, wc, off);
+            const int32_t y = __shfl_up_sync(0xffffffffu, wf, off);
+            const int32_t z = __shfl_up_sync(0xffffffffu, wp, off);
+            if (lane >= off) {
+                wc += x;
+                wf += y;
+                wp += z;
+            }
+        }
+        s_cnt[lane] = wc - c0;  // exclusive warp offsets
+        s_full[lane] = wf - f0;
+        s_part[lane] = wp - p0;
+        if (lane == 31) {
+            s_tot_full = wf;
+            s_tot_part = wp;
+        }
     }
-    const int32_t total_full = s_full[kScanThreads - 1];
-    int64_t off_c = s_cnt[t] - c;
-    int32_t off_f = s_full[t] - nf;
-    int32_t off_p = total_full + s_part[t] - np;
+    __syncthreads();
+    const int32_t total_full = s_tot_full;
+    int64_t off_c = s_cnt[warp] + ic - c;
+    int32_t off_f = s_full[warp] + ifl - nf;
+    int32_t off_p = total_full + s_part[warp] + ip - np;
     for (int i = lo; i < hi; ++i) {
         const int n = tile_count[i];
         cursor[i] = (int32_t)off_c;
@@ -169,8 +207,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
         }
         off_c += n;
     }
-    if (t == kScanThreads - 1)
-        *nitems = total_full + s_part[t];
+    if (t == 0)
+        *nitems = total_full + s_tot_part;
 }
 
 // Pass 3: scatter visibility ids and records to their slots: tile start +
