@@ -671,26 +671,34 @@ def run_ours(args):
         for k in range(2):
             estep(k)
         torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b_ = torch.cuda.Event(enable_timing=True)
         # steady state: at least 8 steps, so that the pipeline fill (the first
         # host->device copy) and drain (the last read-back), both inside the
         # timed region, are shared by several steps
         ne = min(24, max(8, args.steps))
-        a.record(stream)
-        copy_s.wait_event(a)
-        for k in range(ne):
-            estep(k)
-        for b in range(2):
-            stream.wait_event(ev["read"][b])
-        b_.record(stream)
-        torch.cuda.synchronize()
-        ems = a.elapsed_time(b_) / ne
+
+        def timed_run():
+            a = torch.cuda.Event(enable_timing=True)
+            b_ = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            copy_s.wait_event(a)
+            for k in range(ne):
+                estep(k)
+            for b in range(2):
+                stream.wait_event(ev["read"][b])
+            b_.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b_) / ne
+
+        # the host link is shared with other jobs on the machine: three runs,
+        # the median reported and all three recorded
+        runs = [timed_run() for _ in range(3)]
+        ems = statistics.median(runs)
         ok = bool(torch.equal(houts[(ne - 1) % 2], outs[(ne - 1) % 2].cpu()))
         evalue, ems = whole_job(ems, 2.0 * nvis, ws, dist, device="cuda")
         e2e = {"value": evalue, "unit": "vis/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": ems, "steps": ne, "pipelined": "2 batches in flight",
+               "ms_per_step": ems, "steps": ne, "runs_ms_per_step": runs,
+               "pipelined": "2 batches in flight",
                "readback_matches_device": ok}
         del devs, outs, houts, host
 
