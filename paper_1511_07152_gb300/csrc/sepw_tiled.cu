@@ -8,10 +8,11 @@
 // offsets, W V or the output index and weight, key) into shared memory; the
 // inner loop reads them as broadcasts.
 //
-// What limits these kernels is the load data returned to the registers and
-// the instruction issue, not the FMA pipe: every lane loads the taps of the
-// cells it owns for every visibility.  Larger per-lane register blocks load
-// fewer taps per cell, so the forms below use, by support:
+// What limits these kernels is the load data returned to the registers, the
+// latency of those loads (gridder) and the instruction issue (degridder),
+// not the FMA pipe: every lane loads the taps of the cells it owns for every
+// visibility.  Larger per-lane register blocks load fewer taps per cell, so
+// the forms below use, by support:
 //   * gridding, S = 8, 16: lane (rg, cg) = (lane >> 3, lane & 7) owns
 //     rows rg + 4 r and columns cg + 8 c (S / 4 + S / 8 taps per lane per
 //     visibility);
@@ -24,7 +25,9 @@
 //
 // Gridding: per visibility the lane forms the partial product W V F1(u - u_i)
 // for its columns once (Sec. 5: reused down every row) and accumulates its
-// cells' products with the v-taps into a register block.  Visibilities with
+// cells' products with the v-taps into a register block, as paired FP32 FMAs
+// over its row pairs (v-taps from a lane-ordered planar copy of the table,
+// rebuilt per call).  Visibilities with
 // one key share the register block; conj visibilities accumulate
 // conj(W V) F1 F1 and the block is conjugated when it is flushed, so the
 // inner loop needs no sign handling.  The block is added to the HBM grid with
