@@ -230,22 +230,30 @@ __global__ void __launch_bounds__(256) scatter_kernel(
     rec[slot] = rec0[i];
 }
 
-// Pass 4: inside each work item, counting sort by (footprint origin, conj):
-// key = ((ly * T + lx) << 1) | conj.  Visibilities that share a key share one
-// register block in the tiled kernels, and the block never mixes conjugated
-// and plain kernels.  One block per item; the item's slots are rewritten in
-// place.  The order among equal keys is arbitrary.
+// Pass 4: inside each work item, counting sort by (footprint origin, conj),
+// sub-block major: the key orders by the 4 x 4 sub-block of the origin and
+// conj (the bin of pass 1), then by the origin's row and column inside the
+// sub-block (edge at most E = ceil(T / 4)), 32 E^2 <= 8192 keys.
+// Visibilities that share a key share one register block in the tiled
+// kernels, and the block never mixes conjugated and plain kernels; the
+// sub-blocks stay contiguous inside an item, so a run of slots that starts
+// and ends in one sub-block lies inside it.  One block per item; the item's
+// slots are rewritten in place.  The order among equal keys is arbitrary.
 constexpr int kSortThreads = 512;
 constexpr int kMaxSortBins = 2 * 64 * 64;
 constexpr int kMaxBinsPerThread = kMaxSortBins / kSortThreads;
 
-__device__ __forceinline__ int sort_key(uint64_t r, int T)
+__device__ __forceinline__ int sort_key(uint64_t r, const DevParams &p, int E)
 {
-    return ((rec_ly(r) * T + rec_lx(r)) << 1) | (rec_conj(r) ? 1 : 0);
+    const int lx = rec_lx(r), ly = rec_ly(r);
+    const int sx = div_tile(lx * 4, p), sy = div_tile(ly * 4, p);
+    const int x0 = (sx * p.T + 3) >> 2, y0 = (sy * p.T + 3) >> 2;  // first cell
+    const int sub = ((sx * 4 + sy) << 1) | (rec_conj(r) ? 1 : 0);  // as sub_bin
+    return (sub * E + (ly - y0)) * E + (lx - x0);
 }
 
 __global__ void __launch_bounds__(kSortThreads) item_sort_kernel(
-    const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems, int T,
+    DevParams p, const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems,
     int32_t *__restrict__ perm, uint64_t *__restrict__ rec)
 {
     extern __shared__ int32_t hist[];  // per * kSortThreads bins
@@ -257,7 +265,8 @@ __global__ void __launch_bounds__(kSortThreads) item_sort_kernel(
         return;
     const WorkItem it = items[item];
     const int n = it.count;
-    const int nb = 2 * T * T;
+    const int E = (p.T + 3) / 4;
+    const int nb = 32 * E * E;
     const int per = (nb + kSortThreads - 1) / kSortThreads;
     for (int b = threadIdx.x; b < per * kSortThreads; b += kSortThreads)
         hist[b] = 0;
@@ -273,7 +282,7 @@ __global__ void __launch_bounds__(kSortThreads) item_sort_kernel(
             const uint64_t r = rec[it.start + q];
             s_rec[q] = r;
             s_perm[q] = perm[it.start + q];
-            key = sort_key(r, T);
+            key = sort_key(r, p, E);
         }
         const unsigned peers = __match_any_sync(0xffffffffu, key);
         if (act && lane_id == __ffs(peers) - 1)
@@ -329,7 +338,7 @@ __global__ void __launch_bounds__(kSortThreads) item_sort_kernel(
         int key = -1;
         if (act) {
             r = s_rec[q];
-            key = sort_key(r, T);
+            key = sort_key(r, p, E);
         }
         const unsigned peers = __match_any_sync(0xffffffffu, key);
         const int leader = __ffs(peers) - 1;
@@ -393,7 +402,8 @@ cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
             plan.d_perm, plan.d_rec);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
-        const int nb = 2 * p.T * p.T;
+        const int E = (p.T + 3) / 4;
+        const int nb = 32 * E * E;
         const size_t shm =
             sizeof(int32_t) * kSortThreads * ((nb + kSortThreads - 1) / kSortThreads);
         e = cudaFuncSetAttribute(item_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -401,7 +411,7 @@ cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
         if (e != cudaSuccess)
             return e;
         item_sort_kernel<<<plan.items_capacity, kSortThreads, shm, s>>>(
-            plan.d_items, plan.d_nitems, p.T, plan.d_perm, plan.d_rec);
+            p, plan.d_items, plan.d_nitems, plan.d_perm, plan.d_rec);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
     }

@@ -296,9 +296,10 @@ __device__ __forceinline__ int div_tile(int n, const DevParams &p)
     return (int)__umulhi((unsigned)n, p.t_inv);
 }
 
+// column-major: the eight bins of one column of sub-blocks are consecutive
 __device__ __forceinline__ int sub_bin(int lx, int ly, bool conj, const DevParams &p)
 {
-    return ((div_tile(ly * 4, p) * 4 + div_tile(lx * 4, p)) << 1) | (conj ? 1 : 0);
+    return ((div_tile(lx * 4, p) * 4 + div_tile(ly * 4, p)) << 1) | (conj ? 1 : 0);
 }
 
 struct Plan {

@@ -595,7 +595,8 @@ cudaError_t launch_tc_prec(int prec, const DevParams &p, const Plan &plan, const
 //     B[(y,0)][(x,0)] = X_r, B[(y,1)][(x,0)] = X_i,
 //     B[(y,0)][(x,1)] = X_i, B[(y,1)][(x,1)] = -X_r,
 // one tcgen05.mma shape M = 128 (visibilities), N = 128, K = 16 per step,
-// eight steps per stage.  B (the window) is built once per work item in one
+// eight steps per stage; a stage inside one sub-block of the tile contracts
+// only the 32 window columns its footprints reach (N = 64).  B (the window) is built once per work item in one
 // of two buffers; A (2 S values per visibility, cleared after use) in one of
 // two stage buffers; a window buffer is rebuilt only after the epilogue has
 // finished the item before last.  Roles: 8 producer warps (two threads per
@@ -645,6 +646,28 @@ __device__ __forceinline__ uint32_t pack_pair(float x, float y)
     return hi;
 }
 
+// First window column x0 of a stage whose visibilities all lie in one column
+// of sub-blocks of the tile (the plan keeps the bins of a column consecutive
+// inside an item, so the first and last slot decide), when their footprints
+// fit the 32 columns x0 .. x0 + 31: the stage then contracts only those
+// (N = 64).  -1: the whole window (N = 128).  x0 is a multiple of 4 (the
+// operand's 8-row core-matrix groups) and at most 32.
+__device__ __forceinline__ int dg_stage_x0(const DevParams &p, const WorkItem &it, int st,
+                                           const uint64_t *__restrict__ rec, int S)
+{
+    const int first = it.start + st * kDgVis;
+    const int last = min(first + kDgVis, it.start + it.count) - 1;
+    const uint64_t r0 = __ldg(reinterpret_cast<const unsigned long long *>(rec) + first);
+    const uint64_t r1 = __ldg(reinterpret_cast<const unsigned long long *>(rec) + last);
+    const int sx = sub_bin(rec_lx(r0), rec_ly(r0), rec_conj(r0), p) >> 3;
+    if (sx != sub_bin(rec_lx(r1), rec_ly(r1), rec_conj(r1), p) >> 3)
+        return -1;
+    const int lo = (sx * p.T + 3) >> 2;            // first column of the sub-block
+    const int hi = (((sx + 1) * p.T + 3) >> 2) - 1;  // last column
+    const int x0 = min(lo & ~3, 32);
+    return hi + S <= x0 + 32 ? x0 : -1;
+}
+
 template <int S, int PREC>
 __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
     DevParams p, const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems,
@@ -667,6 +690,7 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr uint32_t idesc = instr_desc_n(PREC == 0 ? 1u : 0u, kDgN);
+    constexpr uint32_t idesc64 = instr_desc_n(PREC == 0 ? 1u : 0u, kDgN / 2);
     const int n_items = *nitems;
     const int W = p.T + S - 1;
 
@@ -844,6 +868,7 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
             if (lane == 0) {
                 for (int st = 0; st < nst && !s_abort; ++st) {
                     const int t = tg + st, b = t & 1;
+                    const int x0 = dg_stage_x0(p, it, st, rec, S);
                     if (!mbar_wait(full + b, (t >> 1) & 1) ||
                         (t >= 2 && !mbar_wait(tfree + b, ((t - 2) >> 1) & 1))) {
                         s_abort = 1;
@@ -851,11 +876,15 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
                     }
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(Abuf + b * kDgABytes);
-                    const uint32_t b0 = smem_u32(Bbuf + (n & 1) * kDgBBytes);
+                    // rows 2 x0 .. 2 x0 + 63 of the window operand: x0 / 4
+                    // groups of 8 rows (kSBO bytes each) in
+                    const uint32_t b0 = smem_u32(Bbuf + (n & 1) * kDgBBytes) +
+                                        (x0 >= 0 ? (uint32_t)(x0 / 4) * kSBO : 0u);
+                    const uint32_t id = x0 >= 0 ? idesc64 : idesc;
                     const uint32_t d = tmem + (uint32_t)(b * kDgN);
 #pragma unroll
                     for (int kq = 0; kq < kDgK / 16; ++kq)
-                        mma_f16(d, smem_desc(a0 + 256 * kq), smem_desc(b0 + 256 * kq), idesc,
+                        mma_f16(d, smem_desc(a0 + 256 * kq), smem_desc(b0 + 256 * kq), id,
                                 kq > 0 ? 1u : 0u);
                     mma_commit(empty + b);
                     mma_commit(accf + b);
@@ -912,12 +941,17 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
                 const int t = tg + st, b = t & 1;
                 int inext = 0;
                 const uint64_t rnext = stage_rec(st + 1, inext);
+                const int x0 = dg_stage_x0(p, it, st, rec, S);
+                const int nc = x0 >= 0 ? kDgN / 64 : kDgN / 32;  // accumulator chunks
+                const int xb = x0 >= 0 ? x0 : 0;                  // window column of chunk 0
                 warp_wait(accf + b, (t >> 1) & 1);
                 if (s_abort)
                     break;
                 tc_fence_after();
 #pragma unroll
                 for (int c = 0; c < kDgN / 32; ++c) {
+                    if (c >= nc)
+                        break;
                     uint32_t rr[32];
                     SEPW_TMEM_LD32(tmem + ((uint32_t)(32 * qq) << 16) + (uint32_t)(b * kDgN + 32 * c),
                                    rr);
@@ -940,7 +974,7 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
 #pragma unroll
                     for (int j = 0; j < S; ++j) {
                         const float ur = tu[j].x, ui = sg * tu[j].y;
-                        const int col = 2 * (lx + j);
+                        const int col = 2 * (lx - xb + j);
                         const float qr = row[col ^ lane], qi = row[(col + 1) ^ lane];
                         vr += ur * qr - ui * qi;
                         vi += ur * qi + ui * qr;
