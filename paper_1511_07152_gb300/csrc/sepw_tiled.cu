@@ -66,6 +66,9 @@ __device__ __forceinline__ int meta_dv(int y) { return y >> 13; }
 constexpr int kTiledThreads = 256;
 constexpr int kTiledWarps = kTiledThreads / 32;
 constexpr int kTiledBlocksPerSM = 4;
+// block gridder on dense plans: work units per item (see its work loop)
+constexpr int kGridParts = 8;
+constexpr int kGridPartsMinDensity = 256;  // visibilities per tile
 
 __device__ __forceinline__ int key_ly(int key) { return (key >> 1) >> 6; }
 __device__ __forceinline__ int key_lx(int key) { return (key >> 1) & 63; }
@@ -585,14 +588,14 @@ struct Blk2 {
 // latency, and 40 warps hide it better than 32 (2.37 vs 2.44 ms on 32M
 // visibilities; six CTAs at 40 registers spill and run slower, 2.56 ms)
 constexpr int kGridBlkPerSM = 5;
-constexpr int kGridParts = 8;  // work units per item (see the work loop)
 
 template <int S, bool PLANAR>
 __global__ void __launch_bounds__(kTiledThreads, kGridBlkPerSM) grid_tiled_block_kernel(
     DevParams p, const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems,
     int32_t *counter, const uint64_t *__restrict__ rec, const int32_t *__restrict__ perm,
     const float2 *__restrict__ vis, const float *__restrict__ weight,
-    const float2 *__restrict__ taps, const float *__restrict__ planar, float2 *grid)
+    const float2 *__restrict__ taps, const float *__restrict__ planar, float2 *grid,
+    int parts)
 {
     constexpr int RB = Blk2<S>::RB, RP = Blk2<S>::RP, CB = Blk2<S>::CB;
     constexpr bool FULL = Blk2<S>::FULL;
@@ -611,19 +614,21 @@ __global__ void __launch_bounds__(kTiledThreads, kGridBlkPerSM) grid_tiled_block
     const int n_items = *nitems;
 
     for (;;) {
-        // a warp takes one of kGridParts consecutive parts of an item: whole
-        // 2048-visibility items per warp left the end of the launch to few
-        // warps (parts: 1 -> 2.38 ms, 2 -> 2.24, 4 -> 2.16, 8 -> 2.13,
-        // 16 -> 2.14 on 32M visibilities; runs break only at part edges)
+        // a warp takes one of `parts` consecutive parts of an item: on dense
+        // plans whole 2048-visibility items per warp left the end of the
+        // launch to few warps (parts: 1 -> 2.38 ms, 2 -> 2.24, 4 -> 2.16,
+        // 8 -> 2.13, 16 -> 2.14 on 32M visibilities; runs break only at part
+        // edges).  Sparse plans (many small items) keep parts = 1: split
+        // units there only add atomics on the one counter.
         int unit = 0;
         if (lane == 0)
             unit = atomicAdd(counter, 1);
         unit = __shfl_sync(0xffffffffu, unit, 0);
-        const int item = unit / kGridParts, part = unit % kGridParts;
+        const int item = unit / parts, part = unit % parts;
         if (item >= n_items)
             break;
         const WorkItem it = items[item];
-        const int len = (it.count + kGridParts - 1) / kGridParts;
+        const int len = (it.count + parts - 1) / parts;
         const int b0 = it.start + part * len;
         const int b1 = min(it.start + it.count, b0 + len);
         if (b0 >= b1)
@@ -826,6 +831,8 @@ static cudaError_t launch_grid_S(const DevParams &p, const Plan &plan, const flo
         return e;
     if constexpr (Blk2<S>::OK) {
         const unsigned nb = (unsigned)(num_sms * kGridBlkPerSM);
+        const int parts =
+            plan.nvis >= (int64_t)kGridPartsMinDensity * plan.ntiles ? kGridParts : 1;
         if (planar) {  // rebuilt per call: the caller's table may have changed
             const int64_t n = (p.facet ? 2 : 1) * (int64_t)p.P * p.OS * S;
             if ((e = launch_planar_taps(taps, planar, n, S, s)) != cudaSuccess)
@@ -834,11 +841,11 @@ static cudaError_t launch_grid_S(const DevParams &p, const Plan &plan, const flo
         if (planar)
             grid_tiled_block_kernel<S, true><<<nb, kTiledThreads, 0, s>>>(
                 p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm,
-                vis, weight, taps, planar, grid);
+                vis, weight, taps, planar, grid, parts);
         else
             grid_tiled_block_kernel<S, false><<<nb, kTiledThreads, 0, s>>>(
                 p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm,
-                vis, weight, taps, nullptr, grid);
+                vis, weight, taps, nullptr, grid, parts);
     } else
         grid_tiled_kernel<S><<<num_sms * kTiledBlocksPerSM, kTiledThreads, 0, s>>>(
             p, plan.d_items, plan.d_nitems, plan.d_item_counter, plan.d_rec, plan.d_perm, vis,
