@@ -82,9 +82,9 @@ __device__ __forceinline__ double scale_pow2(double x, int k, double os_d)
 // with every operation rounded separately (no FMA contraction), then
 // c = floor(t/OS), o = t - c*OS; the footprint c - S/2 + 1 .. c + S/2 must lie
 // inside [0, N).  Returns false (drop) otherwise or for non-finite input.
-// Only u*fov and + N/2 use the FP64 pipe; the power-of-two scaling, the
-// rounded + 0.5 with its floor, and the range checks are exact integer
-// operations on the bits.
+// Only u*fov uses the FP64 pipe on the common path (+ N/2 only within the
+// fall-back margin below); the power-of-two scaling, the rounded + 0.5 with
+// its floor, and the range checks are exact integer operations on the bits.
 //
 // Integer path (OS a power of two): with y = fl(coord*fov) the IEEE product,
 // t = floor(fl(y + N/2) OS + 1/2).  The exact value floor((y + N/2) OS + 1/2)
