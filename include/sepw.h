@@ -367,23 +367,32 @@ SEPW_API int sepw_wstack_model_grids(sepw_ctx *ctx, const float *image, float *s
  * must not block on cudaMalloc (which may synchronise the device) while it
  * observes, or a plugin inside a framework that owns the device memory pool.
  *
- * Same result as sepw_grid with the tiled FP32 form (p->form is ignored), but
- * no context is needed and nothing is allocated: the binning workspace is one
+ * Same result as sepw_grid with the tiled FP32 form (p->form is ignored: the
+ * parameters are checked as for SEPW_FORM_TILED, tile 0 meaning 32), but no
+ * context is needed and nothing is allocated: the binning workspace is one
  * file-scope device array of about 26 MB compiled into the library, which
  * every GPU that loads the library keeps until the process exits.  The call
  * makes no cudaMalloc / cudaFree and no allocating library call.
  *   - p, taps, u, v, w, vis, weight (NULL = 1), grid (accumulated, +=):
- *     as for sepw_grid; n_dropped: device int64 or NULL.
+ *     as for sepw_grid; taps must be 16-byte aligned (SEPW_EINVAL
+ *     otherwise); n_dropped: device int64 or NULL.
  *   - nvis > SEPW_NOALLOC_MAX_VIS, or a grid/tile combination with more than
  *     SEPW_NOALLOC_MAX_TILES tiles, returns SEPW_ETOOLARGE before anything is
  *     enqueued; split the visibilities into several calls instead (gridding
  *     accumulates).
- *   - The first call on each device looks up the array's device address
- *     (with that device current) and caches it; make that first call before
- *     any stream capture on the device.
- *   - Every call reuses the same array.  Calls whose GPU work overlaps (two
- *     streams, two host threads, two devices' calls are fine) race on it and
- *     give wrong results: serialise them. */
+ *   - Start-up: the array's device memory is reserved by the CUDA driver when
+ *     it loads the library's device code on a device.  Under CUDA's lazy
+ *     module loading (the default) that happens at the first call on that
+ *     device (or at the first launch of any other libsepw entry point there).
+ *     The first call also looks up the array's device address, with that
+ *     device current, and caches it.  A caller that may not allocate later
+ *     should therefore make one call at start-up (nvis = 0 is enough), and
+ *     before any stream capture on the device.
+ *   - Every call reuses the same array.  Two calls whose GPU work can overlap
+ *     in time race on it and give wrong results, whether they come from two
+ *     streams, two host threads or a captured graph replayed beside a direct
+ *     call: order them on one stream or with events.  Calls on different
+ *     devices do not share an array. */
 SEPW_API int sepw_grid_noalloc(const sepw_params *p, const float *taps, int64_t nvis,
                                const double *u, const double *v, const double *w,
                                const float *vis, const float *weight, float *grid,

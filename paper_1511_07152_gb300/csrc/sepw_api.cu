@@ -86,7 +86,11 @@ int effective_tile(const sepw_params *p)
     return is_tc_form(p->form) ? tc_tile_for_support(p->support) : 32;
 }
 
-DevParams make_dev(const sepw_params *p)
+}  // namespace
+
+// Device-side parameters of p (tile resolved by its form); shared with the
+// allocation-free entry point.
+DevParams sepw::make_dev_params(const sepw_params *p)
 {
     DevParams d;
     d.N = p->grid_size;
@@ -110,6 +114,10 @@ DevParams make_dev(const sepw_params *p)
     d.beta = p->kb_beta;
     return d;
 }
+
+namespace {
+
+DevParams make_dev(const sepw_params *p) { return sepw::make_dev_params(p); }
 
 template <typename T>
 int grow(sepw_ctx *ctx, T **ptr, size_t count)

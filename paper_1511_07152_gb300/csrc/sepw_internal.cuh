@@ -332,6 +332,10 @@ struct Plan {
     const double *u = nullptr, *v = nullptr, *w = nullptr;
 };
 
+// Device-side parameters of a checked sepw_params (sepw_api.cu): derived
+// constants, and the tile edge resolved for the form when p->tile is 0.
+DevParams make_dev_params(const sepw_params *p);
+
 // ---- launchers (each .cu file implements its own) -------------------------
 
 // sepw_taps.cu

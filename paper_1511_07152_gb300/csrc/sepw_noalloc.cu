@@ -103,7 +103,13 @@ extern "C" int sepw_grid_noalloc(const sepw_params *prm, const float *taps, int6
                                  const float *vis, const float *weight, float *grid,
                                  int64_t *n_dropped, sepw_stream_t stream)
 {
-    int rc = sepw_check_params(prm);
+    if (!prm)
+        return SEPW_EINVAL;
+    // the tiled FP32 form runs whatever form the caller names: check (and
+    // resolve the default tile of) that form, not the caller's
+    sepw_params tp = *prm;
+    tp.form = SEPW_FORM_TILED;
+    int rc = sepw_check_params(&tp);
     if (rc != SEPW_OK)
         return rc;
     if (nvis < 0)
@@ -111,32 +117,16 @@ extern "C" int sepw_grid_noalloc(const sepw_params *prm, const float *taps, int6
     if (nvis > kMaxVis)
         return SEPW_ETOOLARGE;
 
-    DevParams dp;
-    dp.N = prm->grid_size;
-    dp.S = prm->support;
-    dp.OS = prm->oversample;
-    dp.P = prm->n_wplanes;
-    dp.T = prm->tile == 0 ? 32 : prm->tile;
-    dp.ntx = (dp.N - dp.S) / dp.T + 1;
-    dp.t_inv = tile_reciprocal(dp.T);
-    dp.fov = prm->fov;
-    dp.half = (double)(dp.N / 2);
-    dp.os_d = (double)dp.OS;
-    dp.os_log2 = -1;
-    for (int k = 0; k < 31; ++k)
-        if ((1 << k) == dp.OS)
-            dp.os_log2 = k;
-    locate_fast_bounds(dp.N, dp.os_log2, dp.fast_elim, dp.fast_near);
-    dp.plane_r = dp.P > 1 ? (double)(dp.P - 1) / prm->w_max : 0.0;
-    dp.w_max = prm->w_max;
-    dp.gamma = prm->gamma;
-    dp.beta = prm->kb_beta;
+    const DevParams dp = make_dev_params(&tp);
     const int64_t ntiles = (int64_t)dp.ntx * dp.ntx;
     if (ntiles > kMaxTiles)
         return SEPW_ETOOLARGE;
 
     if (!device_ptr_ok(taps, false) || !device_ptr_ok(grid, false) ||
         !device_ptr_ok(n_dropped, true))
+        return SEPW_EINVAL;
+    // the tiled gridder reads rows of taps as 16-byte vectors
+    if (((uintptr_t)taps) & 15)
         return SEPW_EINVAL;
     if (nvis > 0 && (!device_ptr_ok(u, false) || !device_ptr_ok(v, false) ||
                      !device_ptr_ok(w, false) || !device_ptr_ok(vis, false) ||

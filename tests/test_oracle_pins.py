@@ -344,6 +344,46 @@ def test_w_support_formula_limits():
     assert abs(O.w_support(w, fov, 0.01) / (w * fov * fov) - 1) < 1e-3
 
 
+def test_w_support_formula_interior():
+    """Sec. 2 support formula where both of its terms matter.
+
+    Hand-evaluated at w = 1000, fov = 0.02, eta = 0.01:
+      (w fov / 2)^2 = 10^2 = 100;
+      w^(3/2) fov / (2 pi eta) = 31622.7766 * 0.02 / 0.0628318531 = 10065.842;
+      2 fov sqrt(100 + 10065.842) = 0.04 * 100.82580 = 4.033032.
+    And at the crossover w* = (2 / (pi eta fov))^2, where the two terms are
+    equal, the support is sqrt(2) w* fov^2 (each term alone gives w* fov^2)."""
+    assert abs(O.w_support(1000.0, 0.02, 0.01) - 4.033032) < 2e-6
+    fov, eta = 0.02, 0.01
+    ws = (2.0 / (math.pi * eta * fov)) ** 2
+    assert abs(O.w_support(ws, fov, eta) / (math.sqrt(2.0) * ws * fov * fov) - 1) < 1e-12
+    # below the crossover the w^(3/2) term dominates: support ~ w^(3/4)
+    r = O.w_support(ws * 1e-12 * 16, fov, eta) / O.w_support(ws * 1e-12, fov, eta)
+    assert abs(r - 16 ** 0.75) < 1e-4
+
+
+def test_n_wplanes_needed():
+    """Sec. 2 number of w planes, pi w_max fov^2 / sqrt(2 dA).
+
+    Hand-evaluated at w_max = 2e5, fov = 0.05, dA = 0.01:
+      pi * 2e5 * 0.0025 = 1570.7963;  sqrt(0.02) = 0.14142136;
+      1570.7963 / 0.14142136 = 11107.207.
+    The paper says the count easily reaches 10^4 at low elevation with
+    dA = 0.01: the SKA1-MID example of Sec. 3 (15 degree elevation, field
+    lambda / D, w_max = B cos(a) / lambda) gives about 1.2e4."""
+    assert abs(O.n_wplanes_needed(2e5, 0.05, 0.01) - 11107.207) < 2e-3
+    # scaling: linear in w_max, quadratic in fov, inverse square root in dA
+    base = O.n_wplanes_needed(1e4, 0.03, 0.02)
+    assert abs(O.n_wplanes_needed(2e4, 0.03, 0.02) / base - 2) < 1e-12
+    assert abs(O.n_wplanes_needed(1e4, 0.06, 0.02) / base - 4) < 1e-12
+    assert abs(O.n_wplanes_needed(1e4, 0.03, 0.005) / base - 2) < 1e-12
+    g = json.load(open(GOLDEN))["wplanes_low_elevation"]
+    ska = json.load(open(GOLDEN))[g["telescope"]]
+    lam, D, B, a = ska["lambda_m"], ska["D_m"], ska["B_m"], math.radians(ska["elevation_deg"])
+    P = O.n_wplanes_needed(B * math.cos(a) / lam, lam / D, g["dA"])
+    assert g["printed_order"] <= P < 10 * g["printed_order"]
+
+
 # --------------------------------------------------------------------------
 # locating visibilities: brute-force rule checks with exact rationals
 # --------------------------------------------------------------------------
