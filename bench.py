@@ -576,14 +576,15 @@ def run_ours(args):
     if not args.skip_tc:
         for name, form, nprod in (("tc_bf16", S.FORM_TC_BF16, 1),
                                   ("tc_fp16", S.FORM_TC_FP16, 1),
-                                  ("tc_fp16x2", S.FORM_TC_FP16X2, 3)):
+                                  ("tc_fp16x2", S.FORM_TC_FP16X2, 2),
+                                  ("tc_bf16x2", S.FORM_TC_BF16X2, 2)):
             c2 = S.sepw_create(S.make_params(**wl.params(), form=form))
             fms, fp, fg, fd = _time_form(S, torch, c2, taps, dev, grid, out,
                                          max(3, args.steps // 2), 2, stream)
-            # executed dense MMA flops: one M128 x N64 x K16 MMA per 8 visibilities
-            # of a stage (three for the hi + lo form), K = 2 real components per
+            # executed dense MMA flops: one M128 x N32 x K16 MMA per 8 visibilities
+            # of a stage (two for the hi + lo forms), K = 2 real components per
             # visibility
-            mma_flops = 2 * 128 * 64 * 2 * nkept * nprod
+            mma_flops = 2 * 128 * 32 * 2 * nkept * nprod
             fvalue, fms = whole_job(fms, 2.0 * nvis, ws, dist, device="cuda")
             forms[name] = {"value": fvalue, "unit": "vis/s",
                            "ms_per_step": fms,
@@ -594,19 +595,19 @@ def run_ours(args):
                                "peak": float(peaks["bf16_tflops"]),
                                "frac": mma_flops / (fg * 1e-3) / 1e12 /
                                float(peaks["bf16_tflops"]),
-                               "note": "dense MMA flops executed (2 x 128 x 64 x 2 per vis "
-                                       "per product) over the grid kernel; burst bf16 peak "
+                               "note": "dense MMA flops executed (2 x 128 x 32 x 2 per vis "
+                                       "per MMA) over the grid kernel; burst bf16 peak "
                                        "(fp16 same)"}}
             if nprod == 1:
-                # degridding: one M128 x N128 x K128 product per 128 visibilities
-                # of a work item (Q = conj(Av) X over the item's window)
-                dg_flops = 2 * 128 * 128 * nkept
+                # degridding: one M128 x N64 x K128 product per 128 visibilities
+                # of a work item (Q = conj(Av) X over the item's 32-column window)
+                dg_flops = 2 * 64 * 128 * nkept
                 forms[name]["degrid_tensor_roofline"] = {
                     "bound": "tensor", "unit": "TFLOP/s",
                     "achieved": dg_flops / (fd * 1e-3) / 1e12,
                     "peak": float(peaks["bf16_tflops"]),
                     "frac": dg_flops / (fd * 1e-3) / 1e12 / float(peaks["bf16_tflops"]),
-                    "note": "dense MMA flops per kept visibility (2 x 128 x 128; "
+                    "note": "dense MMA flops per kept visibility (2 x 64 x 128; "
                             "ragged stages not counted) over the degrid kernel"}
             c2.close()
 
@@ -626,7 +627,7 @@ def run_ours(args):
         fm = {"tiled_fp32": S.FORM_TILED, "plain_fp32": S.FORM_PLAIN}
         if not args.skip_tc:
             fm.update(tc_bf16=S.FORM_TC_BF16, tc_fp16=S.FORM_TC_FP16,
-                      tc_fp16x2=S.FORM_TC_FP16X2)
+                      tc_fp16x2=S.FORM_TC_FP16X2, tc_bf16x2=S.FORM_TC_BF16X2)
         errs, nsub = _form_errors(S, torch, wl, fm)
         for k, e in errs.items():
             if k in forms:

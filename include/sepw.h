@@ -80,9 +80,13 @@ extern "C" {
                                kernel suppresses (image edges divided by
                                c1 c1) loses accuracy accordingly. */
 #define SEPW_FORM_TC_FP16X2 4 /* as SEPW_FORM_TC_FP16 with each operand split into
-                                 FP16 hi + lo and three products per step:
-                                 FP32-class accuracy.  Degridding uses the
-                                 tiled FP32 form. */
+                                 FP16 hi + lo (all four products of the
+                                 splits): FP32-class accuracy.  Degridding
+                                 uses the tiled FP32 form. */
+#define SEPW_FORM_TC_BF16X2 5 /* as SEPW_FORM_TC_BF16 with each operand split into
+                                 BF16 hi + lo (all four products; no scale:
+                                 BF16 has the FP32 exponent range).
+                                 Degridding uses the tiled FP32 form. */
 
 /* image directions (sepw_image) */
 #define SEPW_GRID_TO_IMAGE 0
@@ -104,9 +108,10 @@ typedef struct sepw_params {
     double kb_beta;     /* Kaiser-Bessel antialiasing window parameter; the
                            taper is its transform (Sec. 2 kernel C / c)       */
     int32_t tile;       /* tiled forms: tile edge T in cells; even, 8..64,
-                           T + S - 1 <= 64.  0 = 32 for SEPW_FORM_TILED and
-                           the largest even T with T + S - 1 <= 64 for the
-                           tensor-core forms (48 at S = 16)                   */
+                           T + S - 1 <= 64, and T + S - 1 <= 32 for the
+                           tensor-core forms.  0 = 32 for SEPW_FORM_TILED
+                           and the largest even T with T + S - 1 <= 32 for
+                           the tensor-core forms (16 at S = 16)               */
     int32_t form;       /* SEPW_FORM_*                                        */
 } sepw_params;
 
@@ -231,6 +236,22 @@ SEPW_API int sepw_degrid_planned(sepw_ctx *ctx, const float *taps, const float *
  * wait records SEPW_ETIMEOUT in a device word.  Synchronises `stream`, copies
  * the word to *status (SEPW_OK if nothing was recorded) and resets it. */
 SEPW_API int sepw_device_status(sepw_ctx *ctx, int *status, sepw_stream_t stream);
+
+/* Limit of every bounded wait inside the tensor-core kernels of this context
+ * (nanoseconds of the GPU's global timer; default 2 s; 1 us .. 60 s, else
+ * SEPW_EINVAL).  A kernel whose wait runs out records SEPW_ETIMEOUT (see
+ * sepw_device_status), stops issuing work, waits for its own tensor-core
+ * operations (bounded by the same limit), releases its tensor memory and
+ * returns; its output is then incomplete.  Host only; applies to later calls. */
+SEPW_API int sepw_set_wait_limit(sepw_ctx *ctx, uint64_t limit_ns);
+
+/* Test hook for the timeout path (no counterpart in the paper): with enable
+ * != 0 the tensor-core kernels of this context issue no matrix operations and
+ * signal none, so their other roles' bounded waits run out and the call ends
+ * with SEPW_ETIMEOUT recorded and the grid or predictions incomplete.  Nothing
+ * is left waiting: every wait is bounded (sepw_set_wait_limit).  enable = 0
+ * restores normal operation.  Host only. */
+SEPW_API int sepw_test_stall_mma(sepw_ctx *ctx, int enable);
 
 /* Image step with grid correction, Sec. 2 (I_D / n = F^-1[grid] / c), in
  * place on an N x N complex64 buffer:

@@ -17,26 +17,25 @@ import os
 import statistics
 from dataclasses import dataclass, field
 
-FORM_NAMES = {0: "plain", 1: "tiled", 2: "tc_bf16", 3: "tc_fp16", 4: "tc_fp16x2"}
+FORM_NAMES = {0: "plain", 1: "tiled", 2: "tc_bf16", 3: "tc_fp16", 4: "tc_fp16x2",
+              5: "tc_bf16x2"}
 # accuracy class of each form: the grid's relative L2 error bound it meets
 FORM_ERROR = {"plain": 1e-5, "tiled": 1e-5, "tc_bf16": 1e-2, "tc_fp16": 1.5e-3,
-              "tc_fp16x2": 1e-5}
+              "tc_fp16x2": 1e-5, "tc_bf16x2": 1e-5}
 
 
 def candidate_tiles(support: int, form: str) -> list[int]:
-    """Even tile edges T with T + S - 1 <= 64 (the shared / tensor-memory
-    window), restricted to the sizes worth timing.  The plain form has no
-    tiles (one candidate, 0)."""
+    """Even tile edges T worth timing: T + S - 1 <= 64 (the tiled forms'
+    shared-memory window) or <= 32 (the tensor-core gridder's window, S <= 16
+    only).  The plain form has no tiles (one candidate, 0)."""
     if form == "plain":
         return [0]
-    out = []
-    for T in (16, 24, 32, 40, 48, 56):
-        if T + support - 1 <= 64:
-            out.append(T)
     if form.startswith("tc"):
-        # the tensor-core window is always 64 wide: larger T wastes less
-        out = [T for T in out if T >= 32] or out
-    return out
+        if support > 16:
+            return []
+        tmax = (33 - support) & ~1
+        return [T for T in (tmax - 8, tmax - 4, tmax) if T >= 8]
+    return [T for T in (16, 24, 32, 40, 48, 56) if T + support - 1 <= 64]
 
 
 def cache_key(gpu: str, grid_size: int, support: int, oversample: int, n_wplanes: int,
@@ -110,8 +109,8 @@ def tune(params: dict, u, v, w, vis, weight, max_error: float = 1e-5, forms=None
         hit = cache.get(key)
         if hit and FORM_ERROR[hit["form"]] <= max_error:
             return hit
-    forms = forms or [f for f in ("plain", "tiled", "tc_fp16x2", "tc_fp16", "tc_bf16")
-                      if FORM_ERROR[f] <= max_error]
+    forms = forms or [f for f in ("plain", "tiled", "tc_fp16x2", "tc_bf16x2", "tc_fp16",
+                                  "tc_bf16") if FORM_ERROR[f] <= max_error]
     codes = {v_: k for k, v_ in FORM_NAMES.items()}
     N = params["grid_size"]
     ng = 1 if vis_offsets is None else len(vis_offsets) - 1

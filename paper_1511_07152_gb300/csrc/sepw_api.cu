@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include "sepw_internal.cuh"
+#include "sepw_tc_ptx.cuh"
 
 using namespace sepw;
 
@@ -22,6 +23,10 @@ struct sepw_ctx {
     float *d_taper32 = nullptr;
     double2 *d_tw = nullptr;
     int32_t *d_status = nullptr;  // SEPW_ETIMEOUT recorded by a kernel
+    TcControl tc_ctl{tcx::kDefaultWaitNs, 0};
+    // workspace of the contraction gridder's pre-shifted tap tables
+    unsigned char *d_tc2 = nullptr;
+    size_t tc2_cap = 0;
     // workspace of the tiled gridder's planar copy of the caller's tap
     // table(s) (two tables: facet mode)
     float *d_planar = nullptr;
@@ -71,19 +76,21 @@ int cuda_fail(sepw_ctx *ctx, cudaError_t e, const char *where)
 
 bool is_tc_form(int form)
 {
-    return form == SEPW_FORM_TC_BF16 || form == SEPW_FORM_TC_FP16 || form == SEPW_FORM_TC_FP16X2;
+    return form == SEPW_FORM_TC_BF16 || form == SEPW_FORM_TC_FP16 ||
+           form == SEPW_FORM_TC_FP16X2 || form == SEPW_FORM_TC_BF16X2;
 }
 
 int tc_prec(int form)
 {
-    return form == SEPW_FORM_TC_BF16 ? 0 : form == SEPW_FORM_TC_FP16 ? 1 : 2;
+    return form == SEPW_FORM_TC_BF16 ? 0 : form == SEPW_FORM_TC_FP16 ? 1
+         : form == SEPW_FORM_TC_FP16X2 ? 2 : 3;
 }
 
 int effective_tile(const sepw_params *p)
 {
     if (p->tile != 0)
         return p->tile;
-    return is_tc_form(p->form) ? tc_tile_for_support(p->support) : 32;
+    return is_tc_form(p->form) ? tc2_tile_for_support(p->support) : 32;
 }
 
 }  // namespace
@@ -269,6 +276,8 @@ int sepw_check_params(const sepw_params *p)
         return SEPW_ENOTSUP;
     if (is_tc_form(p->form) && S > 16)
         return SEPW_ENOTSUP;
+    if (is_tc_form(p->form) && T + S - 1 > 32)  // the contraction gridder's window
+        return SEPW_EINVAL;
     return SEPW_OK;
 }
 
@@ -350,6 +359,7 @@ void sepw_destroy(sepw_ctx *ctx)
     cudaFree(ctx->d_tw);
     cudaFree(ctx->d_status);
     cudaFree(ctx->d_planar);
+    cudaFree(ctx->d_tc2);
     free_plan(ctx->plan);
     cudaSetDevice(cur);
     delete ctx;
@@ -514,11 +524,17 @@ int sepw_grid_planned(sepw_ctx *ctx, const float *taps, const float *vis,
                                              nullptr, s));
         }
     } else if (is_tc_form(pl.form)) {
-        if (((uintptr_t)taps) & 15)
-            return fail(ctx, SEPW_EINVAL, "taps must be 16-byte aligned");
-        SEPW_CUDA(ctx, launch_grid_tc(ctx->dp, pl, (const float2 *)vis, weight,
-                                      (const float2 *)taps, (float2 *)grid, ctx->num_sms,
-                                      tc_prec(pl.form), ctx->d_status, s));
+        const size_t need = tc2_tables_bytes(ctx->dp, pl.items_capacity);
+        if (ctx->tc2_cap < need) {
+            ctx->tc2_cap = 0;
+            if ((rc = grow(ctx, &ctx->d_tc2, need)))
+                return rc;
+            ctx->tc2_cap = need;
+        }
+        SEPW_CUDA(ctx, launch_grid_tc2(ctx->dp, pl, (const float2 *)vis, weight,
+                                       (const float2 *)taps, ctx->d_tc2, (float2 *)grid,
+                                       ctx->num_sms, tc_prec(pl.form), ctx->d_status,
+                                       ctx->tc_ctl, s));
     } else {
         if (((uintptr_t)taps) & 15)
             return fail(ctx, SEPW_EINVAL, "taps must be 16-byte aligned");
@@ -563,7 +579,8 @@ int sepw_degrid_planned(sepw_ctx *ctx, const float *taps, const float *grid,
         if (pl.form == SEPW_FORM_TC_BF16 || pl.form == SEPW_FORM_TC_FP16)
             SEPW_CUDA(ctx, launch_degrid_tc(ctx->dp, pl, (const float2 *)grid, weight,
                                             (const float2 *)taps, (float2 *)vis_out,
-                                            ctx->num_sms, tc_prec(pl.form), ctx->d_status, s));
+                                            ctx->num_sms, tc_prec(pl.form), ctx->d_status,
+                                            ctx->tc_ctl, s));
         else
             SEPW_CUDA(ctx, launch_degrid_tiled(ctx->dp, pl, (const float2 *)grid, weight,
                                                (const float2 *)taps, (float2 *)vis_out,
@@ -637,6 +654,25 @@ int sepw_device_status(sepw_ctx *ctx, int *status, sepw_stream_t stream)
     SEPW_CUDA(ctx, cudaStreamSynchronize(s));
     SEPW_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), s));
     *status = v;
+    return SEPW_OK;
+}
+
+int sepw_set_wait_limit(sepw_ctx *ctx, uint64_t limit_ns)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    if (limit_ns < 1000 || limit_ns > 60000000000ull)
+        return fail(ctx, SEPW_EINVAL, "wait limit %llu ns outside [1 us, 60 s]",
+                    (unsigned long long)limit_ns);
+    ctx->tc_ctl.wait_ns = limit_ns;
+    return SEPW_OK;
+}
+
+int sepw_test_stall_mma(sepw_ctx *ctx, int enable)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    ctx->tc_ctl.stall = enable ? 1 : 0;
     return SEPW_OK;
 }
 

@@ -380,16 +380,33 @@ cudaError_t launch_degrid_tiled(const DevParams &p, const Plan &plan,
                                 const float2 *taps, float2 *vis, int num_sms,
                                 cudaStream_t s);
 
-// sepw_tc.cu
-int tc_tile_for_support(int S);
-// contraction-form degridder: prec 0 = BF16, 1 = FP16 (scaled per item)
+// Control of the tensor-core kernels: the limit of every bounded mbarrier
+// wait, and a test hook (stall != 0: the MMA thread issues and commits
+// nothing, so the other roles' waits run out and the kernel reports
+// SEPW_ETIMEOUT).
+struct TcControl {
+    unsigned long long wait_ns;
+    int32_t stall;
+};
+
+// sepw_tc.cu: contraction-form degridder, prec 0 = BF16, 1 = FP16 (scaled
+// per item); T + S - 1 <= 64
 cudaError_t launch_degrid_tc(const DevParams &p, const Plan &plan, const float2 *grid,
                              const float *weight, const float2 *taps, float2 *vis,
-                             int num_sms, int prec, int32_t *status, cudaStream_t s);
-// prec: 0 = BF16, 1 = FP16, 2 = FP16 hi + lo (three products)
-cudaError_t launch_grid_tc(const DevParams &p, const Plan &plan, const float2 *vis,
-                           const float *weight, const float2 *taps, float2 *grid,
-                           int num_sms, int prec, int32_t *status, cudaStream_t s);
+                             int num_sms, int prec, int32_t *status, TcControl ctl,
+                             cudaStream_t s);
+
+// sepw_tc_grid.cu: contraction-form gridder, T + S - 1 <= 32, S <= 16.
+// prec: 0 = BF16, 1 = FP16 (scaled per item), 2 = FP16 hi + lo (scaled),
+// 3 = BF16 hi + lo.  tables: tc2_tables_bytes(p, plan.items_capacity) bytes of
+// device workspace for the per-call pre-shifted tap tables and the per-item
+// scale exponents.
+int tc2_tile_for_support(int S);
+size_t tc2_tables_bytes(const DevParams &p, int64_t items_capacity);
+cudaError_t launch_grid_tc2(const DevParams &p, const Plan &plan, const float2 *vis,
+                            const float *weight, const float2 *taps, void *tables, float2 *grid,
+                            int num_sms, int prec, int32_t *status, TcControl ctl,
+                            cudaStream_t s);
 
 // sepw_wstack.cu
 cudaError_t launch_wstack_assign(int64_t nvis, const double *w, const double *c, int L,

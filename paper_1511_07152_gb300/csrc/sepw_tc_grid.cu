@@ -1,0 +1,682 @@
+// Tensor-core (tcgen05) contraction form of the separable gridder with
+// MN-major operands built by 16-byte stores from pre-shifted tap tables.
+//
+// Sec. 5 writes the update of a visibility as the separable product
+// W V F1(u - u_i) F1(v - v_i).  Summed over the visibilities of one tile it is
+// a dense complex contraction over the tile's window (T + S - 1 <= 32 cells a
+// side): with a_i[y] the v-taps of visibility i at its row offset and
+// b'_i[x] = W_i V_i times its u-taps at its column offset,
+//     G[y][x] = sum_i a_i[y] b'_i[x].
+// In real arithmetic, K = (visibility, re/im component), one tcgen05.mma of
+// shape M = 128, N = 32 H per K = 16 (8 visibilities):
+//     rows m = 64 h + 32 c + y      (h: split part of a, c: re/im of G, y: row)
+//     A[(h,0,y)][(i,0)] =  a_h,r   A[(h,0,y)][(i,1)] = -a_h,i
+//     A[(h,1,y)][(i,0)] =  a_h,i   A[(h,1,y)][(i,1)] =  a_h,r
+//     B[(i,0)][(g,x)] = b'_g,r     B[(i,1)][(g,x)] = b'_g,i
+// where a_h (b'_g) is the h-th (g-th) part of the 16-bit split of the taps
+// (of W V times the taps).  The one-part forms (H = 1) keep h = g = 0 and rows
+// 64..127 of A stay zero; the hi + lo forms (H = 2) put a_hi, a_lo in the two
+// row halves and b'_hi, b'_lo side by side in N, so one MMA yields all four
+// products of the splits, which the epilogue adds.
+//
+// Both operands are MN-major: a visibility's column of A (and its row of B)
+// is contiguous along M (N) in 16-byte pieces of 8 values, so it is written as
+// whole 16-byte chunks.  The chunks come from tables built per call from the
+// caller's complex64 taps:
+//   vtab: per (plane, oversample, shift s = row offset mod 8, part h,
+//         component): three chunks holding taps 8 j - s .. 8 j - s + 7
+//         (zero outside 0 .. S-1), rounded to the 16-bit format;
+//   utab: per (plane, oversample, shift, chunk j): the same eight complex64
+//         taps of the u side, which is multiplied by W V in FP32 before
+//         rounding.
+// Chunk j of a visibility whose footprint starts at row ly goes to chunk row
+// j + ly / 8 of its column: the placement is a computed store address, and the
+// chunk rows its footprint misses get zeros, so each stage overwrites every
+// byte its visibilities own and no buffer ever needs clearing.
+//
+// One lane per visibility: a stage is 32 visibilities (K = 64), one warp.
+// Lanes hold visibilities with consecutive K indices; core matrices adjacent
+// along K are placed 16 bytes past a multiple of 128 (an odd number of
+// 16-byte slots), so the 8 lanes of a quarter warp store into 8 distinct
+// 16-byte bank groups: no conflicts, whatever chunk row each lane writes.
+//
+// Roles (static round-robin assignment of the plan's work items to CTAs, so
+// every role walks the same sequence of items and stages):
+//   - eight producer warps, each owning one of eight stage buffers: warp w
+//     takes the CTA's stages w, w + 8, ...  Owning its buffer, a producer
+//     has itself filled the buffer's previous stage, so its wait for that
+//     stage's MMAs can never be two mbarrier phases ahead (a parity wait
+//     cannot tell those apart).  A lane loads its record one stage ahead,
+//     then its taps and value, waits for the buffer, writes its A column and
+//     B row and the warp arrives on the buffer's "full" mbarrier;
+//   - one MMA thread: per stage it waits for "full", issues the K = 16 MMAs
+//     and commits them to the buffer's "empty" mbarrier; per work item it
+//     accumulates into one of two tensor-memory accumulators and commits
+//     "accf" after the item's last stage;
+//   - four epilogue warps (one per tensor-memory lane quarter): per item they
+//     read the accumulator, release it ("accfree"), stage it in shared memory
+//     and add the window to the HBM grid with float2 atomics (windows of
+//     neighbouring tiles overlap).
+// Every mbarrier wait is bounded; on expiry the kernel records SEPW_ETIMEOUT,
+// every role leaves its loop, the MMA thread waits (bounded) for its own MMAs
+// and the tensor memory is freed.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "sepw_internal.cuh"
+#include "sepw_tc_ptx.cuh"
+
+namespace sepw {
+namespace {
+
+using namespace tcx;
+
+constexpr int kStageVis = 32;                  // visibilities per stage (K = 64)
+constexpr int kBufs = 8;                       // stage buffers = producer warps
+constexpr int kWin = 32;                       // window edge, T + S - 1 <= 32
+constexpr int kM = 128;
+constexpr uint32_t kSboA = 128;                // M-adjacent core matrices
+constexpr uint32_t kLboA = 16 * 128 + 16;      // K-adjacent: 16 M-groups + 16 B
+constexpr int kABytes = 8 * kLboA;             // 8 K-groups per stage
+constexpr int kStgStride = 33;                 // staging row (floats), padded
+constexpr int kStgBytes = kM * kStgStride * 4;
+constexpr int kEpiWarps = 4;
+
+// PREC: 0 = BF16, 1 = FP16 (scaled per item), 2 = FP16 hi + lo (scaled),
+// 3 = BF16 hi + lo
+template <int PREC>
+struct Cfg {
+    static constexpr int H = (PREC == 2 || PREC == 3) ? 2 : 1;  // split parts
+    static constexpr bool SCALED = PREC == 1 || PREC == 2;
+    static constexpr bool BF = PREC == 0 || PREC == 3;
+    static constexpr int N = 32 * H;                       // MMA N: [b'_hi | b'_lo]
+    static constexpr uint32_t kSboB = 128;
+    static constexpr uint32_t kLboB = (N / 8) * 128 + 16;  // K-adjacent, padded
+    static constexpr int kBBytes = 8 * kLboB;
+    static constexpr int kProdWarps = kBufs;  // 13 warps: up to 128 registers each
+    static constexpr int kMmaWarp = kProdWarps;
+    static constexpr int kEpiWarp0 = kProdWarps + 1;
+    static constexpr int kBlock = 32 * (kProdWarps + 1 + kEpiWarps);
+    static constexpr uint32_t kTmemCols = 2 * N;  // two accumulators
+    static constexpr size_t kSmem = (size_t)kBufs * (kABytes + kBBytes) + kStgBytes +
+                                    sizeof(uint64_t) * (2 * kBufs + 5);
+};
+
+// (x, y) rounded to the 16-bit format, part h: 0 = hi = rn(v), 1 = lo = rn(v - hi)
+template <bool BF>
+__device__ __forceinline__ uint32_t pack_part(float x, float y, int h)
+{
+    if constexpr (BF) {
+        __nv_bfloat162 hi = __floats2bfloat162_rn(x, y);
+        if (h) {
+            const float2 f = __bfloat1622float2(hi);
+            hi = __floats2bfloat162_rn(x - f.x, y - f.y);
+        }
+        return *reinterpret_cast<uint32_t *>(&hi);
+    } else {
+        __half2 hi = __floats2half2_rn(x, y);
+        if (h) {
+            const float2 f = __half22float2(hi);
+            hi = __floats2half2_rn(x - f.x, y - f.y);
+        }
+        return *reinterpret_cast<uint32_t *>(&hi);
+    }
+}
+
+// sign flip of the 16-bit values of a chunk selected by mask (exact)
+__device__ __forceinline__ uint4 xor4(uint4 v, uint32_t m)
+{
+    return make_uint4(v.x ^ m, v.y ^ m, v.z ^ m, v.w ^ m);
+}
+
+__device__ __forceinline__ void st16(unsigned char *p, uint4 v)
+{
+    *reinterpret_cast<uint4 *>(p) = v;
+}
+
+// Per-call tables (layouts in the file comment).  vtab from the v-direction
+// taps (voff), utab from the u-direction taps.
+template <int PREC>
+__global__ void tables_kernel(DevParams p, const float2 *__restrict__ taps, uint4 *vtab,
+                              float4 *utab)
+{
+    constexpr int H = Cfg<PREC>::H;
+    const int64_t nrow = (int64_t)p.P * p.OS;
+    const int64_t nv = nrow * 8 * H * 2 * 3;
+    const int64_t nu = nrow * 8 * 3 * 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv + nu; e += stride) {
+        if (e < nv) {
+            int64_t q = e;
+            const int j = (int)(q % 3);
+            q /= 3;
+            const int comp = (int)(q % 2);
+            q /= 2;
+            const int h = (int)(q % H);
+            q /= H;
+            const int s = (int)(q % 8);
+            q /= 8;
+            const float2 *row = taps + p.voff + q * p.S;
+            uint32_t w[4];
+#pragma unroll
+            for (int t2 = 0; t2 < 4; ++t2) {
+                float v[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int k = 8 * j - s + 2 * t2 + u;
+                    v[u] = (k >= 0 && k < p.S) ? (comp ? row[k].y : row[k].x) : 0.f;
+                }
+                w[t2] = pack_part<Cfg<PREC>::BF>(v[0], v[1], h);
+            }
+            vtab[e] = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+            int64_t q = e - nv;
+            const int f = (int)(q % 4);
+            q /= 4;
+            const int j = (int)(q % 3);
+            q /= 3;
+            const int s = (int)(q % 8);
+            q /= 8;
+            const float2 *row = taps + q * p.S;
+            float o[4];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int k = 8 * j - s + 2 * f + u;
+                const float2 t = (k >= 0 && k < p.S) ? row[k] : make_float2(0.f, 0.f);
+                o[2 * u] = t.x;
+                o[2 * u + 1] = t.y;
+            }
+            utab[e - nv] = make_float4(o[0], o[1], o[2], o[3]);
+        }
+    }
+}
+
+// Power-of-two exponent a per work item such that the item's largest |W V|
+// component is below 2^a (FP16 forms scale their B operand by 2^-a).
+__global__ void item_scale_kernel(const WorkItem *__restrict__ items,
+                                  const int32_t *__restrict__ nitems,
+                                  const int32_t *__restrict__ perm,
+                                  const float2 *__restrict__ vis, const float *__restrict__ weight,
+                                  int32_t *item_exp)
+{
+    __shared__ float s_red[8];
+    const int n_items = *nitems;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const WorkItem it = items[item];
+        float m = 0.f;
+        for (int e = threadIdx.x; e < it.count; e += blockDim.x) {
+            const int i = perm[it.start + e];
+            const float2 x = __ldg(vis + i);
+            const float wt = weight ? __ldg(weight + i) : 1.0f;
+            m = fmaxf(m, fmaxf(fabsf(wt * x.x), fabsf(wt * x.y)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0)
+            s_red[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+                m = fmaxf(m, s_red[w]);
+            int a = 0;
+            if (m > 0.f && m <= 3.0e38f) {
+                frexpf(m, &a);  // m = f 2^a, f in [0.5, 1)
+                a = max(-126, min(126, a));
+            }
+            item_exp[item] = a;
+        }
+        __syncthreads();
+    }
+}
+
+// The CTA's work items in order (static round robin) and the global index of
+// each item's first stage.
+struct Cursor {
+    int n = -1;      // ordinal of the item in this CTA's sequence
+    int item = 0;    // plan index of the item
+    int nst = 0;     // its stages
+    int tb = 0;      // CTA stage index of its first stage
+    int start = 0, count = 0, tile = 0;
+};
+
+__device__ __forceinline__ bool cursor_next(Cursor &c, const WorkItem *__restrict__ items,
+                                            int n_items)
+{
+    c.tb += c.nst;
+    ++c.n;
+    c.item = blockIdx.x + c.n * gridDim.x;
+    if (c.item >= n_items) {
+        c.nst = 0;
+        return false;
+    }
+    const WorkItem it = items[c.item];
+    c.start = it.start;
+    c.count = it.count;
+    c.tile = it.tile;
+    c.nst = (it.count + kStageVis - 1) / kStageVis;
+    return true;
+}
+
+// advance c to the item holding CTA stage t (false: past the last item)
+__device__ __forceinline__ bool cursor_seek(Cursor &c, int t, const WorkItem *__restrict__ items,
+                                            int n_items)
+{
+    while (t >= c.tb + c.nst)
+        if (!cursor_next(c, items, n_items))
+            return false;
+    return true;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
+    DevParams p, const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems,
+    const uint64_t *__restrict__ rec, const int32_t *__restrict__ perm,
+    const float2 *__restrict__ vis, const float *__restrict__ weight,
+    const uint4 *__restrict__ vtab, const float4 *__restrict__ utab,
+    const int32_t *__restrict__ item_exp, float2 *grid, int32_t *status, TcControl ctl)
+{
+    using C = Cfg<PREC>;
+    constexpr int H = C::H, N = C::N;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *const Abuf = smem;                          // [kBufs]
+    unsigned char *const Bbuf = smem + kBufs * kABytes;        // [kBufs]
+    float *const stg = reinterpret_cast<float *>(Bbuf + kBufs * C::kBBytes);
+    uint64_t *const full = reinterpret_cast<uint64_t *>(Bbuf + kBufs * C::kBBytes + kStgBytes);
+    uint64_t *const empty = full + kBufs;
+    uint64_t *const accf = empty + kBufs;     // [2]
+    uint64_t *const accfree = accf + 2;       // [2]
+    uint64_t *const drain = accfree + 2;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+    __shared__ int s_epi_ok[kEpiWarps];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_items = *nitems;
+
+    // the one-part forms never write rows 64..127 of A: zero them once
+    for (int e = tid; e < kBufs * kABytes / 16; e += C::kBlock)
+        reinterpret_cast<uint4 *>(Abuf)[e] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        for (int b = 0; b < kBufs; ++b) {
+            mbar_init(full + b, 1);
+            mbar_init(empty + b, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf + b, 1);
+            mbar_init(accfree + b, kEpiWarps);
+        }
+        mbar_init(drain, 1);
+        s_abort = 0;
+        mbar_init_fence();
+    }
+    if (warp == 0)
+        tmem_alloc(&s_tmem, C::kTmemCols);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp < C::kProdWarps) {
+        // ------------------------------------------------------------ producers
+        const int i = lane;  // slot in the stage
+        // A: byte offsets of this slot's two K columns (chunk row 0); B: rows
+        const uint32_t a_off0 = ((2 * i) >> 3) * kLboA + ((2 * i) & 7) * 16;
+        const uint32_t a_off1 = ((2 * i + 1) >> 3) * kLboA + ((2 * i + 1) & 7) * 16;
+        const uint32_t b_off0 = ((2 * i) >> 3) * C::kLboB + ((2 * i) & 7) * 16;
+        const uint32_t b_off1 = ((2 * i + 1) >> 3) * C::kLboB + ((2 * i + 1) & 7) * 16;
+        Cursor cur;
+        int t = warp;
+        bool ok = cursor_next(cur, items, n_items) && cursor_seek(cur, t, items, n_items);
+        // record and visibility index of the lane's slot, one stage ahead
+        uint64_t r = 0;
+        int vi = -1;
+        auto fetch = [&](const Cursor &c, int t_, uint64_t &r_, int &vi_) {
+            const int e = (t_ - c.tb) * kStageVis + i;
+            vi_ = -1;
+            if (e < c.count) {
+                r_ = __ldg(reinterpret_cast<const unsigned long long *>(rec) + c.start + e);
+                vi_ = __ldg(perm + c.start + e);
+            }
+        };
+        if (ok)
+            fetch(cur, t, r, vi);
+        while (ok && !s_abort) {
+            // this stage's taps and value
+            uint4 va[H][2][3];
+            float4 ut[3][4];
+            float2 x = make_float2(0.f, 0.f);
+            float wt = 0.f;
+            int lx = 0, ly = 0;
+            uint32_t cjm = 0;
+            const bool valid = vi >= 0;
+            if (valid) {
+                x = __ldg(vis + vi);
+                wt = weight ? __ldg(weight + vi) : 1.0f;
+                lx = rec_lx(r);
+                ly = rec_ly(r);
+                cjm = rec_conj(r) ? 0x80008000u : 0u;
+                const int64_t row = (int64_t)rec_plane(r) * p.OS;
+                const uint4 *pa = vtab + ((row + rec_ov(r)) * 8 + (ly & 7)) * (H * 6);
+                const float4 *pu = utab + ((row + rec_ou(r)) * 8 + (lx & 7)) * 12;
+#pragma unroll
+                for (int h = 0; h < H; ++h)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j)
+                            va[h][c][j] = __ldg(pa + (h * 2 + c) * 3 + j);
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int f = 0; f < 4; ++f)
+                        ut[j][f] = __ldg(pu + j * 4 + f);
+            }
+            // this warp's next stage: its record and index now
+            Cursor cn = cur;
+            const int tn = t + kBufs;
+            const bool okn = cursor_seek(cn, tn, items, n_items);
+            uint64_t rn = 0;
+            int vin = -1;
+            if (okn)
+                fetch(cn, tn, rn, vin);
+
+            float scale = 1.0f;
+            if constexpr (C::SCALED)
+                scale = ldexpf(1.0f, -__ldg(item_exp + cur.item));
+            const int b = t % kBufs;
+            if (t >= kBufs) {
+                // buffer b held stage t - kBufs: wait (lane 0) for its MMAs
+                if (lane == 0 && !s_abort &&
+                    !mbar_wait(empty + b, ((t / kBufs) - 1) & 1, ctl.wait_ns))
+                    s_abort = 1;
+                __syncwarp();
+                tc_fence_after();
+            }
+            unsigned char *const A = Abuf + b * kABytes;
+            unsigned char *const B = Bbuf + b * C::kBBytes;
+            const uint4 z = make_uint4(0, 0, 0, 0);
+            // A: chunk j of part h goes to chunk row j + ly / 8 of each quarter
+            // (h, re rows) / (h, im rows) of the two columns
+            const int oy8 = valid ? (ly >> 3) : 8;
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int xq = j + oy8;
+                    if (xq < 4) {
+                        const uint4 R = va[h][0][j];
+                        const uint4 I = xor4(va[h][1][j], cjm);  // conj(a) for w < 0
+                        const uint32_t g0 = (h * 8 + xq) * kSboA, g1 = g0 + 4 * kSboA;
+                        st16(A + a_off0 + g0, R);
+                        st16(A + a_off0 + g1, I);
+                        st16(A + a_off1 + g0, xor4(I, 0x80008000u));
+                        st16(A + a_off1 + g1, R);
+                    }
+                }
+#pragma unroll
+                for (int xq = 0; xq < 4; ++xq) {
+                    if (xq < oy8 || xq > oy8 + 2) {
+                        const uint32_t g0 = (h * 8 + xq) * kSboA, g1 = g0 + 4 * kSboA;
+                        st16(A + a_off0 + g0, z);
+                        st16(A + a_off0 + g1, z);
+                        st16(A + a_off1 + g0, z);
+                        st16(A + a_off1 + g1, z);
+                    }
+                }
+            }
+            // B: W V times the u-taps, chunk j to chunk row j + lx / 8 (and
+            // 4 + that for the lo part)
+            const int ox8 = valid ? (lx >> 3) : 8;
+            {
+                const float wr = (wt * x.x) * scale;  // exact power-of-two scaling
+                const float wi = (wt * x.y) * scale;
+                const float wis = cjm ? -wi : wi;      // conj(u-taps) for w < 0
+                const float wrs = cjm ? -wr : wr;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int xq = j + ox8;
+                    if (xq < 4) {
+                        float re[8], im[8];
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) {
+                            const float4 u = ut[j][f];
+                            // (wr + i wi)(tr + i s ti), s = -1 for w < 0
+                            re[2 * f] = wr * u.x - wis * u.y;
+                            im[2 * f] = wrs * u.y + wi * u.x;
+                            re[2 * f + 1] = wr * u.z - wis * u.w;
+                            im[2 * f + 1] = wrs * u.w + wi * u.z;
+                        }
+#pragma unroll
+                        for (int g = 0; g < H; ++g) {
+                            uint4 pr, pi;
+                            pr.x = pack_part<C::BF>(re[0], re[1], g);
+                            pr.y = pack_part<C::BF>(re[2], re[3], g);
+                            pr.z = pack_part<C::BF>(re[4], re[5], g);
+                            pr.w = pack_part<C::BF>(re[6], re[7], g);
+                            pi.x = pack_part<C::BF>(im[0], im[1], g);
+                            pi.y = pack_part<C::BF>(im[2], im[3], g);
+                            pi.z = pack_part<C::BF>(im[4], im[5], g);
+                            pi.w = pack_part<C::BF>(im[6], im[7], g);
+                            const uint32_t gb = (g * 4 + xq) * C::kSboB;
+                            st16(B + b_off0 + gb, pr);
+                            st16(B + b_off1 + gb, pi);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int xq = 0; xq < 4; ++xq) {
+                    if (xq < ox8 || xq > ox8 + 2) {
+#pragma unroll
+                        for (int g = 0; g < H; ++g) {
+                            const uint32_t gb = (g * 4 + xq) * C::kSboB;
+                            st16(B + b_off0 + gb, z);
+                            st16(B + b_off1 + gb, z);
+                        }
+                    }
+                }
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(full + b);
+            cur = cn;
+            t = tn;
+            ok = okn;
+            r = rn;
+            vi = vin;
+        }
+    } else if (warp == C::kMmaWarp) {
+        // ------------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            constexpr uint32_t idesc = instr_desc(C::BF ? 1u : 0u, true, true, kM, N);
+            Cursor cur;
+            int ne = 0;  // non-empty items so far (accumulator ne & 1)
+            while (cursor_next(cur, items, n_items) && !s_abort) {
+                if (cur.nst == 0)
+                    continue;
+                const int ab = ne & 1;
+                if (ne >= 2 && !mbar_wait(accfree + ab, ((ne >> 1) - 1) & 1, ctl.wait_ns)) {
+                    s_abort = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(ab * N);
+                for (int st = 0; st < cur.nst && !s_abort; ++st) {
+                    const int t = cur.tb + st, b = t % kBufs;
+                    if (!mbar_wait(full + b, (t / kBufs) & 1, ctl.wait_ns)) {
+                        s_abort = 1;
+                        break;
+                    }
+                    if (ctl.stall)
+                        continue;  // test hook: issue and signal nothing
+                    tc_fence_after();
+                    const int nv = min(kStageVis, cur.count - st * kStageVis);
+                    const int nk = (nv + 7) >> 3;  // K = 16 steps holding visibilities
+                    const uint32_t a0 = smem_u32(Abuf + b * kABytes);
+                    const uint32_t b0 = smem_u32(Bbuf + b * C::kBBytes);
+                    for (int kq = 0; kq < nk; ++kq)
+                        mma_f16(d, smem_desc(a0 + kq * 2 * kLboA, kLboA, kSboA),
+                                smem_desc(b0 + kq * 2 * C::kLboB, C::kLboB, C::kSboB), idesc,
+                                (st > 0 || kq > 0) ? 1u : 0u);
+                    mma_commit(empty + b);
+                }
+                if (!s_abort && !ctl.stall)
+                    mma_commit(accf + ab);
+                ++ne;
+            }
+            if (s_abort) {
+                // bounded wait for every MMA this thread issued before the
+                // tensor memory is released
+                mma_commit(drain);
+                mbar_wait(drain, 0, ctl.wait_ns);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int qq = warp & 3;  // tensor-memory lane quarter of this warp
+        const int ew = warp - C::kEpiWarp0;
+        const int et = tid - 32 * C::kEpiWarp0;  // 0 .. 127
+        float *const row = stg + (32 * qq + lane) * kStgStride;
+        Cursor cur;
+        int ne = 0;
+        while (cursor_next(cur, items, n_items)) {
+            if (cur.nst == 0)
+                continue;
+            const int ab = ne & 1;
+            // every epilogue warp takes the same decision: wait, publish, agree
+            int okw = 0;
+            if (lane == 0)
+                okw = !s_abort && mbar_wait(accf + ab, (ne >> 1) & 1, ctl.wait_ns);
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (lane == 0)
+                s_epi_ok[ew] = okw;
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+            const bool go = s_epi_ok[0] && s_epi_ok[1] && s_epi_ok[2] && s_epi_ok[3];
+            asm volatile("bar.sync 2, %0;" ::"n"(32 * kEpiWarps) : "memory");
+            if (!go) {
+                if (lane == 0)
+                    s_abort = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t ta = tmem + ((uint32_t)(32 * qq) << 16) + (uint32_t)(ab * N);
+            uint32_t rr[32];
+            SEPW_TMEM_LD32(ta, rr);
+            tmem_wait_ld();
+            float v[32];
+#pragma unroll
+            for (int xx = 0; xx < 32; ++xx)
+                v[xx] = __uint_as_float(rr[xx]);
+            if constexpr (H == 2) {
+                SEPW_TMEM_LD32(ta + 32, rr);  // the b'_lo columns
+                tmem_wait_ld();
+#pragma unroll
+                for (int xx = 0; xx < 32; ++xx)
+                    v[xx] += __uint_as_float(rr[xx]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(accfree + ab);
+            float back = 1.0f;
+            if constexpr (C::SCALED)
+                back = ldexpf(1.0f, __ldg(item_exp + cur.item));
+#pragma unroll
+            for (int xx = 0; xx < 32; ++xx)
+                row[xx] = v[xx] * back;
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+            const int W = p.T + p.S - 1;
+            const TileOrigin o = tile_origin(p, cur.tile);
+            for (int e = et; e < kWin * kWin; e += 32 * kEpiWarps) {
+                const int y = e >> 5, xx = e & 31;
+                if (y >= W || xx >= W)
+                    continue;
+                float re = stg[y * kStgStride + xx], im = stg[(32 + y) * kStgStride + xx];
+                if constexpr (H == 2) {
+                    re += stg[(64 + y) * kStgStride + xx];
+                    im += stg[(96 + y) * kStgStride + xx];
+                }
+                if (re != 0.f || im != 0.f)
+                    atomicAdd(grid + o.base + (o.gy0 + y) * p.N + o.gx0 + xx, make_float2(re, im));
+            }
+            asm volatile("bar.sync 2, %0;" ::"n"(32 * kEpiWarps) : "memory");
+            ++ne;
+        }
+    }
+
+    __syncthreads();
+    if (s_abort && tid == 0)
+        atomicExch(status, SEPW_ETIMEOUT);
+    tc_fence_after();
+    if (warp == 0)
+        tmem_dealloc(tmem, C::kTmemCols);
+}
+
+template <int PREC>
+cudaError_t launch_prec(const DevParams &p, const Plan &plan, const float2 *vis,
+                        const float *weight, const float2 *taps, void *tables, float2 *grid,
+                        int num_sms, int32_t *status, TcControl ctl, cudaStream_t s)
+{
+    using C = Cfg<PREC>;
+    const int64_t nrow = (int64_t)p.P * p.OS;
+    uint4 *vtab = reinterpret_cast<uint4 *>(tables);
+    float4 *utab = reinterpret_cast<float4 *>(vtab + nrow * 8 * C::H * 2 * 3);
+    int32_t *item_exp = reinterpret_cast<int32_t *>(utab + nrow * 8 * 3 * 4);
+    const int64_t n = nrow * 8 * (C::H * 6 + 12);
+    const int nb = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    tables_kernel<PREC><<<nb, 256, 0, s>>>(p, taps, vtab, utab);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    if constexpr (C::SCALED) {
+        item_scale_kernel<<<std::max(1, std::min(plan.items_capacity, 8 * num_sms)), 256, 0, s>>>(
+            plan.d_items, plan.d_nitems, plan.d_perm, vis, weight, item_exp);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+    }
+    e = cudaFuncSetAttribute(grid_tc2_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)C::kSmem);
+    if (e != cudaSuccess)
+        return e;
+    grid_tc2_kernel<PREC><<<num_sms, C::kBlock, C::kSmem, s>>>(
+        p, plan.d_items, plan.d_nitems, plan.d_rec, plan.d_perm, vis, weight, vtab, utab,
+        item_exp, grid, status, ctl);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc2_tile_for_support(int S)
+{
+    return (kWin - S + 1) & ~1;
+}
+
+size_t tc2_tables_bytes(const DevParams &p, int64_t items_capacity)
+{
+    // vtab sized for the two-part forms (2 * 6 chunks per (plane, oversample,
+    // shift)), utab 12 float4, then one exponent per work item
+    return (size_t)p.P * p.OS * 8 * (2 * 6 + 12) * 16 +
+           sizeof(int32_t) * (size_t)std::max<int64_t>(items_capacity, 1);
+}
+
+cudaError_t launch_grid_tc2(const DevParams &p, const Plan &plan, const float2 *vis,
+                            const float *weight, const float2 *taps, void *tables, float2 *grid,
+                            int num_sms, int prec, int32_t *status, TcControl ctl,
+                            cudaStream_t s)
+{
+    if (p.T + p.S - 1 > kWin || p.S > 16)
+        return cudaErrorInvalidValue;
+    switch (prec) {
+    case 0: return launch_prec<0>(p, plan, vis, weight, taps, tables, grid, num_sms, status, ctl, s);
+    case 1: return launch_prec<1>(p, plan, vis, weight, taps, tables, grid, num_sms, status, ctl, s);
+    case 2: return launch_prec<2>(p, plan, vis, weight, taps, tables, grid, num_sms, status, ctl, s);
+    case 3: return launch_prec<3>(p, plan, vis, weight, taps, tables, grid, num_sms, status, ctl, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sepw

@@ -19,6 +19,7 @@ FORM_TILED = 1
 FORM_TC_BF16 = 2
 FORM_TC_FP16 = 3
 FORM_TC_FP16X2 = 4
+FORM_TC_BF16X2 = 5
 GRID_TO_IMAGE = 0
 IMAGE_TO_GRID = 1
 IMAGE_TO_GRID_ADJOINT = 2
@@ -80,6 +81,8 @@ _SIG = {
     "sepw_degrid_planned": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "sepw_image": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "sepw_device_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P]),
+    "sepw_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "sepw_test_stall_mma": (ctypes.c_int, [_P, ctypes.c_int]),
     "sepw_plan_batched": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, _P]),
     "sepw_grid_batched": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P,
                                          _P, _P]),
@@ -374,6 +377,16 @@ def sepw_device_status(ctx: Context, stream=None) -> int:
     st = ctypes.c_int(0)
     ctx.check(LIB.sepw_device_status(ctx.handle, ctypes.byref(st), _stream(stream)))
     return int(st.value)
+
+
+def sepw_set_wait_limit(ctx: Context, limit_ns: int):
+    """Limit of every bounded wait in the context's tensor-core kernels."""
+    ctx.check(LIB.sepw_set_wait_limit(ctx.handle, int(limit_ns)))
+
+
+def sepw_test_stall_mma(ctx: Context, enable: bool):
+    """Test hook: the tensor-core kernels issue no MMAs, so their waits run out."""
+    ctx.check(LIB.sepw_test_stall_mma(ctx.handle, 1 if enable else 0))
 
 
 def sepw_image(ctx: Context, direction: int, buf, stream=None):

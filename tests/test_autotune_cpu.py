@@ -8,10 +8,14 @@ from paper_1511_07152_gb300 import autotune as A
 
 def test_candidate_tiles_respect_window():
     for S in (2, 8, 12, 16, 32):
-        for form in ("tiled", "tc_bf16"):
-            ts = A.candidate_tiles(S, form)
-            assert ts and all(T % 2 == 0 and T + S - 1 <= 64 for T in ts)
-    assert A.candidate_tiles(16, "tc_fp16") == [32, 40, 48]
+        ts = A.candidate_tiles(S, "tiled")
+        assert ts and all(T % 2 == 0 and T + S - 1 <= 64 for T in ts)
+    for S in (2, 8, 12, 16):
+        ts = A.candidate_tiles(S, "tc_bf16")
+        assert ts and all(T % 2 == 0 and 8 <= T and T + S - 1 <= 32 for T in ts)
+    assert A.candidate_tiles(32, "tc_bf16") == []  # tensor-core forms take S <= 16
+    assert A.candidate_tiles(16, "tc_fp16") == [8, 12, 16]
+    assert A.candidate_tiles(12, "tc_bf16x2") == [12, 16, 20]
 
 
 def test_choose_respects_accuracy_class():

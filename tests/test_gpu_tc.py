@@ -7,13 +7,15 @@ independent operand roundings, relative rms sqrt(2/3) u, and the grid's
 relative L2 error is about that: 3.2e-3 (BF16) and 4.0e-4 (FP16).  The bars
 below allow a factor ~3: 1e-2 and 1.5e-3.
 
-The split form represents each operand as FP16 hi + lo: the representation
-error is at most 2^-22 of the operand (two roundings of 2^-11 each) once the
-per-item scale puts the largest |W V| near 1, and the dropped lo * lo term is
-another 2^-22; a product is then within 3 * 2^-22 = 7.2e-7 of exact, so the
-grid is held to the FP32 forms' bar, 1e-5.  Degridding in the BF16 and FP16
-forms is the contraction form on tensor cores with the same bars; the hi + lo
-form degrids with the tiled FP32 kernel (1e-5).
+The split forms represent each operand as hi + lo, hi = rn(x), lo = rn(x - hi),
+and take all four products of the splits, so only the rounding of lo is left:
+at most half an ulp of lo, 2^-17 of the operand for BF16 (8-bit significands)
+and 2^-22 for FP16 (11 bits, after the per-item scale puts the largest |W V|
+near 1).  Uniform over that interval, the product's relative rms is 3.3e-6
+(BF16 hi + lo) and 1.9e-7 (FP16 hi + lo), measured on a million random
+operand pairs; both forms are held to the FP32 forms' bar, 1e-5.  Degridding
+in the BF16 and FP16 forms is the contraction form on tensor cores with the
+same bars; the hi + lo forms degrid with the tiled FP32 kernel (1e-5).
 """
 import math
 
@@ -25,7 +27,8 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"bf16": 1e-2, "fp16": 1.5e-3, "fp16x2": 1e-5}
+TOL = {"bf16": 1e-2, "fp16": 1.5e-3, "fp16x2": 1e-5, "bf16x2": 1e-5}
+PRECS = ["bf16", "fp16", "fp16x2", "bf16x2"]
 
 
 @pytest.fixture(scope="module")
@@ -46,7 +49,8 @@ def rel_l2(a, b):
 
 
 def _form(S, name):
-    return {"bf16": S.FORM_TC_BF16, "fp16": S.FORM_TC_FP16, "fp16x2": S.FORM_TC_FP16X2}[name]
+    return {"bf16": S.FORM_TC_BF16, "fp16": S.FORM_TC_FP16, "fp16x2": S.FORM_TC_FP16X2,
+            "bf16x2": S.FORM_TC_BF16X2}[name]
 
 
 def _grid(torch, S, wl, form, tile=0):
@@ -74,7 +78,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16", "fp16x2"])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("name", list(CASES))
 def test_tc_grid_parity(env, prec, name):
     torch, S = env
@@ -86,13 +90,25 @@ def test_tc_grid_parity(env, prec, name):
     assert nd == int((~loc["keep"]).sum())
 
 
-@pytest.mark.parametrize("tile", [16, 32, 48])
-def test_tc_tile_sizes(env, tile):
+@pytest.mark.parametrize("tile", [8, 12, 16])
+@pytest.mark.parametrize("prec", ["fp16", "bf16x2"])
+def test_tc_tile_sizes(env, tile, prec):
+    """Tiles up to the 32-cell window (T + S - 1 <= 32 at S = 16)."""
     torch, S = env
     wl = CASES["rand_S16"]()
     want, _ = _oracle(wl)
-    got, *_ = _grid(torch, S, wl, S.FORM_TC_FP16, tile=tile)
-    assert rel_l2(got, want) <= TOL["fp16"]
+    got, *_ = _grid(torch, S, wl, _form(S, prec), tile=tile)
+    assert rel_l2(got, want) <= TOL[prec]
+
+
+def test_tc_tile_beyond_window_rejected(env):
+    torch, S = env
+    wl = CASES["rand_S16"]()
+    for tile in (18, 32, 48):
+        assert S.sepw_check_params(S.make_params(**wl.params(), tile=tile,
+                                                 form=S.FORM_TC_BF16)) == S.EINVAL
+        assert S.sepw_check_params(S.make_params(**wl.params(), tile=tile,
+                                                 form=S.FORM_TILED)) == S.OK
 
 
 def test_tc_heavy_tile(env):
@@ -114,17 +130,18 @@ def test_tc_heavy_tile(env):
     # about 2^-24 sqrt(n / 2) = 9.4e-6 of the result, the floor of any form
     # that accumulates in FP32.  The hi + lo form's bar is three times that.
     floor = 3.0 * 2.0 ** -24 * math.sqrt(50000 / 2)
-    for prec in ("fp16", "fp16x2"):
+    for prec in ("fp16", "fp16x2", "bf16x2"):
         got, *_ = _grid(torch, S, wl, _form(S, prec))
         assert rel_l2(got, want) <= max(TOL[prec], floor), prec
 
 
 @pytest.mark.parametrize("amp", [1e-7, 1e6, 3e30])
-@pytest.mark.parametrize("prec", ["fp16", "fp16x2"])
+@pytest.mark.parametrize("prec", ["fp16", "fp16x2", "bf16x2"])
 def test_tc_fp16_amplitude_range(env, amp, prec):
     """Visibility amplitudes far outside FP16's range: the per-item
-    power-of-two scale keeps the operands representable and the error bar
-    is unchanged (the grid scales with the amplitude)."""
+    power-of-two scale keeps the FP16 operands representable, BF16 has the
+    FP32 exponent range, and the error bar is unchanged (the grid scales
+    with the amplitude)."""
     torch, S = env
     wl = CASES["rand_S16"]()
     wl.vis = (wl.vis.astype(np.complex128) * amp).astype(np.complex64)
@@ -134,7 +151,7 @@ def test_tc_fp16_amplitude_range(env, amp, prec):
     assert rel_l2(got, want) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16", "fp16x2"])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("name", list(CASES))
 def test_tc_degrid_parity(env, prec, name):
     """Degridding in the tensor-core forms: the contraction form
@@ -263,7 +280,34 @@ def test_tc_meerkat_subsample_errors(env):
     wl = synth.meerkat_like()
     sub = wl.subsample(wl.nvis // 100)
     want, _ = _oracle(sub)
-    for prec in ("bf16", "fp16"):
+    for prec in PRECS:
         got, *_ = _grid(torch, S, sub, _form(S, prec))
         err = rel_l2(got, want)
         assert err <= TOL[prec], (prec, err)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16x2"])
+def test_tc_wait_timeout_reported_and_recovered(env, prec):
+    """The timeout path of the bounded waits: with the MMA thread stalled by
+    the test hook and a 2 ms limit, the launch ends by itself with
+    SEPW_ETIMEOUT recorded (nothing is left waiting, tensor memory is
+    released), and the next launch on the same context is correct."""
+    torch, S = env
+    wl = CASES["rand_S16"]()
+    want, _ = _oracle(wl)
+    _, _, ctx, taps, d = _grid(torch, S, wl, _form(S, prec))
+    N = wl.grid_size
+    S.sepw_set_wait_limit(ctx, 2_000_000)
+    S.sepw_test_stall_mma(ctx, True)
+    g = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+    S.sepw_grid(ctx, taps, d["u"], d["v"], d["w"], d["vis"], d["weight"], g)
+    out = torch.zeros(wl.nvis, dtype=torch.complex64, device="cuda")
+    S.sepw_degrid(ctx, taps, d["u"], d["v"], d["w"], g, d["weight"], out)
+    assert S.sepw_device_status(ctx) == S.ETIMEOUT
+    assert S.sepw_device_status(ctx) == S.OK  # read and reset
+    S.sepw_test_stall_mma(ctx, False)
+    S.sepw_set_wait_limit(ctx, 2_000_000_000)
+    g.zero_()
+    S.sepw_grid(ctx, taps, d["u"], d["v"], d["w"], d["vis"], d["weight"], g)
+    assert S.sepw_device_status(ctx) == S.OK
+    assert rel_l2(g.cpu().numpy(), want) <= TOL[prec]
