@@ -14,8 +14,11 @@ figure through the C ABI with host buffers, and the FP64 oracle timed on the
 host cores on a bounded sample.
 
 --impl reference times the FP64 CPU oracle (the baseline arm) instead.
-Multi-GPU (torchrun): every rank runs an independent replica of the
-workload (the path is not sharded in this build), time = max over ranks.
+Multi-GPU (torchrun, one GPU per rank): every rank grids its own visibility
+shard (the bench workload, the same data on every rank, so the per-rank work
+is fixed: weak scaling) into its grid, one NCCL all-reduce sums the grids,
+and every rank degrids its shard from the summed grid
+(paper_1511_07152_gb300.shard); time = max over ranks.
 """
 from __future__ import annotations
 
@@ -218,9 +221,10 @@ def run_reference(args):
 
 
 def _time_form(S, torch, ctx, taps, dev, grid, out, steps, warmup, stream, evs_out=None,
-               clocks=None):
-    """Times `steps` steps (zero grid, plan, grid, degrid) of one form.
-    Returns (ms per step, plan ms, grid ms, degrid ms)."""
+               clocks=None, reduce_grid=None):
+    """Times `steps` steps (zero grid, plan, grid, [all-reduce of the grid
+    over the ranks], degrid) of one form.  Returns (ms per step, plan ms,
+    grid ms (with the reduction), degrid ms)."""
     def step(ev=None):
         if ev:
             ev[0].record(stream)
@@ -229,6 +233,8 @@ def _time_form(S, torch, ctx, taps, dev, grid, out, steps, warmup, stream, evs_o
         if ev:
             ev[1].record(stream)
         S.sepw_grid_planned(ctx, taps, dev["vis"], dev["weight"], grid)
+        if reduce_grid is not None:
+            reduce_grid(grid)
         if ev:
             ev[2].record(stream)
         S.sepw_degrid_planned(ctx, taps, grid, dev["weight"], out)
@@ -560,11 +566,13 @@ def run_ours(args):
     clocks = Clocks(local)
     clocks.wait_ready()
     t_start = time.perf_counter()
+    from paper_1511_07152_gb300 import shard as SH
+    reduce_grid = SH.allreduce_sum if ws > 1 else None
     ms, plan_ms, grid_ms, degrid_ms = _time_form(S, torch, ctx, taps, dev, grid, out,
                                                  args.steps, args.warmup, stream,
-                                                 clocks=clocks)
+                                                 clocks=clocks, reduce_grid=reduce_grid)
     clk = clocks.stop()
-    # every replica grids and degrids the whole workload once per step
+    # every rank grids and degrids its shard (the whole workload) once per step
     value, ms = whole_job(ms, 2.0 * nvis, ws, dist, device="cuda")
     forms = {"tiled_fp32": {"value": value, "unit": "vis/s", "ms_per_step": ms,
                             "phases_ms": {"plan": plan_ms, "grid": grid_ms,
@@ -669,6 +677,9 @@ def run_ours(args):
             S.sepw_plan(ctx, devs[b]["u"], devs[b]["v"], devs[b]["w"], stream=stream)
             S.sepw_grid_planned(ctx, taps, devs[b]["vis"], devs[b]["weight"], grid,
                                 stream=stream)
+            if reduce_grid is not None:
+                with torch.cuda.stream(stream):
+                    reduce_grid(grid)
             S.sepw_degrid_planned(ctx, taps, grid, devs[b]["weight"], outs[b], stream=stream)
             ev["done"][b].record(stream)
             read_s.wait_event(ev["done"][b])
@@ -766,7 +777,8 @@ def run_ours(args):
             "config": {"workload": wl.name, "nvis": nvis, "kept": nkept, "grid": N,
                        "support": wl.support, "oversample": wl.oversample,
                        "wplanes": wl.n_wplanes, "form": "tiled", "tile": args.tile or 32,
-                       "parallelism": "replicas" if ws > 1 else "single",
+                       "parallelism": (f"vis-sharded x{ws}, one grid all-reduce per step"
+                                       if ws > 1 else "single"),
                        "l2": "inputs larger than L2 (1.16 GB per step), no flush"},
             "phases_ms": {"plan": plan_ms, "grid": grid_ms, "degrid": degrid_ms},
             "grid_updates_per_s": nkept * Ssup * Ssup * 2 * ws / (ms * 1e-3),
