@@ -451,3 +451,44 @@ def test_meerkat_full_size(torch_cuda, S_, meerkat):
     loc = O.locate(p, wl.u[idx], wl.v[idx], wl.w[idx])
     want = O.degrid_separable(p, loc, a.astype(np.complex128), wl.weight[idx], O.taps(p))
     assert rel_l2(out.cpu().numpy()[idx], want) <= TOL_FP32
+
+
+def test_full_step_graph_replay_matches_eager(torch_cuda, S_):
+    """The whole planned step (zero, plan, grid, degrid) captured in one CUDA
+    graph: two replays give the eager step's grid and predictions (to FP32
+    rounding: the atomics' order may differ) and the oracle's within the FP32
+    bar."""
+    torch, S = torch_cuda, S_
+    wl = synth.small_disk()
+    ctx = S.sepw_create(S.make_params(**wl.params(), form=S.FORM_TILED))
+    taps = S.sepw_make_taps(ctx)
+    d = {k: torch.from_numpy(getattr(wl, k)).cuda() for k in ("u", "v", "w", "vis", "weight")}
+    N = wl.grid_size
+    grid = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+    out = torch.empty(wl.nvis, dtype=torch.complex64, device="cuda")
+
+    def step():
+        grid.zero_()
+        S.sepw_plan(ctx, d["u"], d["v"], d["w"])
+        S.sepw_grid_planned(ctx, taps, d["vis"], d["weight"], grid)
+        S.sepw_degrid_planned(ctx, taps, grid, d["weight"], out)
+
+    step()
+    torch.cuda.synchronize()
+    g_eager, o_eager = grid.clone(), out.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        step()
+    p = O.params_from(wl.params())
+    loc = O.locate(p, wl.u, wl.v, wl.w)
+    want = O.grid_separable(p, loc, wl.vis, wl.weight, O.taps(p))
+    for _ in range(2):
+        grid.fill_(7.0)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert rel_l2(grid.cpu().numpy(), g_eager.cpu().numpy()) <= 1e-6
+        assert rel_l2(out.cpu().numpy(), o_eager.cpu().numpy()) <= 1e-6
+        assert rel_l2(grid.cpu().numpy(), want) <= TOL_FP32
+    assert S.sepw_device_status(ctx) == S.OK
