@@ -174,7 +174,11 @@ SEPW_API int sepw_locate(sepw_ctx *ctx, int64_t nvis, const double *u, const dou
  * sepw_plan; u, v, w need not stay alive.  Binning is amortisable over the
  * gridding/degridding calls of a major cycle (Sec. 6).  For the plain form
  * the plan only records the coordinates' pointers, which must then stay
- * valid and unchanged until the next sepw_plan. */
+ * valid and unchanged until the next sepw_plan.  The plan allocates or grows
+ * the context's workspace (bins, work items, and for the tensor-core forms
+ * the gridder's per-call tap tables); sepw_grid_planned and
+ * sepw_degrid_planned then allocate nothing, so those calls can be captured
+ * in a CUDA graph. */
 SEPW_API int sepw_plan(sepw_ctx *ctx, int64_t nvis, const double *u, const double *v,
               const double *w, sepw_stream_t stream);
 

@@ -448,6 +448,18 @@ static int plan_impl(sepw_ctx *ctx, int32_t ngrids, const int64_t *offsets_host,
         SEPW_CUDA(ctx, launch_count_dropped(ctx->dp, nvis, u, v, w, pl.d_dropped, s));
     } else {
         pl.u = pl.v = pl.w = nullptr;
+        if (is_tc_form(ctx->p.form)) {
+            // the contraction gridder's per-call tables and per-item scales:
+            // allocated here, so that the *_planned calls allocate nothing and
+            // can be captured in a CUDA graph
+            const size_t need = tc2_tables_bytes(ctx->dp, pl.items_capacity);
+            if (ctx->tc2_cap < need) {
+                ctx->tc2_cap = 0;
+                if ((rc = grow(ctx, &ctx->d_tc2, need)))
+                    return rc;
+                ctx->tc2_cap = need;
+            }
+        }
         SEPW_CUDA(ctx, launch_plan(ctx->dp, nvis, u, v, w, pl, s));
     }
     pl.valid = true;
@@ -524,13 +536,8 @@ int sepw_grid_planned(sepw_ctx *ctx, const float *taps, const float *vis,
                                              nullptr, s));
         }
     } else if (is_tc_form(pl.form)) {
-        const size_t need = tc2_tables_bytes(ctx->dp, pl.items_capacity);
-        if (ctx->tc2_cap < need) {
-            ctx->tc2_cap = 0;
-            if ((rc = grow(ctx, &ctx->d_tc2, need)))
-                return rc;
-            ctx->tc2_cap = need;
-        }
+        if (ctx->tc2_cap < tc2_tables_bytes(ctx->dp, pl.items_capacity))
+            return fail(ctx, SEPW_ENOPLAN, "tensor-core workspace missing (plan first)");
         SEPW_CUDA(ctx, launch_grid_tc2(ctx->dp, pl, (const float2 *)vis, weight,
                                        (const float2 *)taps, ctx->d_tc2, (float2 *)grid,
                                        ctx->num_sms, tc_prec(pl.form), ctx->d_status,
