@@ -440,11 +440,14 @@ def run_batched(S, torch, args):
     out = {"workload": wl.name, "ngrids": ng, "nvis": wl.nvis, "support": wl.support,
            "counts_min_max": [int(wl.extra["counts"].min()), int(wl.extra["counts"].max())],
            "autotune": tuned}
-    tuned_tile = tuned["tile"] if tuned["form"] == "tiled" else 0
-    for name, form, tile in (("tiled_fp32", S.FORM_TILED, tuned_tile),
+    tiled_tuned = tuned["form"] == "tiled"
+    for name, form, tile in (("tiled_fp32", S.FORM_TILED, tuned["tile"] if tiled_tuned else 0),
                              ("tc_fp16", S.FORM_TC_FP16, 0),
-                             ("tc_fp16x2", S.FORM_TC_FP16X2, 0)):
+                             ("tc_fp16x2", S.FORM_TC_FP16X2, 0),
+                             ("tc_bf16x2", S.FORM_TC_BF16X2, 0)):
         ctx = S.sepw_create(S.make_params(**wl.params(), tile=tile, form=form))
+        if form == S.FORM_TILED and tiled_tuned:
+            S.sepw_set_schedule(ctx, tuned["chunk"], tuned["grid_parts"])
         taps = S.sepw_make_taps(ctx)
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
@@ -477,6 +480,7 @@ def run_batched(S, torch, args):
     out["speedup_tiled_graph_vs_plain"] = pms / out["tiled_fp32"]["graph_grid_ms"]
     out["speedup_tc_fp16_graph_vs_plain"] = pms / out["tc_fp16"]["graph_grid_ms"]
     out["speedup_tc_fp16x2_graph_vs_plain"] = pms / out["tc_fp16x2"]["graph_grid_ms"]
+    out["speedup_tc_bf16x2_graph_vs_plain"] = pms / out["tc_bf16x2"]["graph_grid_ms"]
     ctxp.close()
     del grids, dev
     torch.cuda.empty_cache()

@@ -249,6 +249,16 @@ SEPW_API int sepw_device_status(sepw_ctx *ctx, int *status, sepw_stream_t stream
  * returns; its output is then incomplete.  Host only; applies to later calls. */
 SEPW_API int sepw_set_wait_limit(sepw_ctx *ctx, uint64_t limit_ns);
 
+/* Schedule of the tiled and tensor-core plans (the visibility-per-tile
+ * schedule of a batch of W-stacking layers or channels with uneven counts,
+ * Sec. 4.3): `chunk` visibilities per work item (64 .. 2048, a multiple of
+ * 32; 0 = 2048, the default) and the number of parts a warp of the FP32
+ * block gridder (S = 8, 16) takes of an item at a time (1 .. 16; 0 = 8 on
+ * plans of at least 256 visibilities per tile, else 1, the default).  Takes
+ * effect at the next sepw_plan (the current plan is invalidated); results
+ * do not depend on it beyond FP32 rounding order.  Host only. */
+SEPW_API int sepw_set_schedule(sepw_ctx *ctx, int32_t chunk, int32_t grid_parts);
+
 /* Test hook for the timeout path (no counterpart in the paper): with enable
  * != 0 the tensor-core kernels of this context issue no matrix operations and
  * signal none, so their other roles' bounded waits run out and the call ends

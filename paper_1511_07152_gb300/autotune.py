@@ -1,11 +1,14 @@
-"""Autotuner for the tiled and tensor-core forms: tile edge T and form.
+"""Autotuner for the tiled and tensor-core forms: form, tile edge T and the
+visibility-per-tile schedule.
 
 For a given geometry (grid size, support, oversampling, planes) and a
 representative set of visibilities, every candidate (form, T) is timed on the
 GPU through the C ABI (plan + grid, CUDA events, median of a few runs) and the
-fastest one that meets the caller's accuracy class is kept.  Results are
-cached in a JSON file keyed by the GPU name and the geometry, so a pipeline
-tunes once and reuses the choice.
+fastest one that meets the caller's accuracy class is kept; then, for that
+(form, T), the schedule of the plan (visibilities per work item, and for the
+FP32 block gridder the parts of an item a warp takes at a time) is tuned the
+same way.  Results are cached in a JSON file keyed by the GPU name and the
+geometry, so a pipeline tunes once and reuses the choice.
 
 Host logic (candidate lists, keys, the choice, the cache) is plain Python and
 is tested without a GPU; timing needs the CUDA library.
@@ -36,6 +39,18 @@ def candidate_tiles(support: int, form: str) -> list[int]:
         tmax = (33 - support) & ~1
         return [T for T in (tmax - 8, tmax - 4, tmax) if T >= 8]
     return [T for T in (16, 24, 32, 40, 48, 56) if T + support - 1 <= 64]
+
+
+def candidate_schedules(form: str) -> list[tuple[int, int]]:
+    """(chunk, grid_parts) candidates for a form: work items of 512 .. 2048
+    visibilities; the FP32 tiled form also tries whole items (1) and eighths
+    (8) per warp unit besides the density rule (0).  The plain form has no
+    plan schedule."""
+    if form == "plain":
+        return [(0, 0)]
+    chunks = (512, 1024, 2048)
+    parts = (0, 1, 8) if form == "tiled" else (0,)
+    return [(c, q) for c in chunks for q in parts]
 
 
 def cache_key(gpu: str, grid_size: int, support: int, oversample: int, n_wplanes: int,
@@ -138,7 +153,32 @@ def tune(params: dict, u, v, w, vis, weight, max_error: float = 1e-5, forms=None
             timings[(form, T)] = ms
             ctx.close()
     form, T, m = choose(timings, max_error)
-    out = dict(form=form, tile=T, ms=m,
-               timings={f"{k[0]}:T{k[1]}": statistics.median(v_) for k, v_ in timings.items()})
+    # the schedule of the chosen (form, T)
+    sched = {}
+    ctx = S.sepw_create(S.make_params(**params, tile=T, form=codes[form]))
+    taps = S.sepw_make_taps(ctx)
+    for chunk, parts in candidate_schedules(form):
+        if form != "plain":
+            S.sepw_set_schedule(ctx, chunk, parts)
+        ms = []
+        for r in range(reps + 1):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if vis_offsets is None:
+                S.sepw_plan(ctx, u, v, w)
+            else:
+                S.sepw_plan_batched(ctx, vis_offsets, u, v, w)
+            S.sepw_grid_planned(ctx, taps, vis, weight, grid)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if r > 0:
+                ms.append(a.elapsed_time(b))
+        sched[(chunk, parts)] = statistics.median(ms)
+    ctx.close()
+    (chunk, parts), m2 = min(sched.items(), key=lambda kv: kv[1])
+    out = dict(form=form, tile=T, chunk=chunk, grid_parts=parts, ms=min(m, m2),
+               timings={f"{k[0]}:T{k[1]}": statistics.median(v_) for k, v_ in timings.items()},
+               schedule_timings={f"chunk{k[0]}:parts{k[1]}": v_ for k, v_ in sched.items()})
     cache.put(key, out)
     return out

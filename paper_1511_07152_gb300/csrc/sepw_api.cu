@@ -216,7 +216,7 @@ int ensure_plan_capacity(sepw_ctx *ctx, int64_t nvis, int ngrids)
             return rc;
         pl.capacity = cap;
     }
-    int64_t items = (int64_t)ntiles + nvis / kChunk + 1;
+    int64_t items = (int64_t)ntiles + nvis / ctx->dp.chunk + 1;
     if (items > INT32_MAX)
         return fail(ctx, SEPW_EINVAL, "too many work items");
     if (pl.items_capacity < items) {
@@ -672,6 +672,23 @@ int sepw_set_wait_limit(sepw_ctx *ctx, uint64_t limit_ns)
         return fail(ctx, SEPW_EINVAL, "wait limit %llu ns outside [1 us, 60 s]",
                     (unsigned long long)limit_ns);
     ctx->tc_ctl.wait_ns = limit_ns;
+    return SEPW_OK;
+}
+
+int sepw_set_schedule(sepw_ctx *ctx, int32_t chunk, int32_t grid_parts)
+{
+    if (!ctx)
+        return SEPW_EINVAL;
+    if (chunk == 0)
+        chunk = kChunk;
+    if (chunk < 64 || chunk > kChunk || chunk % 32)
+        return fail(ctx, SEPW_EINVAL, "chunk %d outside 64..%d or not a multiple of 32", chunk,
+                    kChunk);
+    if (grid_parts < 0 || grid_parts > 16)
+        return fail(ctx, SEPW_EINVAL, "grid_parts %d outside 0..16", grid_parts);
+    ctx->dp.chunk = chunk;
+    ctx->dp.grid_parts = grid_parts;
+    ctx->plan.valid = false;  // the next sepw_plan cuts items of the new size
     return SEPW_OK;
 }
 

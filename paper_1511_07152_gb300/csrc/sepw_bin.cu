@@ -106,13 +106,13 @@ __global__ void __launch_bounds__(256) bin_scan_kernel(int32_t ntiles,
 
 // Pass 2 (one block of 1024 threads): exclusive scans of the tile counts
 // (-> slot cursors) and of the per-tile chunk counts (-> work items).  Full
-// chunks (kChunk visibilities) are listed before the partial ones, so that
+// chunks (`chunk` visibilities) are listed before the partial ones, so that
 // dynamically scheduled workers take the heavy items first.
 constexpr int kScanThreads = 1024;
 
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(
-    int32_t ntiles, const int32_t *__restrict__ tile_count, int32_t *__restrict__ cursor,
-    WorkItem *__restrict__ items, int32_t *nitems)
+    int32_t ntiles, int32_t chunk, const int32_t *__restrict__ tile_count,
+    int32_t *__restrict__ cursor, WorkItem *__restrict__ items, int32_t *nitems)
 {
     __shared__ int64_t s_cnt[kScanThreads / 32];
     __shared__ int32_t s_tot_full, s_tot_part;
@@ -132,8 +132,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             c += n[k];
-            nf += n[k] / kChunk;
-            np += (n[k] % kChunk) != 0;
+            nf += n[k] / chunk;
+            np += (n[k] % chunk) != 0;
         }
     }
     // exclusive scans over the threads: warp shuffles, then the warp totals
@@ -188,20 +188,20 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
     for (int i = lo; i < hi; ++i) {
         const int n = tile_count[i];
         cursor[i] = (int32_t)off_c;
-        const int nk = n / kChunk;
+        const int nk = n / chunk;
         for (int q = 0; q < nk; ++q) {
             WorkItem it;
             it.tile = i;
-            it.start = (int32_t)(off_c + (int64_t)q * kChunk);
-            it.count = kChunk;
+            it.start = (int32_t)(off_c + (int64_t)q * chunk);
+            it.count = chunk;
             it.pad = 0;
             items[off_f++] = it;
         }
-        if (n % kChunk) {
+        if (n % chunk) {
             WorkItem it;
             it.tile = i;
-            it.start = (int32_t)(off_c + (int64_t)nk * kChunk);
-            it.count = n % kChunk;
+            it.start = (int32_t)(off_c + (int64_t)nk * chunk);
+            it.count = n % chunk;
             it.pad = 0;
             items[off_p++] = it;
         }
@@ -392,7 +392,7 @@ cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
         plan.ntiles, plan.d_bin, plan.d_tile_count);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    scan_kernel<<<1, kScanThreads, 0, s>>>(plan.ntiles, plan.d_tile_count,
+    scan_kernel<<<1, kScanThreads, 0, s>>>(plan.ntiles, p.chunk, plan.d_tile_count,
                                            plan.d_tile_cursor, plan.d_items, plan.d_nitems);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;

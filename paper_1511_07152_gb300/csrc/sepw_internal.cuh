@@ -32,6 +32,11 @@ struct DevParams {
     // screens exp(2 pi i w a2 l^2) with a2 = a2u (u table), a2v (v table)
     int64_t voff = 0;
     int32_t facet = 0;
+    // schedule of the tiled and tensor-core plans (sepw_set_schedule):
+    // visibilities per work item (<= kChunk) and the parts a block-gridder
+    // warp unit takes of an item (0: by the plan's density)
+    int32_t chunk = 2048;
+    int32_t grid_parts = 0;
     double l0 = 0.0, m0 = 0.0;
     double a2u = -0.5, a2v = -0.5;
 };
@@ -253,7 +258,7 @@ struct WorkItem {
     int32_t pad;
 };
 
-constexpr int kChunk = 2048;      // visibilities per work item (tiled forms)
+constexpr int kChunk = 2048;      // largest work item (visibilities), the default
 constexpr int kMaxWindow = 64;    // T + S - 1 <= kMaxWindow
 
 // Plan workspace (owned by the context).

@@ -832,7 +832,8 @@ static cudaError_t launch_grid_S(const DevParams &p, const Plan &plan, const flo
     if constexpr (Blk2<S>::OK) {
         const unsigned nb = (unsigned)(num_sms * kGridBlkPerSM);
         const int parts =
-            plan.nvis >= (int64_t)kGridPartsMinDensity * plan.ntiles ? kGridParts : 1;
+            p.grid_parts > 0 ? p.grid_parts
+            : plan.nvis >= (int64_t)kGridPartsMinDensity * plan.ntiles ? kGridParts : 1;
         if (planar) {  // rebuilt per call: the caller's table may have changed
             const int64_t n = (p.facet ? 2 : 1) * (int64_t)p.P * p.OS * S;
             if ((e = launch_planar_taps(taps, planar, n, S, s)) != cudaSuccess)

@@ -83,6 +83,7 @@ _SIG = {
     "sepw_device_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P]),
     "sepw_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "sepw_test_stall_mma": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sepw_set_schedule": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "sepw_plan_batched": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, _P]),
     "sepw_grid_batched": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P,
                                          _P, _P]),
@@ -382,6 +383,12 @@ def sepw_device_status(ctx: Context, stream=None) -> int:
 def sepw_set_wait_limit(ctx: Context, limit_ns: int):
     """Limit of every bounded wait in the context's tensor-core kernels."""
     ctx.check(LIB.sepw_set_wait_limit(ctx.handle, int(limit_ns)))
+
+
+def sepw_set_schedule(ctx: Context, chunk: int = 0, grid_parts: int = 0):
+    """Work-item size and block-gridder parts of the next plans (0: defaults)."""
+    ctx.check(LIB.sepw_set_schedule(ctx.handle, int(chunk), int(grid_parts)))
+    ctx.plan_nvis = 0
 
 
 def sepw_test_stall_mma(ctx: Context, enable: bool):

@@ -38,3 +38,13 @@ def test_cache_roundtrip(tmp_path):
     assert c2.get(key)["tile"] == 32
     assert json.load(open(p))[key]["form"] == "tiled"
     assert key != A.cache_key("GB300", 4096, 16, 16, 128, True)
+
+
+def test_candidate_schedules():
+    assert A.candidate_schedules("plain") == [(0, 0)]
+    tiled = A.candidate_schedules("tiled")
+    assert (2048, 0) in tiled and (512, 8) in tiled and len(tiled) == 9
+    tc = A.candidate_schedules("tc_bf16x2")
+    assert all(q == 0 for _, q in tc) and {c for c, _ in tc} == {512, 1024, 2048}
+    for c, q in tiled + tc:
+        assert 64 <= c <= 2048 and c % 32 == 0 and 0 <= q <= 16

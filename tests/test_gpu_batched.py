@@ -136,6 +136,8 @@ def test_autotune_on_gpu(env, tmp_path):
                  reps=2, cache_path=str(tmp_path / "t.json"))
     assert A.FORM_ERROR[res["form"]] <= 1e-5
     assert res["tile"] in A.candidate_tiles(16, res["form"])
+    assert (res["chunk"], res["grid_parts"]) in A.candidate_schedules(res["form"])
+    assert len(res["schedule_timings"]) == len(A.candidate_schedules(res["form"]))
     res2 = A.tune(wl.params(), d["u"], d["v"], d["w"], d["vis"], d["weight"],
                   max_error=1e-5, cache_path=str(tmp_path / "t.json"))
     assert res2 == res

@@ -519,3 +519,37 @@ def test_full_step_graph_replay_matches_eager(torch_cuda, S_):
         assert rel_l2(out.cpu().numpy(), o_eager.cpu().numpy()) <= 1e-6
         assert rel_l2(grid.cpu().numpy(), want) <= TOL_FP32
     assert S.sepw_device_status(ctx) == S.OK
+
+
+@pytest.mark.parametrize("chunk,parts", [(64, 1), (256, 3), (1024, 16), (2048, 0)])
+def test_schedule_does_not_change_the_grid(torch_cuda, S_, chunk, parts):
+    """Work items of any size and any split of them among the gridder's warps
+    give the oracle's grid and predictions (FP32 rounding order aside)."""
+    torch = torch_cuda
+    wl = synth.random_case(81, 30000, 256, 16, 16, 33, edge_fraction=0.1,
+                           radius_cells=40.0)  # dense tiles: many items per tile
+    ctx = _ctx(S_, wl, S_.FORM_TILED)
+    S_.sepw_set_schedule(ctx, chunk, parts)
+    taps = S_.sepw_make_taps(ctx)
+    d = _dev(torch, wl)
+    N = wl.grid_size
+    g = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+    S_.sepw_plan(ctx, d["u"], d["v"], d["w"])
+    S_.sepw_grid_planned(ctx, taps, d["vis"], d["weight"], g)
+    out = torch.empty(wl.nvis, dtype=torch.complex64, device="cuda")
+    S_.sepw_degrid_planned(ctx, taps, g, d["weight"], out)
+    p = O.params_from(wl.params())
+    loc = O.locate(p, wl.u, wl.v, wl.w)
+    T = O.taps(p)
+    a = g.cpu().numpy()
+    assert rel_l2(a, O.grid_separable(p, loc, wl.vis, wl.weight, T)) <= TOL_FP32
+    assert rel_l2(out.cpu().numpy(),
+                  O.degrid_separable(p, loc, a.astype(np.complex128), wl.weight, T)) <= TOL_FP32
+
+
+def test_schedule_rejects_bad_sizes(torch_cuda, S_):
+    wl = synth.random_case(82, 100, 64, 8, 4, 3)
+    ctx = _ctx(S_, wl, S_.FORM_TILED)
+    for chunk, parts in ((32, 0), (4096, 0), (100, 0), (2048, 17), (2048, -1)):
+        with pytest.raises(S_.SepwError):
+            S_.sepw_set_schedule(ctx, chunk, parts)

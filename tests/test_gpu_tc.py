@@ -311,3 +311,22 @@ def test_tc_wait_timeout_reported_and_recovered(env, prec):
     S.sepw_grid(ctx, taps, d["u"], d["v"], d["w"], d["vis"], d["weight"], g)
     assert S.sepw_device_status(ctx) == S.OK
     assert rel_l2(g.cpu().numpy(), want) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x2"])
+@pytest.mark.parametrize("chunk", [64, 544])
+def test_tc_schedule_item_sizes(env, prec, chunk):
+    """Smaller work items (ragged 32-visibility stages, more items per CTA and
+    so both tensor-memory accumulators in turn) give the oracle's grid."""
+    torch, S = env
+    wl = synth.random_case(83, 30000, 256, 16, 16, 33, edge_fraction=0.1, radius_cells=40.0)
+    want, _ = _oracle(wl)
+    ctx = S.sepw_create(S.make_params(**wl.params(), form=_form(S, prec)))
+    S.sepw_set_schedule(ctx, chunk, 0)
+    taps = S.sepw_make_taps(ctx)
+    d = {k: torch.from_numpy(getattr(wl, k)).cuda() for k in ("u", "v", "w", "vis", "weight")}
+    N = wl.grid_size
+    g = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+    S.sepw_grid(ctx, taps, d["u"], d["v"], d["w"], d["vis"], d["weight"], g)
+    assert S.sepw_device_status(ctx) == S.OK
+    assert rel_l2(g.cpu().numpy(), want) <= TOL[prec]
