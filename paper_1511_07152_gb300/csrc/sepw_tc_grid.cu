@@ -75,6 +75,7 @@ using namespace tcx;
 
 constexpr int kStageVis = 32;                  // visibilities per stage (K = 64)
 constexpr int kBufs = 8;                       // stage buffers = producer warps
+static_assert((kBufs & (kBufs - 1)) == 0, "the issue loop takes t mod kBufs as a mask");
 constexpr int kWin = 32;                       // window edge, T + S - 1 <= 32
 constexpr int kM = 128;
 constexpr uint32_t kSboA = 128;                // M-adjacent core matrices
@@ -134,6 +135,17 @@ __device__ __forceinline__ uint4 xor4(uint4 v, uint32_t m)
 __device__ __forceinline__ void st16(unsigned char *p, uint4 v)
 {
     *reinterpret_cast<uint4 *>(p) = v;
+}
+
+// One 32-byte read-only global load (a and b: the two 16-byte halves); p is
+// 32-byte aligned.  A lane's table rows take half as many gathered accesses
+// as with 16-byte loads.
+__device__ __forceinline__ void ldg32(const void *p, uint4 &a, uint4 &b)
+{
+    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z),
+                   "=r"(b.w)
+                 : "l"(p));
 }
 
 // Per-call tables (layouts in the file comment).  vtab from the v-direction
@@ -362,18 +374,24 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                 const int64_t row = (int64_t)rec_plane(r) * p.OS;
                 const uint4 *pa = vtab + ((row + rec_ov(r)) * 8 + (ly & 7)) * (H * 6);
                 const float4 *pu = utab + ((row + rec_ou(r)) * 8 + (lx & 7)) * 12;
+                // the row's 6 H chunks ([h][component][j]) in 32-byte loads
 #pragma unroll
-                for (int h = 0; h < H; ++h)
-#pragma unroll
-                    for (int c = 0; c < 2; ++c)
-#pragma unroll
-                        for (int j = 0; j < 3; ++j)
-                            va[h][c][j] = __ldg(pa + (h * 2 + c) * 3 + j);
+                for (int h = 0; h < H; ++h) {
+                    ldg32(pa + h * 6, va[h][0][0], va[h][0][1]);
+                    ldg32(pa + h * 6 + 2, va[h][0][2], va[h][1][0]);
+                    ldg32(pa + h * 6 + 4, va[h][1][1], va[h][1][2]);
+                }
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
 #pragma unroll
-                    for (int f = 0; f < 4; ++f)
-                        ut[j][f] = __ldg(pu + j * 4 + f);
+                    for (int f = 0; f < 4; f += 2) {
+                        uint4 a, b;
+                        ldg32(pu + j * 4 + f, a, b);
+                        ut[j][f] = make_float4(__uint_as_float(a.x), __uint_as_float(a.y),
+                                               __uint_as_float(a.z), __uint_as_float(a.w));
+                        ut[j][f + 1] = make_float4(__uint_as_float(b.x), __uint_as_float(b.y),
+                                                   __uint_as_float(b.z), __uint_as_float(b.w));
+                    }
             }
             // this warp's next stage: its record and index now
             Cursor cn = cur;
@@ -492,43 +510,58 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
     } else if (warp == C::kMmaWarp) {
         // ------------------------------------------------------------ MMA issue
         if (lane == 0) {
+            // The issue loop is one thread's dependent chain per stage, so it
+            // is kept short: descriptors of buffer 0 computed once, a buffer
+            // and a K step are integer offsets of the start-address field
+            // (shared addresses stay below 2^18, so the 14-bit field never
+            // carries), the K steps are unrolled, and a partner that stopped
+            // is noticed through the bounded wait itself.
             constexpr uint32_t idesc = instr_desc(C::BF ? 1u : 0u, true, true, kM, N);
+            const uint64_t da0 = smem_desc(smem_u32(Abuf), kLboA, kSboA);
+            const uint64_t db0 = smem_desc(smem_u32(Bbuf), C::kLboB, C::kSboB);
+            constexpr uint64_t kStepA = (2 * kLboA) >> 4, kStepB = (2 * C::kLboB) >> 4;
+            constexpr uint64_t kBufA = kABytes >> 4, kBufB = C::kBBytes >> 4;
             Cursor cur;
             int ne = 0;  // non-empty items so far (accumulator ne & 1)
-            while (cursor_next(cur, items, n_items) && !s_abort) {
+            bool ok = true;
+            while (ok && cursor_next(cur, items, n_items)) {
                 if (cur.nst == 0)
                     continue;
                 const int ab = ne & 1;
                 if (ne >= 2 && !mbar_wait(accfree + ab, ((ne >> 1) - 1) & 1, ctl.wait_ns)) {
-                    s_abort = 1;
+                    ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(ab * N);
-                for (int st = 0; st < cur.nst && !s_abort; ++st) {
-                    const int t = cur.tb + st, b = t % kBufs;
+                int t = cur.tb;
+                int left = cur.count;
+                for (int st = 0; st < cur.nst; ++st, ++t, left -= kStageVis) {
+                    const int b = t & (kBufs - 1);
                     if (!mbar_wait(full + b, (t / kBufs) & 1, ctl.wait_ns)) {
-                        s_abort = 1;
+                        ok = false;
                         break;
                     }
                     if (ctl.stall)
                         continue;  // test hook: issue and signal nothing
                     tc_fence_after();
-                    const int nv = min(kStageVis, cur.count - st * kStageVis);
-                    const int nk = (nv + 7) >> 3;  // K = 16 steps holding visibilities
-                    const uint32_t a0 = smem_u32(Abuf + b * kABytes);
-                    const uint32_t b0 = smem_u32(Bbuf + b * C::kBBytes);
-                    for (int kq = 0; kq < nk; ++kq)
-                        mma_f16(d, smem_desc(a0 + kq * 2 * kLboA, kLboA, kSboA),
-                                smem_desc(b0 + kq * 2 * C::kLboB, C::kLboB, C::kSboB), idesc,
-                                (st > 0 || kq > 0) ? 1u : 0u);
+                    const int nk = (min(kStageVis, left) + 7) >> 3;  // K = 16 steps in use
+                    const uint64_t da = da0 + kBufA * b, db = db0 + kBufB * b;
+#pragma unroll
+                    for (int kq = 0; kq < kStageVis / 8; ++kq)
+                        if (kq < nk)
+                            mma_f16(d, da + kStepA * kq, db + kStepB * kq, idesc,
+                                    (st > 0 || kq > 0) ? 1u : 0u);
                     mma_commit(empty + b);
                 }
-                if (!s_abort && !ctl.stall)
+                if (!ok)
+                    break;
+                if (!ctl.stall)
                     mma_commit(accf + ab);
                 ++ne;
             }
-            if (s_abort) {
+            if (!ok) {
+                s_abort = 1;
                 // bounded wait for every MMA this thread issued before the
                 // tensor memory is released
                 mma_commit(drain);
