@@ -73,16 +73,11 @@ namespace {
 
 using namespace tcx;
 
-constexpr int kStageVis = 32;                  // visibilities per stage (K = 64)
 constexpr int kBufs = 8;                       // stage buffers = producer warps
 static_assert((kBufs & (kBufs - 1)) == 0, "the issue loop takes t mod kBufs as a mask");
 constexpr int kWin = 32;                       // window edge, T + S - 1 <= 32
-constexpr int kM = 128;
 constexpr uint32_t kSboA = 128;                // M-adjacent core matrices
-constexpr uint32_t kLboA = 16 * 128 + 16;      // K-adjacent: 16 M-groups + 16 B
-constexpr int kABytes = 8 * kLboA;             // 8 K-groups per stage
 constexpr int kStgStride = 33;                 // staging row (floats), padded
-constexpr int kStgBytes = kM * kStgStride * 4;
 constexpr int kEpiWarps = 4;
 
 // PREC: 0 = BF16, 1 = FP16 (scaled per item), 2 = FP16 hi + lo (scaled),
@@ -93,9 +88,19 @@ struct Cfg {
     static constexpr bool SCALED = PREC == 1 || PREC == 2;
     static constexpr bool BF = PREC == 0 || PREC == 3;
     static constexpr int N = 32 * H;                       // MMA N: [b'_hi | b'_lo]
+    // M = 64 H rows: (h, c, y).  An M = 64 accumulator puts row m in tensor-
+    // memory lane 32 (m / 16) + m % 16 (measured), the first 16 lanes of each
+    // warp quarter; the one-part forms then read and store no zero half of A.
+    static constexpr int M = 64 * H;
+    static constexpr int SV = 32;                          // visibilities per stage
+    static constexpr int SLOTS = SV / 32;                  // per lane
+    static constexpr int KG = SV / 4;                      // K-groups (of 8) per stage
+    static constexpr uint32_t kLboA = (M / 8) * 128 + 16;  // K-adjacent, padded
+    static constexpr int kABytes = KG * kLboA;
+    static constexpr int kStgBytes = M * kStgStride * 4;
     static constexpr uint32_t kSboB = 128;
     static constexpr uint32_t kLboB = (N / 8) * 128 + 16;  // K-adjacent, padded
-    static constexpr int kBBytes = 8 * kLboB;
+    static constexpr int kBBytes = KG * kLboB;
     static constexpr int kProdWarps = kBufs;  // 13 warps: up to 128 registers each
     static constexpr int kMmaWarp = kProdWarps;
     static constexpr int kEpiWarp0 = kProdWarps + 1;
@@ -103,6 +108,7 @@ struct Cfg {
     static constexpr uint32_t kTmemCols = 2 * N;  // two accumulators
     static constexpr size_t kSmem = (size_t)kBufs * (kABytes + kBBytes) + kStgBytes +
                                     sizeof(uint64_t) * (2 * kBufs + 5);
+    static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 };
 
 // (x, y) rounded to the 16-bit format, part h: 0 = hi = rn(v), 1 = lo = rn(v - hi)
@@ -254,6 +260,7 @@ struct Cursor {
     int start = 0, count = 0, tile = 0;
 };
 
+template <int SV>
 __device__ __forceinline__ bool cursor_next(Cursor &c, const WorkItem *__restrict__ items,
                                             int n_items)
 {
@@ -268,16 +275,17 @@ __device__ __forceinline__ bool cursor_next(Cursor &c, const WorkItem *__restric
     c.start = it.start;
     c.count = it.count;
     c.tile = it.tile;
-    c.nst = (it.count + kStageVis - 1) / kStageVis;
+    c.nst = (it.count + SV - 1) / SV;
     return true;
 }
 
 // advance c to the item holding CTA stage t (false: past the last item)
+template <int SV>
 __device__ __forceinline__ bool cursor_seek(Cursor &c, int t, const WorkItem *__restrict__ items,
                                             int n_items)
 {
     while (t >= c.tb + c.nst)
-        if (!cursor_next(c, items, n_items))
+        if (!cursor_next<SV>(c, items, n_items))
             return false;
     return true;
 }
@@ -291,12 +299,13 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
     const int32_t *__restrict__ item_exp, float2 *grid, int32_t *status, TcControl ctl)
 {
     using C = Cfg<PREC>;
-    constexpr int H = C::H, N = C::N;
+    constexpr int H = C::H, N = C::N, SV = C::SV;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *const Abuf = smem;                          // [kBufs]
-    unsigned char *const Bbuf = smem + kBufs * kABytes;        // [kBufs]
+    unsigned char *const Bbuf = smem + kBufs * C::kABytes;     // [kBufs]
     float *const stg = reinterpret_cast<float *>(Bbuf + kBufs * C::kBBytes);
-    uint64_t *const full = reinterpret_cast<uint64_t *>(Bbuf + kBufs * C::kBBytes + kStgBytes);
+    uint64_t *const full =
+        reinterpret_cast<uint64_t *>(Bbuf + kBufs * C::kBBytes + C::kStgBytes);
     uint64_t *const empty = full + kBufs;
     uint64_t *const accf = empty + kBufs;     // [2]
     uint64_t *const accfree = accf + 2;       // [2]
@@ -308,8 +317,8 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_items = *nitems;
 
-    // the one-part forms never write rows 64..127 of A: zero them once
-    for (int e = tid; e < kBufs * kABytes / 16; e += C::kBlock)
+    // operand bytes every stage overwrites; zeroed once for a clean start
+    for (int e = tid; e < kBufs * C::kABytes / 16; e += C::kBlock)
         reinterpret_cast<uint4 *>(Abuf)[e] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         for (int b = 0; b < kBufs; ++b) {
@@ -334,122 +343,135 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
 
     if (warp < C::kProdWarps) {
         // ------------------------------------------------------------ producers
-        const int i = lane;  // slot in the stage
-        // A: byte offsets of this slot's two K columns (chunk row 0); B: rows
-        const uint32_t a_off0 = ((2 * i) >> 3) * kLboA + ((2 * i) & 7) * 16;
-        const uint32_t a_off1 = ((2 * i + 1) >> 3) * kLboA + ((2 * i + 1) & 7) * 16;
-        const uint32_t b_off0 = ((2 * i) >> 3) * C::kLboB + ((2 * i) & 7) * 16;
-        const uint32_t b_off1 = ((2 * i + 1) >> 3) * C::kLboB + ((2 * i + 1) & 7) * 16;
         Cursor cur;
         int t = warp;
-        bool ok = cursor_next(cur, items, n_items) && cursor_seek(cur, t, items, n_items);
-        // record and visibility index of the lane's slot, one stage ahead
-        uint64_t r = 0;
-        int vi = -1;
-        auto fetch = [&](const Cursor &c, int t_, uint64_t &r_, int &vi_) {
-            const int e = (t_ - c.tb) * kStageVis + i;
-            vi_ = -1;
-            if (e < c.count) {
-                r_ = __ldg(reinterpret_cast<const unsigned long long *>(rec) + c.start + e);
-                vi_ = __ldg(perm + c.start + e);
+        bool ok = cursor_next<SV>(cur, items, n_items) && cursor_seek<SV>(cur, t, items, n_items);
+        // records and visibility indices of the lane's slots, one stage ahead
+        uint64_t r[C::SLOTS];
+        int vi[C::SLOTS];
+        auto fetch = [&](const Cursor &c, int t_, uint64_t (&r_)[C::SLOTS],
+                         int (&vi_)[C::SLOTS]) {
+#pragma unroll
+            for (int sl = 0; sl < C::SLOTS; ++sl) {
+                const int e = (t_ - c.tb) * SV + 32 * sl + lane;
+                vi_[sl] = -1;
+                if (e < c.count) {
+                    r_[sl] = __ldg(reinterpret_cast<const unsigned long long *>(rec) + c.start +
+                                   e);
+                    vi_[sl] = __ldg(perm + c.start + e);
+                }
             }
         };
         if (ok)
             fetch(cur, t, r, vi);
         while (ok && !s_abort) {
-            // this stage's taps and value
-            uint4 va[H][2][3];
-            float4 ut[3][4];
-            float2 x = make_float2(0.f, 0.f);
-            float wt = 0.f;
-            int lx = 0, ly = 0;
-            uint32_t cjm = 0;
-            const bool valid = vi >= 0;
-            if (valid) {
-                x = __ldg(vis + vi);
-                wt = weight ? __ldg(weight + vi) : 1.0f;
-                lx = rec_lx(r);
-                ly = rec_ly(r);
-                cjm = rec_conj(r) ? 0x80008000u : 0u;
-                const int64_t row = (int64_t)rec_plane(r) * p.OS;
-                const uint4 *pa = vtab + ((row + rec_ov(r)) * 8 + (ly & 7)) * (H * 6);
-                const float4 *pu = utab + ((row + rec_ou(r)) * 8 + (lx & 7)) * 12;
-                // the row's 6 H chunks ([h][component][j]) in 32-byte loads
-#pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    ldg32(pa + h * 6, va[h][0][0], va[h][0][1]);
-                    ldg32(pa + h * 6 + 2, va[h][0][2], va[h][1][0]);
-                    ldg32(pa + h * 6 + 4, va[h][1][1], va[h][1][2]);
-                }
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-#pragma unroll
-                    for (int f = 0; f < 4; f += 2) {
-                        uint4 a, b;
-                        ldg32(pu + j * 4 + f, a, b);
-                        ut[j][f] = make_float4(__uint_as_float(a.x), __uint_as_float(a.y),
-                                               __uint_as_float(a.z), __uint_as_float(a.w));
-                        ut[j][f + 1] = make_float4(__uint_as_float(b.x), __uint_as_float(b.y),
-                                                   __uint_as_float(b.z), __uint_as_float(b.w));
-                    }
-            }
-            // this warp's next stage: its record and index now
             Cursor cn = cur;
             const int tn = t + kBufs;
-            const bool okn = cursor_seek(cn, tn, items, n_items);
-            uint64_t rn = 0;
-            int vin = -1;
-            if (okn)
-                fetch(cn, tn, rn, vin);
-
+            bool okn = false;
+            uint64_t rn[C::SLOTS];
+            int vin[C::SLOTS];
+#pragma unroll
+            for (int sl = 0; sl < C::SLOTS; ++sl)
+                vin[sl] = -1;
             float scale = 1.0f;
             if constexpr (C::SCALED)
                 scale = ldexpf(1.0f, -__ldg(item_exp + cur.item));
             const int b = t % kBufs;
-            if (t >= kBufs) {
-                // buffer b held stage t - kBufs: wait (lane 0) for its MMAs
-                if (lane == 0 && !s_abort &&
-                    !mbar_wait(empty + b, ((t / kBufs) - 1) & 1, ctl.wait_ns))
-                    s_abort = 1;
-                __syncwarp();
-                tc_fence_after();
-            }
-            unsigned char *const A = Abuf + b * kABytes;
+            unsigned char *const A = Abuf + b * C::kABytes;
             unsigned char *const B = Bbuf + b * C::kBBytes;
             const uint4 z = make_uint4(0, 0, 0, 0);
-            // A: chunk j of part h goes to chunk row j + ly / 8 of each quarter
-            // (h, re rows) / (h, im rows) of the two columns
-            const int oy8 = valid ? (ly >> 3) : 8;
 #pragma unroll
-            for (int h = 0; h < H; ++h) {
+            for (int sl = 0; sl < C::SLOTS; ++sl) {
+                const int i = 32 * sl + lane;  // slot in the stage
+                // this slot's taps and value
+                uint4 va[H][2][3];
+                float4 ut[3][4];
+                float2 x = make_float2(0.f, 0.f);
+                float wt = 0.f;
+                int lx = 0, ly = 0;
+                uint32_t cjm = 0;
+                const bool valid = vi[sl] >= 0;
+                if (valid) {
+                    x = __ldg(vis + vi[sl]);
+                    wt = weight ? __ldg(weight + vi[sl]) : 1.0f;
+                    lx = rec_lx(r[sl]);
+                    ly = rec_ly(r[sl]);
+                    cjm = rec_conj(r[sl]) ? 0x80008000u : 0u;
+                    const int64_t row = (int64_t)rec_plane(r[sl]) * p.OS;
+                    const uint4 *pa = vtab + ((row + rec_ov(r[sl])) * 8 + (ly & 7)) * (H * 6);
+                    const float4 *pu = utab + ((row + rec_ou(r[sl])) * 8 + (lx & 7)) * 12;
+                    // the row's 6 H chunks ([h][component][j]) in 32-byte loads
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const int xq = j + oy8;
-                    if (xq < 4) {
-                        const uint4 R = va[h][0][j];
-                        const uint4 I = xor4(va[h][1][j], cjm);  // conj(a) for w < 0
-                        const uint32_t g0 = (h * 8 + xq) * kSboA, g1 = g0 + 4 * kSboA;
-                        st16(A + a_off0 + g0, R);
-                        st16(A + a_off0 + g1, I);
-                        st16(A + a_off1 + g0, xor4(I, 0x80008000u));
-                        st16(A + a_off1 + g1, R);
+                    for (int h = 0; h < H; ++h) {
+                        ldg32(pa + h * 6, va[h][0][0], va[h][0][1]);
+                        ldg32(pa + h * 6 + 2, va[h][0][2], va[h][1][0]);
+                        ldg32(pa + h * 6 + 4, va[h][1][1], va[h][1][2]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+#pragma unroll
+                        for (int f = 0; f < 4; f += 2) {
+                            uint4 a, bb;
+                            ldg32(pu + j * 4 + f, a, bb);
+                            ut[j][f] = make_float4(__uint_as_float(a.x), __uint_as_float(a.y),
+                                                   __uint_as_float(a.z), __uint_as_float(a.w));
+                            ut[j][f + 1] =
+                                make_float4(__uint_as_float(bb.x), __uint_as_float(bb.y),
+                                            __uint_as_float(bb.z), __uint_as_float(bb.w));
+                        }
+                }
+                if (sl == 0) {
+                    // the next stage of this warp: its records and indices now
+                    okn = cursor_seek<SV>(cn, tn, items, n_items);
+                    if (okn)
+                        fetch(cn, tn, rn, vin);
+                }
+                if (sl == 0 && t >= kBufs) {
+                    // buffer b held stage t - kBufs: wait (lane 0) for its MMAs
+                    if (lane == 0 && !s_abort &&
+                        !mbar_wait(empty + b, ((t / kBufs) - 1) & 1, ctl.wait_ns))
+                        s_abort = 1;
+                    __syncwarp();
+                    tc_fence_after();
+                }
+                // A: byte offsets of this slot's two K columns (chunk row 0);
+                // B likewise
+                const uint32_t a_off0 = ((2 * i) >> 3) * C::kLboA + ((2 * i) & 7) * 16;
+                const uint32_t a_off1 = ((2 * i + 1) >> 3) * C::kLboA + ((2 * i + 1) & 7) * 16;
+                const uint32_t b_off0 = ((2 * i) >> 3) * C::kLboB + ((2 * i) & 7) * 16;
+                const uint32_t b_off1 = ((2 * i + 1) >> 3) * C::kLboB + ((2 * i + 1) & 7) * 16;
+                // A: chunk j of part h goes to chunk row j + ly / 8 of the
+                // (h, re rows) and (h, im rows) quarters of the two columns
+                const int oy8 = valid ? (ly >> 3) : 8;
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const int xq = j + oy8;
+                        if (xq < 4) {
+                            const uint4 R = va[h][0][j];
+                            const uint4 I = xor4(va[h][1][j], cjm);  // conj(a) for w < 0
+                            const uint32_t g0 = (h * 8 + xq) * kSboA, g1 = g0 + 4 * kSboA;
+                            st16(A + a_off0 + g0, R);
+                            st16(A + a_off0 + g1, I);
+                            st16(A + a_off1 + g0, xor4(I, 0x80008000u));
+                            st16(A + a_off1 + g1, R);
+                        }
+                    }
+#pragma unroll
+                    for (int xq = 0; xq < 4; ++xq) {
+                        if (xq < oy8 || xq > oy8 + 2) {
+                            const uint32_t g0 = (h * 8 + xq) * kSboA, g1 = g0 + 4 * kSboA;
+                            st16(A + a_off0 + g0, z);
+                            st16(A + a_off0 + g1, z);
+                            st16(A + a_off1 + g0, z);
+                            st16(A + a_off1 + g1, z);
+                        }
                     }
                 }
-#pragma unroll
-                for (int xq = 0; xq < 4; ++xq) {
-                    if (xq < oy8 || xq > oy8 + 2) {
-                        const uint32_t g0 = (h * 8 + xq) * kSboA, g1 = g0 + 4 * kSboA;
-                        st16(A + a_off0 + g0, z);
-                        st16(A + a_off0 + g1, z);
-                        st16(A + a_off1 + g0, z);
-                        st16(A + a_off1 + g1, z);
-                    }
-                }
-            }
-            // B: W V times the u-taps, chunk j to chunk row j + lx / 8 (and
-            // 4 + that for the lo part)
-            const int ox8 = valid ? (lx >> 3) : 8;
-            {
+                // B: W V times the u-taps, chunk j to chunk row j + lx / 8 (and
+                // 4 + that for the lo part)
+                const int ox8 = valid ? (lx >> 3) : 8;
                 const float wr = (wt * x.x) * scale;  // exact power-of-two scaling
                 const float wi = (wt * x.y) * scale;
                 const float wis = cjm ? -wi : wi;      // conj(u-taps) for w < 0
@@ -504,8 +526,11 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
             cur = cn;
             t = tn;
             ok = okn;
-            r = rn;
-            vi = vin;
+#pragma unroll
+            for (int sl = 0; sl < C::SLOTS; ++sl) {
+                r[sl] = rn[sl];
+                vi[sl] = vin[sl];
+            }
         }
     } else if (warp == C::kMmaWarp) {
         // ------------------------------------------------------------ MMA issue
@@ -516,15 +541,15 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
             // (shared addresses stay below 2^18, so the 14-bit field never
             // carries), the K steps are unrolled, and a partner that stopped
             // is noticed through the bounded wait itself.
-            constexpr uint32_t idesc = instr_desc(C::BF ? 1u : 0u, true, true, kM, N);
-            const uint64_t da0 = smem_desc(smem_u32(Abuf), kLboA, kSboA);
+            constexpr uint32_t idesc = instr_desc(C::BF ? 1u : 0u, true, true, C::M, N);
+            const uint64_t da0 = smem_desc(smem_u32(Abuf), C::kLboA, kSboA);
             const uint64_t db0 = smem_desc(smem_u32(Bbuf), C::kLboB, C::kSboB);
-            constexpr uint64_t kStepA = (2 * kLboA) >> 4, kStepB = (2 * C::kLboB) >> 4;
-            constexpr uint64_t kBufA = kABytes >> 4, kBufB = C::kBBytes >> 4;
+            constexpr uint64_t kStepA = (2 * C::kLboA) >> 4, kStepB = (2 * C::kLboB) >> 4;
+            constexpr uint64_t kBufA = C::kABytes >> 4, kBufB = C::kBBytes >> 4;
             Cursor cur;
             int ne = 0;  // non-empty items so far (accumulator ne & 1)
             bool ok = true;
-            while (ok && cursor_next(cur, items, n_items)) {
+            while (ok && cursor_next<SV>(cur, items, n_items)) {
                 if (cur.nst == 0)
                     continue;
                 const int ab = ne & 1;
@@ -536,7 +561,7 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                 const uint32_t d = tmem + (uint32_t)(ab * N);
                 int t = cur.tb;
                 int left = cur.count;
-                for (int st = 0; st < cur.nst; ++st, ++t, left -= kStageVis) {
+                for (int st = 0; st < cur.nst; ++st, ++t, left -= SV) {
                     const int b = t & (kBufs - 1);
                     if (!mbar_wait(full + b, (t / kBufs) & 1, ctl.wait_ns)) {
                         ok = false;
@@ -545,10 +570,10 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                     if (ctl.stall)
                         continue;  // test hook: issue and signal nothing
                     tc_fence_after();
-                    const int nk = (min(kStageVis, left) + 7) >> 3;  // K = 16 steps in use
+                    const int nk = (min(SV, left) + 7) >> 3;  // K = 16 steps in use
                     const uint64_t da = da0 + kBufA * b, db = db0 + kBufB * b;
 #pragma unroll
-                    for (int kq = 0; kq < kStageVis / 8; ++kq)
+                    for (int kq = 0; kq < SV / 8; ++kq)
                         if (kq < nk)
                             mma_f16(d, da + kStepA * kq, db + kStepB * kq, idesc,
                                     (st > 0 || kq > 0) ? 1u : 0u);
@@ -573,10 +598,13 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
         const int qq = warp & 3;  // tensor-memory lane quarter of this warp
         const int ew = warp - C::kEpiWarp0;
         const int et = tid - 32 * C::kEpiWarp0;  // 0 .. 127
-        float *const row = stg + (32 * qq + lane) * kStgStride;
+        // accumulator row held by this lane: M = 128, row 32 qq + lane; M = 64,
+        // row 16 qq + lane for lanes below 16 (the other lanes hold nothing)
+        const bool holds = C::M == 128 || lane < 16;
+        float *const row = stg + (C::M == 128 ? 32 * qq + lane : 16 * qq + (lane & 15)) * kStgStride;
         Cursor cur;
         int ne = 0;
-        while (cursor_next(cur, items, n_items)) {
+        while (cursor_next<SV>(cur, items, n_items)) {
             if (cur.nst == 0)
                 continue;
             const int ab = ne & 1;
@@ -618,9 +646,11 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
             float back = 1.0f;
             if constexpr (C::SCALED)
                 back = ldexpf(1.0f, __ldg(item_exp + cur.item));
+            if (holds) {
 #pragma unroll
-            for (int xx = 0; xx < 32; ++xx)
-                row[xx] = v[xx] * back;
+                for (int xx = 0; xx < 32; ++xx)
+                    row[xx] = v[xx] * back;
+            }
             asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
             const int W = p.T + p.S - 1;
             const TileOrigin o = tile_origin(p, cur.tile);
