@@ -697,17 +697,20 @@ def run_ours(args):
     # bf16 / fp16, tiled FP32 for the hi + lo form) ----
     peaks, peak_src = _peaks()
     if not args.skip_tc:
-        for name, form, nprod in (("tc_bf16", S.FORM_TC_BF16, 1),
-                                  ("tc_fp16", S.FORM_TC_FP16, 1),
-                                  ("tc_fp16x2", S.FORM_TC_FP16X2, 2),
-                                  ("tc_bf16x2", S.FORM_TC_BF16X2, 2)):
+        # (name, form, split parts H, peak / bf16 peak, degrid on tensor cores)
+        for name, form, H, pratio, tc_dg in (
+                ("tc_bf16", S.FORM_TC_BF16, 1, 1.0, True),
+                ("tc_fp16", S.FORM_TC_FP16, 1, 1.0, True),
+                ("tc_fp16x2", S.FORM_TC_FP16X2, 2, 1.0, False),
+                ("tc_bf16x2", S.FORM_TC_BF16X2, 2, 1.0, False),
+                ("tc_tf32", S.FORM_TC_TF32, 1, 1.1 / 2.25, False)):
             c2 = S.sepw_create(S.make_params(**wl.params(), form=form))
             fms, fp, fg, fd = _time_form(S, torch, c2, taps, dev, grid, out,
                                          max(3, args.steps // 2), 2, stream)
-            # executed dense MMA flops: one M128 x N32 x K16 MMA per 8 visibilities
-            # of a stage (two for the hi + lo forms), K = 2 real components per
-            # visibility
-            mma_flops = 2 * 128 * 32 * 2 * nkept * nprod
+            # executed dense MMA flops: an M (64 H) x N (32 H) accumulator, K = 2
+            # real components per visibility (ragged stages not counted)
+            mma_flops = 2 * (64 * H) * (32 * H) * 2 * nkept
+            peak = float(peaks["bf16_tflops"]) * pratio
             fvalue, fms = whole_job(fms, 2.0 * nvis, ws, dist, device="cuda")
             forms[name] = {"value": fvalue, "unit": "vis/s",
                            "ms_per_step": fms,
@@ -715,13 +718,13 @@ def run_ours(args):
                            "tensor_roofline": {
                                "bound": "tensor", "unit": "TFLOP/s",
                                "achieved": mma_flops / (fg * 1e-3) / 1e12,
-                               "peak": float(peaks["bf16_tflops"]),
-                               "frac": mma_flops / (fg * 1e-3) / 1e12 /
-                               float(peaks["bf16_tflops"]),
-                               "note": "dense MMA flops executed (2 x 128 x 32 x 2 per vis "
-                                       "per MMA) over the grid kernel; burst bf16 peak "
-                                       "(fp16 same)"}}
-            if nprod == 1:
+                               "peak": peak,
+                               "frac": mma_flops / (fg * 1e-3) / 1e12 / peak,
+                               "note": "dense MMA flops executed (2 x 64H x 32H x 2 per "
+                                       "vis) over the grid kernel; burst bf16 peak of "
+                                       "measured (fp16 same; tf32: x 1.1/2.25, the "
+                                       "nominal ratio)"}}
+            if tc_dg:
                 # degridding: one M128 x N64 x K128 product per 128 visibilities
                 # of a work item (Q = conj(Av) X over the item's 32-column window)
                 dg_flops = 2 * 64 * 128 * nkept
@@ -750,7 +753,8 @@ def run_ours(args):
         fm = {"tiled_fp32": S.FORM_TILED, "plain_fp32": S.FORM_PLAIN}
         if not args.skip_tc:
             fm.update(tc_bf16=S.FORM_TC_BF16, tc_fp16=S.FORM_TC_FP16,
-                      tc_fp16x2=S.FORM_TC_FP16X2, tc_bf16x2=S.FORM_TC_BF16X2)
+                      tc_fp16x2=S.FORM_TC_FP16X2, tc_bf16x2=S.FORM_TC_BF16X2,
+                      tc_tf32=S.FORM_TC_TF32)
         errs, nsub = _form_errors(S, torch, wl, fm)
         for k, e in errs.items():
             if k in forms:

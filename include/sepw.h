@@ -87,6 +87,11 @@ extern "C" {
                                  BF16 hi + lo (all four products; no scale:
                                  BF16 has the FP32 exponent range).
                                  Degridding uses the tiled FP32 form. */
+#define SEPW_FORM_TC_TF32 6   /* as SEPW_FORM_TC_BF16 with TF32 operands (10-bit
+                                 mantissa, FP32 range: no scale), rounded from
+                                 the caller's FP32 taps and W V times them;
+                                 FP16-class accuracy.  Degridding uses the
+                                 tiled FP32 form. */
 
 /* image directions (sepw_image) */
 #define SEPW_GRID_TO_IMAGE 0

@@ -21,10 +21,10 @@ import statistics
 from dataclasses import dataclass, field
 
 FORM_NAMES = {0: "plain", 1: "tiled", 2: "tc_bf16", 3: "tc_fp16", 4: "tc_fp16x2",
-              5: "tc_bf16x2"}
+              5: "tc_bf16x2", 6: "tc_tf32"}
 # accuracy class of each form: the grid's relative L2 error bound it meets
 FORM_ERROR = {"plain": 1e-5, "tiled": 1e-5, "tc_bf16": 1e-2, "tc_fp16": 1.5e-3,
-              "tc_fp16x2": 1e-5, "tc_bf16x2": 1e-5}
+              "tc_fp16x2": 1e-5, "tc_bf16x2": 1e-5, "tc_tf32": 1.5e-3}
 
 
 def candidate_tiles(support: int, form: str) -> list[int]:
@@ -124,7 +124,7 @@ def tune(params: dict, u, v, w, vis, weight, max_error: float = 1e-5, forms=None
         hit = cache.get(key)
         if hit and FORM_ERROR[hit["form"]] <= max_error:
             return hit
-    forms = forms or [f for f in ("plain", "tiled", "tc_fp16x2", "tc_bf16x2", "tc_fp16",
+    forms = forms or [f for f in ("plain", "tiled", "tc_fp16x2", "tc_bf16x2", "tc_tf32", "tc_fp16",
                                   "tc_bf16") if FORM_ERROR[f] <= max_error]
     codes = {v_: k for k, v_ in FORM_NAMES.items()}
     N = params["grid_size"]

@@ -77,13 +77,14 @@ int cuda_fail(sepw_ctx *ctx, cudaError_t e, const char *where)
 bool is_tc_form(int form)
 {
     return form == SEPW_FORM_TC_BF16 || form == SEPW_FORM_TC_FP16 ||
-           form == SEPW_FORM_TC_FP16X2 || form == SEPW_FORM_TC_BF16X2;
+           form == SEPW_FORM_TC_FP16X2 || form == SEPW_FORM_TC_BF16X2 ||
+           form == SEPW_FORM_TC_TF32;
 }
 
 int tc_prec(int form)
 {
     return form == SEPW_FORM_TC_BF16 ? 0 : form == SEPW_FORM_TC_FP16 ? 1
-         : form == SEPW_FORM_TC_FP16X2 ? 2 : 3;
+         : form == SEPW_FORM_TC_FP16X2 ? 2 : form == SEPW_FORM_TC_BF16X2 ? 3 : 4;
 }
 
 int effective_tile(const sepw_params *p)

@@ -81,12 +81,15 @@ constexpr int kStgStride = 33;                 // staging row (floats), padded
 constexpr int kEpiWarps = 4;
 
 // PREC: 0 = BF16, 1 = FP16 (scaled per item), 2 = FP16 hi + lo (scaled),
-// 3 = BF16 hi + lo
+// 3 = BF16 hi + lo, 4 = TF32
 template <int PREC>
 struct Cfg {
     static constexpr int H = (PREC == 2 || PREC == 3) ? 2 : 1;  // split parts
     static constexpr bool SCALED = PREC == 1 || PREC == 2;
     static constexpr bool BF = PREC == 0 || PREC == 3;
+    // TF32: K-major operands of 4-byte elements (MN-major TF32 operands gave
+    // zeros on the GB300), written from the caller's taps; K = 8 per MMA
+    static constexpr bool TF32 = PREC == 4;
     static constexpr int N = 32 * H;                       // MMA N: [b'_hi | b'_lo]
     // M = 64 H rows: (h, c, y).  An M = 64 accumulator puts row m in tensor-
     // memory lane 32 (m / 16) + m % 16 (measured), the first 16 lanes of each
@@ -94,7 +97,9 @@ struct Cfg {
     static constexpr int M = 64 * H;
     static constexpr int SV = 32;                          // visibilities per stage
     static constexpr int SLOTS = SV / 32;                  // per lane
-    static constexpr int KG = SV / 4;                      // K-groups (of 8) per stage
+    // core matrices along K per stage: 8 (16-bit) or 4 (TF32) K elements each
+    static constexpr int KG = TF32 ? SV / 2 : SV / 4;
+    static constexpr int VPK = TF32 ? 4 : 8;               // visibilities per MMA
     static constexpr uint32_t kLboA = (M / 8) * 128 + 16;  // K-adjacent, padded
     static constexpr int kABytes = KG * kLboA;
     static constexpr int kStgBytes = M * kStgStride * 4;
@@ -152,6 +157,19 @@ __device__ __forceinline__ void ldg32(const void *p, uint4 &a, uint4 &b)
                  : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z),
                    "=r"(b.w)
                  : "l"(p));
+}
+
+// FP32 -> TF32, round to nearest (ties away), as a 32-bit pattern
+__device__ __forceinline__ uint32_t to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void st8(unsigned char *p, uint32_t a, uint32_t b)
+{
+    *reinterpret_cast<uint2 *>(p) = make_uint2(a, b);
 }
 
 // Per-call tables (layouts in the file comment).  vtab from the v-direction
@@ -296,7 +314,8 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
     const uint64_t *__restrict__ rec, const int32_t *__restrict__ perm,
     const float2 *__restrict__ vis, const float *__restrict__ weight,
     const uint4 *__restrict__ vtab, const float4 *__restrict__ utab,
-    const int32_t *__restrict__ item_exp, float2 *grid, int32_t *status, TcControl ctl)
+    const float2 *__restrict__ taps, const int32_t *__restrict__ item_exp, float2 *grid,
+    int32_t *status, TcControl ctl)
 {
     using C = Cfg<PREC>;
     constexpr int H = C::H, N = C::N, SV = C::SV;
@@ -383,6 +402,78 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
 #pragma unroll
             for (int sl = 0; sl < C::SLOTS; ++sl) {
                 const int i = 32 * sl + lane;  // slot in the stage
+                if constexpr (C::TF32) {
+                    // K-major, 4-byte elements: slot i's two K elements (re, im
+                    // components) are 8 adjacent bytes of every row
+                    float2 tv[16], tu[16];
+                    float2 x = make_float2(0.f, 0.f);
+                    float wt = 0.f;
+                    int lx = 64, ly = 64;
+                    bool cj = false;
+                    const bool valid = vi[sl] >= 0;
+                    if (valid) {
+                        x = __ldg(vis + vi[sl]);
+                        wt = weight ? __ldg(weight + vi[sl]) : 1.0f;
+                        lx = rec_lx(r[sl]);
+                        ly = rec_ly(r[sl]);
+                        cj = rec_conj(r[sl]);
+                        const int64_t row = (int64_t)rec_plane(r[sl]) * p.OS;
+                        const float2 *pv = taps + p.voff + (row + rec_ov(r[sl])) * p.S;
+                        const float2 *pu = taps + (row + rec_ou(r[sl])) * p.S;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            tv[j] = j < p.S ? __ldg(pv + j) : make_float2(0.f, 0.f);
+                            tu[j] = j < p.S ? __ldg(pu + j) : make_float2(0.f, 0.f);
+                        }
+                    }
+                    if (sl == 0) {
+                        okn = cursor_seek<SV>(cn, tn, items, n_items);
+                        if (okn)
+                            fetch(cn, tn, rn, vin);
+                    }
+                    if (sl == 0 && t >= kBufs) {
+                        if (lane == 0 && !s_abort &&
+                            !mbar_wait(empty + b, ((t / kBufs) - 1) & 1, ctl.wait_ns))
+                            s_abort = 1;
+                        __syncwarp();
+                        tc_fence_after();
+                    }
+                    // element (m, k) at (k % 4) 4 + (k / 4) LBO + (m % 8) 16 + (m / 8) 128
+                    unsigned char *const Ak = A + (i & 1) * 8 + (i >> 1) * C::kLboA;
+                    unsigned char *const Bk = B + (i & 1) * 8 + (i >> 1) * C::kLboB;
+                    auto roff = [](int m) { return (uint32_t)((m & 7) * 16 + (m >> 3) * 128); };
+                    const int S = p.S;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (valid && j < S) {
+                            const int y = ly + j;  // rows (0, y): re of G, (1, y): im
+                            const float ar = tv[j].x, ai = cj ? -tv[j].y : tv[j].y;
+                            st8(Ak + roff(y), to_tf32(ar), to_tf32(-ai));
+                            st8(Ak + roff(32 + y), to_tf32(ai), to_tf32(ar));
+                        }
+                    }
+#pragma unroll
+                    for (int y = 0; y < 32; ++y) {
+                        if (y < ly || y >= ly + S) {
+                            st8(Ak + roff(y), 0u, 0u);
+                            st8(Ak + roff(32 + y), 0u, 0u);
+                        }
+                    }
+                    const float wr = wt * x.x, wi = wt * x.y;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (valid && j < S) {
+                            const float ur = tu[j].x, ui = cj ? -tu[j].y : tu[j].y;
+                            st8(Bk + roff(lx + j), to_tf32(wr * ur - wi * ui),
+                                to_tf32(wr * ui + wi * ur));
+                        }
+                    }
+#pragma unroll
+                    for (int xq = 0; xq < 32; ++xq) {
+                        if (xq < lx || xq >= lx + S)
+                            st8(Bk + roff(xq), 0u, 0u);
+                    }
+                } else {
                 // this slot's taps and value
                 uint4 va[H][2][3];
                 float4 ut[3][4];
@@ -518,6 +609,7 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                         }
                     }
                 }
+                }
             }
             fence_proxy_async();
             __syncwarp();
@@ -541,7 +633,8 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
             // (shared addresses stay below 2^18, so the 14-bit field never
             // carries), the K steps are unrolled, and a partner that stopped
             // is noticed through the bounded wait itself.
-            constexpr uint32_t idesc = instr_desc(C::BF ? 1u : 0u, true, true, C::M, N);
+            constexpr uint32_t idesc = C::TF32 ? instr_desc(2u, false, false, C::M, N)
+                                               : instr_desc(C::BF ? 1u : 0u, true, true, C::M, N);
             const uint64_t da0 = smem_desc(smem_u32(Abuf), C::kLboA, kSboA);
             const uint64_t db0 = smem_desc(smem_u32(Bbuf), C::kLboB, C::kSboB);
             constexpr uint64_t kStepA = (2 * C::kLboA) >> 4, kStepB = (2 * C::kLboB) >> 4;
@@ -570,13 +663,19 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                     if (ctl.stall)
                         continue;  // test hook: issue and signal nothing
                     tc_fence_after();
-                    const int nk = (min(SV, left) + 7) >> 3;  // K = 16 steps in use
+                    // K steps in use (8 visibilities each, 4 for TF32)
+                    const int nk = (min(SV, left) + C::VPK - 1) / C::VPK;
                     const uint64_t da = da0 + kBufA * b, db = db0 + kBufB * b;
 #pragma unroll
-                    for (int kq = 0; kq < SV / 8; ++kq)
-                        if (kq < nk)
-                            mma_f16(d, da + kStepA * kq, db + kStepB * kq, idesc,
-                                    (st > 0 || kq > 0) ? 1u : 0u);
+                    for (int kq = 0; kq < SV / C::VPK; ++kq)
+                        if (kq < nk) {
+                            if constexpr (C::TF32)
+                                mma_tf32(d, da + kStepA * kq, db + kStepB * kq, idesc,
+                                         (st > 0 || kq > 0) ? 1u : 0u);
+                            else
+                                mma_f16(d, da + kStepA * kq, db + kStepB * kq, idesc,
+                                        (st > 0 || kq > 0) ? 1u : 0u);
+                        }
                     mma_commit(empty + b);
                 }
                 if (!ok)
@@ -689,12 +788,14 @@ cudaError_t launch_prec(const DevParams &p, const Plan &plan, const float2 *vis,
     uint4 *vtab = reinterpret_cast<uint4 *>(tables);
     float4 *utab = reinterpret_cast<float4 *>(vtab + nrow * 8 * C::H * 2 * 3);
     int32_t *item_exp = reinterpret_cast<int32_t *>(utab + nrow * 8 * 3 * 4);
-    const int64_t n = nrow * 8 * (C::H * 6 + 12);
-    const int nb = (int)std::min<int64_t>((n + 255) / 256, 4096);
-    tables_kernel<PREC><<<nb, 256, 0, s>>>(p, taps, vtab, utab);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
-        return e;
+    cudaError_t e;
+    if constexpr (!C::TF32) {  // TF32 reads the caller's taps directly
+        const int64_t n = nrow * 8 * (C::H * 6 + 12);
+        const int nb = (int)std::min<int64_t>((n + 255) / 256, 4096);
+        tables_kernel<PREC><<<nb, 256, 0, s>>>(p, taps, vtab, utab);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+    }
     if constexpr (C::SCALED) {
         item_scale_kernel<<<std::max(1, std::min(plan.items_capacity, 8 * num_sms)), 256, 0, s>>>(
             plan.d_items, plan.d_nitems, plan.d_perm, vis, weight, item_exp);
@@ -706,7 +807,7 @@ cudaError_t launch_prec(const DevParams &p, const Plan &plan, const float2 *vis,
     if (e != cudaSuccess)
         return e;
     grid_tc2_kernel<PREC><<<num_sms, C::kBlock, C::kSmem, s>>>(
-        p, plan.d_items, plan.d_nitems, plan.d_rec, plan.d_perm, vis, weight, vtab, utab,
+        p, plan.d_items, plan.d_nitems, plan.d_rec, plan.d_perm, vis, weight, vtab, utab, taps,
         item_exp, grid, status, ctl);
     return cudaGetLastError();
 }
@@ -738,6 +839,7 @@ cudaError_t launch_grid_tc2(const DevParams &p, const Plan &plan, const float2 *
     case 1: return launch_prec<1>(p, plan, vis, weight, taps, tables, grid, num_sms, status, ctl, s);
     case 2: return launch_prec<2>(p, plan, vis, weight, taps, tables, grid, num_sms, status, ctl, s);
     case 3: return launch_prec<3>(p, plan, vis, weight, taps, tables, grid, num_sms, status, ctl, s);
+    case 4: return launch_prec<4>(p, plan, vis, weight, taps, tables, grid, num_sms, status, ctl, s);
     default: return cudaErrorInvalidValue;
     }
 }

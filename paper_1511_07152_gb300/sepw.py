@@ -20,6 +20,7 @@ FORM_TC_BF16 = 2
 FORM_TC_FP16 = 3
 FORM_TC_FP16X2 = 4
 FORM_TC_BF16X2 = 5
+FORM_TC_TF32 = 6
 GRID_TO_IMAGE = 0
 IMAGE_TO_GRID = 1
 IMAGE_TO_GRID_ADJOINT = 2

@@ -1,11 +1,12 @@
 """Tensor-core contraction form (tcgen05) of the gridder against the FP64
 oracle.
 
-The operands are rounded to BF16 (unit roundoff u = 2^-8) or FP16 (u = 2^-11)
-and accumulated in FP32.  Every product W V F1(u) F1(v) then carries two
+The operands are rounded to BF16 (unit roundoff u = 2^-8), FP16 or TF32 (both
+11-bit significands, u = 2^-11; TF32 keeps the FP32 exponent range) and
+accumulated in FP32.  Every product W V F1(u) F1(v) then carries two
 independent operand roundings, relative rms sqrt(2/3) u, and the grid's
-relative L2 error is about that: 3.2e-3 (BF16) and 4.0e-4 (FP16).  The bars
-below allow a factor ~3: 1e-2 and 1.5e-3.
+relative L2 error is about that: 3.2e-3 (BF16) and 4.0e-4 (FP16, TF32).  The
+bars below allow a factor ~3: 1e-2 and 1.5e-3.
 
 The split forms represent each operand as hi + lo, hi = rn(x), lo = rn(x - hi),
 and take all four products of the splits, so only the rounding of lo is left:
@@ -15,7 +16,7 @@ near 1).  Uniform over that interval, the product's relative rms is 3.3e-6
 (BF16 hi + lo) and 1.9e-7 (FP16 hi + lo), measured on a million random
 operand pairs; both forms are held to the FP32 forms' bar, 1e-5.  Degridding
 in the BF16 and FP16 forms is the contraction form on tensor cores with the
-same bars; the hi + lo forms degrid with the tiled FP32 kernel (1e-5).
+same bars; the hi + lo and TF32 forms degrid with the tiled FP32 kernel.
 """
 import math
 
@@ -27,8 +28,8 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"bf16": 1e-2, "fp16": 1.5e-3, "fp16x2": 1e-5, "bf16x2": 1e-5}
-PRECS = ["bf16", "fp16", "fp16x2", "bf16x2"]
+TOL = {"bf16": 1e-2, "fp16": 1.5e-3, "fp16x2": 1e-5, "bf16x2": 1e-5, "tf32": 1.5e-3}
+PRECS = ["bf16", "fp16", "fp16x2", "bf16x2", "tf32"]
 
 
 @pytest.fixture(scope="module")
@@ -50,7 +51,7 @@ def rel_l2(a, b):
 
 def _form(S, name):
     return {"bf16": S.FORM_TC_BF16, "fp16": S.FORM_TC_FP16, "fp16x2": S.FORM_TC_FP16X2,
-            "bf16x2": S.FORM_TC_BF16X2}[name]
+            "bf16x2": S.FORM_TC_BF16X2, "tf32": S.FORM_TC_TF32}[name]
 
 
 def _grid(torch, S, wl, form, tile=0):
@@ -91,7 +92,7 @@ def test_tc_grid_parity(env, prec, name):
 
 
 @pytest.mark.parametrize("tile", [8, 12, 16])
-@pytest.mark.parametrize("prec", ["fp16", "bf16x2"])
+@pytest.mark.parametrize("prec", ["fp16", "bf16x2", "tf32"])
 def test_tc_tile_sizes(env, tile, prec):
     """Tiles up to the 32-cell window (T + S - 1 <= 32 at S = 16)."""
     torch, S = env
@@ -130,17 +131,17 @@ def test_tc_heavy_tile(env):
     # about 2^-24 sqrt(n / 2) = 9.4e-6 of the result, the floor of any form
     # that accumulates in FP32.  The hi + lo form's bar is three times that.
     floor = 3.0 * 2.0 ** -24 * math.sqrt(50000 / 2)
-    for prec in ("fp16", "fp16x2", "bf16x2"):
+    for prec in ("fp16", "fp16x2", "bf16x2", "tf32"):
         got, *_ = _grid(torch, S, wl, _form(S, prec))
         assert rel_l2(got, want) <= max(TOL[prec], floor), prec
 
 
 @pytest.mark.parametrize("amp", [1e-7, 1e6, 3e30])
-@pytest.mark.parametrize("prec", ["fp16", "fp16x2", "bf16x2"])
+@pytest.mark.parametrize("prec", ["fp16", "fp16x2", "bf16x2", "tf32"])
 def test_tc_fp16_amplitude_range(env, amp, prec):
     """Visibility amplitudes far outside FP16's range: the per-item
-    power-of-two scale keeps the FP16 operands representable, BF16 has the
-    FP32 exponent range, and the error bar is unchanged (the grid scales
+    power-of-two scale keeps the FP16 operands representable, BF16 and TF32
+    have the FP32 exponent range, and the error bar is unchanged (the grid scales
     with the amplitude)."""
     torch, S = env
     wl = CASES["rand_S16"]()
@@ -286,7 +287,7 @@ def test_tc_meerkat_subsample_errors(env):
         assert err <= TOL[prec], (prec, err)
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16x2"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16x2", "tf32"])
 def test_tc_wait_timeout_reported_and_recovered(env, prec):
     """The timeout path of the bounded waits: with the MMA thread stalled by
     the test hook and a 2 ms limit, the launch ends by itself with
@@ -313,7 +314,7 @@ def test_tc_wait_timeout_reported_and_recovered(env, prec):
     assert rel_l2(g.cpu().numpy(), want) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["bf16", "bf16x2"])
+@pytest.mark.parametrize("prec", ["bf16", "bf16x2", "tf32"])
 @pytest.mark.parametrize("chunk", [64, 544])
 def test_tc_schedule_item_sizes(env, prec, chunk):
     """Smaller work items (ragged 32-visibility stages, more items per CTA and
