@@ -7,21 +7,29 @@
 // side): with a_i[y] the v-taps of visibility i at its row offset and
 // b'_i[x] = W_i V_i times its u-taps at its column offset,
 //     G[y][x] = sum_i a_i[y] b'_i[x].
-// In real arithmetic, K = (visibility, re/im component), one tcgen05.mma of
-// shape M = 128, N = 32 H per K = 16 (8 visibilities):
-//     rows m = 64 h + 32 c + y      (h: split part of a, c: re/im of G, y: row)
-//     A[(h,0,y)][(i,0)] =  a_h,r   A[(h,0,y)][(i,1)] = -a_h,i
-//     A[(h,1,y)][(i,0)] =  a_h,i   A[(h,1,y)][(i,1)] =  a_h,r
-//     B[(i,0)][(g,x)] = b'_g,r     B[(i,1)][(g,x)] = b'_g,i
-// where a_h (b'_g) is the h-th (g-th) part of the 16-bit split of the taps
-// (of W V times the taps).  The one-part forms (H = 1) keep h = g = 0 and rows
-// 64..127 of A stay zero; the hi + lo forms (H = 2) put a_hi, a_lo in the two
-// row halves and b'_hi, b'_lo side by side in N, so one MMA yields all four
-// products of the splits, which the epilogue adds.
+// In real arithmetic the 16-bit forms take K = visibility and put the real
+// and imaginary parts of both factors in M and N, one tcgen05.mma of shape
+// M = 64 H, N = 64 H per K = 16 visibilities:
+//     rows    m = 64 h + 32 c + y    (h: split part of a, c: re/im of a, y: row)
+//     columns n = 64 g + 32 d + x    (g: split part of b', d: re/im of b', x)
+//     A[(h,c,y)][i] = a_h,c[y]       B[i][(g,d,x)] = b'_g,d[x]
+// so the accumulator holds the four real products summed over the
+// visibilities, D[(h,c,y)][(g,d,x)], and the epilogue forms
+//     Re G = sum_h,g D[(h,0,y)][(g,0,x)] - D[(h,1,y)][(g,1,x)]
+//     Im G = sum_h,g D[(h,0,y)][(g,1,x)] + D[(h,1,y)][(g,0,x)].
+// a_h (b'_g) is the h-th (g-th) part of the 16-bit split of the taps (of W V
+// times the taps): H = 1 for the one-part forms, H = 2 for the hi + lo forms,
+// where one MMA yields all four products of the splits.  The TF32 form keeps
+// K = (visibility, re/im) with M = 64 rows (c, y) and N = 32 columns x:
+//     A[(0,y)][(i,0)] = a_r   A[(0,y)][(i,1)] = -a_i
+//     A[(1,y)][(i,0)] = a_i   A[(1,y)][(i,1)] =  a_r
+//     B[(i,0)][x] = b'_r      B[(i,1)][x] = b'_i
+// (the accumulator is G itself), with K-major operands: MN-major TF32
+// operands gave zeros on the GB300.
 //
-// Both operands are MN-major: a visibility's column of A (and its row of B)
-// is contiguous along M (N) in 16-byte pieces of 8 values, so it is written as
-// whole 16-byte chunks.  The chunks come from tables built per call from the
+// The 16-bit operands are MN-major: a visibility's column of A (and its row
+// of B) is contiguous along M (N) in 16-byte pieces of 8 values, so it is
+// written as whole 16-byte chunks.  The chunks come from tables built per call from the
 // caller's complex64 taps:
 //   vtab: per (plane, oversample, shift s = row offset mod 8, part h,
 //         component): three chunks holding taps 8 j - s .. 8 j - s + 7
@@ -34,11 +42,11 @@
 // chunk rows its footprint misses get zeros, so each stage overwrites every
 // byte its visibilities own and no buffer ever needs clearing.
 //
-// One lane per visibility: a stage is 32 visibilities (K = 64), one warp.
-// Lanes hold visibilities with consecutive K indices; core matrices adjacent
-// along K are placed 16 bytes past a multiple of 128 (an odd number of
-// 16-byte slots), so the 8 lanes of a quarter warp store into 8 distinct
-// 16-byte bank groups: no conflicts, whatever chunk row each lane writes.
+// One lane per visibility: a stage is 32 visibilities, one warp.  Slot i is
+// K row i % 8 of core-matrix group i / 8, so the 8 lanes of a quarter warp
+// write the 8 rows of one aligned 128-byte core matrix: no bank conflicts,
+// whatever chunk row each lane writes, and no padding between the core
+// matrices the MMA reads.
 //
 // Roles (static round-robin assignment of the plan's work items to CTAs, so
 // every role walks the same sequence of items and stages):
@@ -49,8 +57,8 @@
 //     cannot tell those apart).  A lane loads its record one stage ahead,
 //     then its taps and value, waits for the buffer, writes its A column and
 //     B row and the warp arrives on the buffer's "full" mbarrier;
-//   - one MMA thread: per stage it waits for "full", issues the K = 16 MMAs
-//     and commits them to the buffer's "empty" mbarrier; per work item it
+//   - one MMA thread: per stage it waits for "full", issues the MMAs (two of
+//     K = 16 for the 16-bit forms) and commits them to the buffer's "empty" mbarrier; per work item it
 //     accumulates into one of two tensor-memory accumulators and commits
 //     "accf" after the item's last stage;
 //   - four epilogue warps (one per tensor-memory lane quarter): per item they
@@ -77,7 +85,6 @@ constexpr int kBufs = 8;                       // stage buffers = producer warps
 static_assert((kBufs & (kBufs - 1)) == 0, "the issue loop takes t mod kBufs as a mask");
 constexpr int kWin = 32;                       // window edge, T + S - 1 <= 32
 constexpr uint32_t kSboA = 128;                // M-adjacent core matrices
-constexpr int kStgStride = 33;                 // staging row (floats), padded
 constexpr int kEpiWarps = 4;
 
 // PREC: 0 = BF16, 1 = FP16 (scaled per item), 2 = FP16 hi + lo (scaled),
@@ -90,21 +97,28 @@ struct Cfg {
     // TF32: K-major operands of 4-byte elements (MN-major TF32 operands gave
     // zeros on the GB300), written from the caller's taps; K = 8 per MMA
     static constexpr bool TF32 = PREC == 4;
-    static constexpr int N = 32 * H;                       // MMA N: [b'_hi | b'_lo]
+    // N: columns (g, d, x), 64 H; TF32: x only
+    static constexpr int N = TF32 ? 32 : 64 * H;
     // M = 64 H rows: (h, c, y).  An M = 64 accumulator puts row m in tensor-
     // memory lane 32 (m / 16) + m % 16 (measured), the first 16 lanes of each
-    // warp quarter; the one-part forms then read and store no zero half of A.
+    // warp quarter.
     static constexpr int M = 64 * H;
     static constexpr int SV = 32;                          // visibilities per stage
     static constexpr int SLOTS = SV / 32;                  // per lane
-    // core matrices along K per stage: 8 (16-bit) or 4 (TF32) K elements each
-    static constexpr int KG = TF32 ? SV / 2 : SV / 4;
-    static constexpr int VPK = TF32 ? 4 : 8;               // visibilities per MMA
-    static constexpr uint32_t kLboA = (M / 8) * 128 + 16;  // K-adjacent, padded
+    // core matrices along K per stage: 8 visibilities each (16-bit forms), or
+    // 4 K elements = 2 visibilities (TF32)
+    static constexpr int KG = TF32 ? SV / 2 : SV / 8;
+    static constexpr int VPK = TF32 ? 4 : 16;              // visibilities per MMA
+    // K-adjacent core matrices: 128-byte aligned for the 16-bit forms; TF32
+    // pads by 16 bytes (its lanes store 8 bytes along K)
+    static constexpr uint32_t kPad = TF32 ? 16 : 0;
+    static constexpr uint32_t kLboA = (M / 8) * 128 + kPad;
     static constexpr int kABytes = KG * kLboA;
+    // staged accumulator row: (d, x) summed over g, or x (TF32); padded
+    static constexpr int kStgStride = TF32 ? 33 : 65;
     static constexpr int kStgBytes = M * kStgStride * 4;
     static constexpr uint32_t kSboB = 128;
-    static constexpr uint32_t kLboB = (N / 8) * 128 + 16;  // K-adjacent, padded
+    static constexpr uint32_t kLboB = (N / 8) * 128 + kPad;
     static constexpr int kBBytes = KG * kLboB;
     static constexpr int kProdWarps = kBufs;  // 13 warps: up to 128 registers each
     static constexpr int kMmaWarp = kProdWarps;
@@ -525,14 +539,11 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                     __syncwarp();
                     tc_fence_after();
                 }
-                // A: byte offsets of this slot's two K columns (chunk row 0);
-                // B likewise
-                const uint32_t a_off0 = ((2 * i) >> 3) * C::kLboA + ((2 * i) & 7) * 16;
-                const uint32_t a_off1 = ((2 * i + 1) >> 3) * C::kLboA + ((2 * i + 1) & 7) * 16;
-                const uint32_t b_off0 = ((2 * i) >> 3) * C::kLboB + ((2 * i) & 7) * 16;
-                const uint32_t b_off1 = ((2 * i + 1) >> 3) * C::kLboB + ((2 * i + 1) & 7) * 16;
+                // byte offsets of this slot's K row in A and B (chunk row 0)
+                const uint32_t a_off = (i >> 3) * C::kLboA + (i & 7) * 16;
+                const uint32_t b_off = (i >> 3) * C::kLboB + (i & 7) * 16;
                 // A: chunk j of part h goes to chunk row j + ly / 8 of the
-                // (h, re rows) and (h, im rows) quarters of the two columns
+                // (h, re) and (h, im) row blocks
                 const int oy8 = valid ? (ly >> 3) : 8;
 #pragma unroll
                 for (int h = 0; h < H; ++h) {
@@ -540,28 +551,22 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                     for (int j = 0; j < 3; ++j) {
                         const int xq = j + oy8;
                         if (xq < 4) {
-                            const uint4 R = va[h][0][j];
-                            const uint4 I = xor4(va[h][1][j], cjm);  // conj(a) for w < 0
-                            const uint32_t g0 = (h * 8 + xq) * kSboA, g1 = g0 + 4 * kSboA;
-                            st16(A + a_off0 + g0, R);
-                            st16(A + a_off0 + g1, I);
-                            st16(A + a_off1 + g0, xor4(I, 0x80008000u));
-                            st16(A + a_off1 + g1, R);
+                            const uint32_t g0 = (h * 8 + xq) * kSboA;
+                            st16(A + a_off + g0, va[h][0][j]);
+                            st16(A + a_off + g0 + 4 * kSboA, xor4(va[h][1][j], cjm));  // conj(a), w < 0
                         }
                     }
 #pragma unroll
                     for (int xq = 0; xq < 4; ++xq) {
                         if (xq < oy8 || xq > oy8 + 2) {
-                            const uint32_t g0 = (h * 8 + xq) * kSboA, g1 = g0 + 4 * kSboA;
-                            st16(A + a_off0 + g0, z);
-                            st16(A + a_off0 + g1, z);
-                            st16(A + a_off1 + g0, z);
-                            st16(A + a_off1 + g1, z);
+                            const uint32_t g0 = (h * 8 + xq) * kSboA;
+                            st16(A + a_off + g0, z);
+                            st16(A + a_off + g0 + 4 * kSboA, z);
                         }
                     }
                 }
-                // B: W V times the u-taps, chunk j to chunk row j + lx / 8 (and
-                // 4 + that for the lo part)
+                // B: W V times the u-taps, chunk j to chunk row j + lx / 8 of the
+                // (g, re) and (g, im) column blocks
                 const int ox8 = valid ? (lx >> 3) : 8;
                 const float wr = (wt * x.x) * scale;  // exact power-of-two scaling
                 const float wi = (wt * x.y) * scale;
@@ -592,9 +597,9 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                             pi.y = pack_part<C::BF>(im[2], im[3], g);
                             pi.z = pack_part<C::BF>(im[4], im[5], g);
                             pi.w = pack_part<C::BF>(im[6], im[7], g);
-                            const uint32_t gb = (g * 4 + xq) * C::kSboB;
-                            st16(B + b_off0 + gb, pr);
-                            st16(B + b_off1 + gb, pi);
+                            const uint32_t gb = (g * 8 + xq) * C::kSboB;
+                            st16(B + b_off + gb, pr);
+                            st16(B + b_off + gb + 4 * C::kSboB, pi);
                         }
                     }
                 }
@@ -603,9 +608,9 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                     if (xq < ox8 || xq > ox8 + 2) {
 #pragma unroll
                         for (int g = 0; g < H; ++g) {
-                            const uint32_t gb = (g * 4 + xq) * C::kSboB;
-                            st16(B + b_off0 + gb, z);
-                            st16(B + b_off1 + gb, z);
+                            const uint32_t gb = (g * 8 + xq) * C::kSboB;
+                            st16(B + b_off + gb, z);
+                            st16(B + b_off + gb + 4 * C::kSboB, z);
                         }
                     }
                 }
@@ -663,7 +668,7 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                     if (ctl.stall)
                         continue;  // test hook: issue and signal nothing
                     tc_fence_after();
-                    // K steps in use (8 visibilities each, 4 for TF32)
+                    // K steps in use (16 visibilities each, 4 for TF32)
                     const int nk = (min(SV, left) + C::VPK - 1) / C::VPK;
                     const uint64_t da = da0 + kBufA * b, db = db0 + kBufB * b;
 #pragma unroll
@@ -700,7 +705,9 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
         // accumulator row held by this lane: M = 128, row 32 qq + lane; M = 64,
         // row 16 qq + lane for lanes below 16 (the other lanes hold nothing)
         const bool holds = C::M == 128 || lane < 16;
-        float *const row = stg + (C::M == 128 ? 32 * qq + lane : 16 * qq + (lane & 15)) * kStgStride;
+        float *const row =
+            stg + (C::M == 128 ? 32 * qq + lane : 16 * qq + (lane & 15)) * C::kStgStride;
+        constexpr int NC = C::TF32 ? 32 : 64;  // staged columns: x, or (d, x)
         Cursor cur;
         int ne = 0;
         while (cursor_next<SV>(cur, items, n_items)) {
@@ -724,19 +731,23 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
             }
             tc_fence_after();
             const uint32_t ta = tmem + ((uint32_t)(32 * qq) << 16) + (uint32_t)(ab * N);
-            uint32_t rr[32];
-            SEPW_TMEM_LD32(ta, rr);
-            tmem_wait_ld();
-            float v[32];
+            // this row's columns (d, x), summed over the split part g of b'
+            float v[NC];
 #pragma unroll
-            for (int xx = 0; xx < 32; ++xx)
-                v[xx] = __uint_as_float(rr[xx]);
-            if constexpr (H == 2) {
-                SEPW_TMEM_LD32(ta + 32, rr);  // the b'_lo columns
+            for (int d = 0; d < NC / 32; ++d) {
+                uint32_t rr[32];
+                SEPW_TMEM_LD32(ta + 32 * d, rr);
                 tmem_wait_ld();
 #pragma unroll
                 for (int xx = 0; xx < 32; ++xx)
-                    v[xx] += __uint_as_float(rr[xx]);
+                    v[32 * d + xx] = __uint_as_float(rr[xx]);
+                if constexpr (H == 2) {
+                    SEPW_TMEM_LD32(ta + 64 + 32 * d, rr);  // the b'_lo columns
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int xx = 0; xx < 32; ++xx)
+                        v[32 * d + xx] += __uint_as_float(rr[xx]);
+                }
             }
             tc_fence_before();
             __syncwarp();
@@ -747,7 +758,7 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                 back = ldexpf(1.0f, __ldg(item_exp + cur.item));
             if (holds) {
 #pragma unroll
-                for (int xx = 0; xx < 32; ++xx)
+                for (int xx = 0; xx < NC; ++xx)
                     row[xx] = v[xx] * back;
             }
             asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
@@ -757,10 +768,21 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                 const int y = e >> 5, xx = e & 31;
                 if (y >= W || xx >= W)
                     continue;
-                float re = stg[y * kStgStride + xx], im = stg[(32 + y) * kStgStride + xx];
-                if constexpr (H == 2) {
-                    re += stg[(64 + y) * kStgStride + xx];
-                    im += stg[(96 + y) * kStgStride + xx];
+                float re, im;
+                if constexpr (C::TF32) {  // rows (c, y) of G itself
+                    re = stg[y * C::kStgStride + xx];
+                    im = stg[(32 + y) * C::kStgStride + xx];
+                } else {
+                    // rows (h, c, y), columns (d, x): Re = rr - ii, Im = ri + ir
+                    re = 0.f;
+                    im = 0.f;
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        const float *r0 = stg + (64 * h + y) * C::kStgStride;
+                        const float *r1 = r0 + 32 * C::kStgStride;
+                        re += r0[xx] - r1[32 + xx];
+                        im += r0[32 + xx] + r1[xx];
+                    }
                 }
                 if (re != 0.f || im != 0.f)
                     atomicAdd(grid + o.base + (o.gy0 + y) * p.N + o.gx0 + xx, make_float2(re, im));
