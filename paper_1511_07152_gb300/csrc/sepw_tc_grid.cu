@@ -42,25 +42,29 @@
 // chunk rows its footprint misses get zeros, so each stage overwrites every
 // byte its visibilities own and no buffer ever needs clearing.
 //
-// One lane per visibility: a stage is 32 visibilities, one warp.  Slot i is
-// K row i % 8 of core-matrix group i / 8, so the 8 lanes of a quarter warp
-// write the 8 rows of one aligned 128-byte core matrix: no bank conflicts,
-// whatever chunk row each lane writes, and no padding between the core
-// matrices the MMA reads.
+// One lane per visibility: a stage is 64 visibilities, written by a pair of
+// producer warps (32 each).  Slot i is K row i % 8 of core-matrix group i / 8,
+// so the 8 lanes of a quarter warp write the 8 rows of one aligned 128-byte
+// core matrix: no bank conflicts, whatever chunk row each lane writes, and no
+// padding between the core matrices the MMA reads.
 //
 // Roles (static round-robin assignment of the plan's work items to CTAs, so
 // every role walks the same sequence of items and stages):
-//   - eight producer warps, each owning one of eight stage buffers: warp w
-//     takes the CTA's stages w, w + 8, ...  Owning its buffer, a producer
-//     has itself filled the buffer's previous stage, so its wait for that
-//     stage's MMAs can never be two mbarrier phases ahead (a parity wait
-//     cannot tell those apart).  A lane loads its record one stage ahead,
-//     then its taps and value, waits for the buffer, writes its A column and
-//     B row and the warp arrives on the buffer's "full" mbarrier;
-//   - one MMA thread: per stage it waits for "full", issues the MMAs (two of
-//     K = 16 for the 16-bit forms) and commits them to the buffer's "empty" mbarrier; per work item it
-//     accumulates into one of two tensor-memory accumulators and commits
-//     "accf" after the item's last stage;
+//   - eight producer warps in four pairs, each pair owning one of four stage
+//     buffers: pair p takes the CTA's stages p, p + 4, ...  Owning its
+//     buffer, a warp has itself filled the buffer's previous stage, so its
+//     wait for that stage's MMAs can never be two mbarrier phases ahead (a
+//     parity wait cannot tell those apart): the buffer's "empty" barrier
+//     cannot complete this round before the warp's own half of the round's
+//     stage has arrived.  A lane loads its record one stage ahead, then its
+//     taps and value, waits for the buffer, writes its A column and B row,
+//     and the warp arrives on the buffer's "full" mbarrier (two arrivals);
+//   - one MMA thread: per stage it waits for "full", issues the MMAs (four of
+//     K = 16 for the 16-bit forms) and commits them to the buffer's "empty"
+//     mbarrier.  Per work item it accumulates into one of two tensor-memory
+//     accumulators and commits "accf" after the item's last stage.  This
+//     thread's per-stage chain (wait, issue, commit: about 550 cycles for
+//     32-visibility stages, measured) is what stages of 64 halve;
 //   - four epilogue warps (one per tensor-memory lane quarter): per item they
 //     read the accumulator, release it ("accfree"), stage it in shared memory
 //     and add the window to the HBM grid with float2 atomics (windows of
@@ -81,8 +85,15 @@ namespace {
 
 using namespace tcx;
 
-constexpr int kBufs = 8;                       // stage buffers = producer warps
+constexpr int kProd = 8;                       // producer warps
+constexpr int kWps = 2;                        // producer warps per stage
+constexpr int kBufs = kProd / kWps;            // stage buffers, one per warp pair
 static_assert((kBufs & (kBufs - 1)) == 0, "the issue loop takes t mod kBufs as a mask");
+// Buffers may be released in groups of kGroup consecutive buffers (one
+// tcgen05.commit per group); each group's "empty" barrier still completes
+// once per round of kBufs stages.  Measured: groups gave nothing.
+constexpr int kGroup = 1;
+static_assert(kBufs % kGroup == 0, "groups tile the buffers");
 constexpr int kWin = 32;                       // window edge, T + S - 1 <= 32
 constexpr uint32_t kSboA = 128;                // M-adjacent core matrices
 constexpr int kEpiWarps = 4;
@@ -103,12 +114,15 @@ struct Cfg {
     // memory lane 32 (m / 16) + m % 16 (measured), the first 16 lanes of each
     // warp quarter.
     static constexpr int M = 64 * H;
-    static constexpr int SV = 32;                          // visibilities per stage
-    static constexpr int SLOTS = SV / 32;                  // per lane
+    static constexpr int SV = 32 * kWps;                   // visibilities per stage
+    static constexpr int SLOTS = 1;                        // per lane
     // core matrices along K per stage: 8 visibilities each (16-bit forms), or
     // 4 K elements = 2 visibilities (TF32)
     static constexpr int KG = TF32 ? SV / 2 : SV / 8;
     static constexpr int VPK = TF32 ? 4 : 16;              // visibilities per MMA
+    // values and weights loaded one stage ahead (the one-part 16-bit forms;
+    // the others have no registers to spare: measured slower)
+    static constexpr bool PRE = H == 1 && !TF32;
     // K-adjacent core matrices: 128-byte aligned for the 16-bit forms; TF32
     // pads by 16 bytes (its lanes store 8 bytes along K)
     static constexpr uint32_t kPad = TF32 ? 16 : 0;
@@ -120,7 +134,7 @@ struct Cfg {
     static constexpr uint32_t kSboB = 128;
     static constexpr uint32_t kLboB = (N / 8) * 128 + kPad;
     static constexpr int kBBytes = KG * kLboB;
-    static constexpr int kProdWarps = kBufs;  // 13 warps: up to 128 registers each
+    static constexpr int kProdWarps = kProd;  // 13 warps: up to 128 registers each
     static constexpr int kMmaWarp = kProdWarps;
     static constexpr int kEpiWarp0 = kProdWarps + 1;
     static constexpr int kBlock = 32 * (kProdWarps + 1 + kEpiWarps);
@@ -355,7 +369,7 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
         reinterpret_cast<uint4 *>(Abuf)[e] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         for (int b = 0; b < kBufs; ++b) {
-            mbar_init(full + b, 1);
+            mbar_init(full + b, kWps);
             mbar_init(empty + b, 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -377,16 +391,20 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
     if (warp < C::kProdWarps) {
         // ------------------------------------------------------------ producers
         Cursor cur;
-        int t = warp;
+        int t = warp / kWps;                // the pair's first stage
+        const int slot0 = 32 * (warp % kWps);  // this warp's half of a stage
         bool ok = cursor_next<SV>(cur, items, n_items) && cursor_seek<SV>(cur, t, items, n_items);
-        // records and visibility indices of the lane's slots, one stage ahead
+        // records and visibility indices of the lane's slots one stage ahead,
+        // and with C::PRE their values and weights (random gathers from HBM)
         uint64_t r[C::SLOTS];
         int vi[C::SLOTS];
+        float2 xv[C::SLOTS];
+        float wv[C::SLOTS];
         auto fetch = [&](const Cursor &c, int t_, uint64_t (&r_)[C::SLOTS],
-                         int (&vi_)[C::SLOTS]) {
+                         int (&vi_)[C::SLOTS], float2 (&x_)[C::SLOTS], float (&w_)[C::SLOTS]) {
 #pragma unroll
             for (int sl = 0; sl < C::SLOTS; ++sl) {
-                const int e = (t_ - c.tb) * SV + 32 * sl + lane;
+                const int e = (t_ - c.tb) * SV + slot0 + 32 * sl + lane;
                 vi_[sl] = -1;
                 if (e < c.count) {
                     r_[sl] = __ldg(reinterpret_cast<const unsigned long long *>(rec) + c.start +
@@ -394,18 +412,32 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                     vi_[sl] = __ldg(perm + c.start + e);
                 }
             }
+#pragma unroll
+            for (int sl = 0; sl < C::SLOTS; ++sl) {
+                x_[sl] = make_float2(0.f, 0.f);
+                w_[sl] = 0.f;
+                if (C::PRE && vi_[sl] >= 0) {
+                    x_[sl] = __ldg(vis + vi_[sl]);
+                    w_[sl] = weight ? __ldg(weight + vi_[sl]) : 1.0f;
+                }
+            }
         };
         if (ok)
-            fetch(cur, t, r, vi);
+            fetch(cur, t, r, vi, xv, wv);
         while (ok && !s_abort) {
             Cursor cn = cur;
             const int tn = t + kBufs;
             bool okn = false;
             uint64_t rn[C::SLOTS];
             int vin[C::SLOTS];
+            float2 xn[C::SLOTS];
+            float wn[C::SLOTS];
 #pragma unroll
-            for (int sl = 0; sl < C::SLOTS; ++sl)
+            for (int sl = 0; sl < C::SLOTS; ++sl) {
                 vin[sl] = -1;
+                xn[sl] = make_float2(0.f, 0.f);
+                wn[sl] = 0.f;
+            }
             float scale = 1.0f;
             if constexpr (C::SCALED)
                 scale = ldexpf(1.0f, -__ldg(item_exp + cur.item));
@@ -415,7 +447,7 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
             const uint4 z = make_uint4(0, 0, 0, 0);
 #pragma unroll
             for (int sl = 0; sl < C::SLOTS; ++sl) {
-                const int i = 32 * sl + lane;  // slot in the stage
+                const int i = slot0 + 32 * sl + lane;  // slot in the stage
                 if constexpr (C::TF32) {
                     // K-major, 4-byte elements: slot i's two K elements (re, im
                     // components) are 8 adjacent bytes of every row
@@ -443,11 +475,11 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                     if (sl == 0) {
                         okn = cursor_seek<SV>(cn, tn, items, n_items);
                         if (okn)
-                            fetch(cn, tn, rn, vin);
+                            fetch(cn, tn, rn, vin, xn, wn);
                     }
                     if (sl == 0 && t >= kBufs) {
                         if (lane == 0 && !s_abort &&
-                            !mbar_wait(empty + b, ((t / kBufs) - 1) & 1, ctl.wait_ns))
+                            !mbar_wait(empty + b / kGroup, ((t / kBufs) - 1) & 1, ctl.wait_ns))
                             s_abort = 1;
                         __syncwarp();
                         tc_fence_after();
@@ -497,8 +529,13 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                 uint32_t cjm = 0;
                 const bool valid = vi[sl] >= 0;
                 if (valid) {
-                    x = __ldg(vis + vi[sl]);
-                    wt = weight ? __ldg(weight + vi[sl]) : 1.0f;
+                    if constexpr (C::PRE) {
+                        x = xv[sl];
+                        wt = wv[sl];
+                    } else {
+                        x = __ldg(vis + vi[sl]);
+                        wt = weight ? __ldg(weight + vi[sl]) : 1.0f;
+                    }
                     lx = rec_lx(r[sl]);
                     ly = rec_ly(r[sl]);
                     cjm = rec_conj(r[sl]) ? 0x80008000u : 0u;
@@ -526,15 +563,15 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                         }
                 }
                 if (sl == 0) {
-                    // the next stage of this warp: its records and indices now
+                    // the pair's next stage: its records and indices now
                     okn = cursor_seek<SV>(cn, tn, items, n_items);
                     if (okn)
-                        fetch(cn, tn, rn, vin);
+                        fetch(cn, tn, rn, vin, xn, wn);
                 }
                 if (sl == 0 && t >= kBufs) {
                     // buffer b held stage t - kBufs: wait (lane 0) for its MMAs
                     if (lane == 0 && !s_abort &&
-                        !mbar_wait(empty + b, ((t / kBufs) - 1) & 1, ctl.wait_ns))
+                        !mbar_wait(empty + b / kGroup, ((t / kBufs) - 1) & 1, ctl.wait_ns))
                         s_abort = 1;
                     __syncwarp();
                     tc_fence_after();
@@ -627,6 +664,8 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
             for (int sl = 0; sl < C::SLOTS; ++sl) {
                 r[sl] = rn[sl];
                 vi[sl] = vin[sl];
+                xv[sl] = xn[sl];
+                wv[sl] = wn[sl];
             }
         }
     } else if (warp == C::kMmaWarp) {
@@ -681,7 +720,11 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                                 mma_f16(d, da + kStepA * kq, db + kStepB * kq, idesc,
                                         (st > 0 || kq > 0) ? 1u : 0u);
                         }
-                    mma_commit(empty + b);
+                    // release the group once its last buffer is issued (a group
+                    // cut short by the end of the CTA's stages has no later
+                    // user, and the item's "accf" commit covers its MMAs)
+                    if ((b % kGroup) == kGroup - 1)
+                        mma_commit(empty + b / kGroup);
                 }
                 if (!ok)
                     break;
