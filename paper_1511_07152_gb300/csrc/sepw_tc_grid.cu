@@ -34,9 +34,10 @@
 //   vtab: per (plane, oversample, shift s = row offset mod 8, part h,
 //         component): three chunks holding taps 8 j - s .. 8 j - s + 7
 //         (zero outside 0 .. S-1), rounded to the 16-bit format;
-//   utab: per (plane, oversample, shift, chunk j): the same eight complex64
-//         taps of the u side, which is multiplied by W V in FP32 before
-//         rounding.
+//   utab: per (plane, oversample, shift, chunk j): the same eight taps of
+//         the u side, complex64 for the hi + lo forms and (re, im) pairs in
+//         the 16-bit format for the one-part forms, multiplied by W V in FP32
+//         before rounding.
 // Chunk j of a visibility whose footprint starts at row ly goes to chunk row
 // j + ly / 8 of its column: the placement is a computed store address, and the
 // chunk rows its footprint misses get zeros, so each stage overwrites every
@@ -123,6 +124,9 @@ struct Cfg {
     // values and weights loaded one stage ahead (the one-part 16-bit forms;
     // the others have no registers to spare: measured slower)
     static constexpr bool PRE = H == 1 && !TF32;
+    // u-side table in the 16-bit format (the one-part forms: W V times the
+    // rounded taps, rounded again); FP32 for the hi + lo forms
+    static constexpr bool U16 = H == 1 && !TF32;
     // K-adjacent core matrices: 128-byte aligned for the 16-bit forms; TF32
     // pads by 16 bytes (its lanes store 8 bytes along K)
     static constexpr uint32_t kPad = TF32 ? 16 : 0;
@@ -162,6 +166,17 @@ __device__ __forceinline__ uint32_t pack_part(float x, float y, int h)
             hi = __floats2half2_rn(x - f.x, y - f.y);
         }
         return *reinterpret_cast<uint32_t *>(&hi);
+    }
+}
+
+// (x, y) of a pair of 16-bit values (exact)
+template <bool BF>
+__device__ __forceinline__ float2 unpack_part(uint32_t w)
+{
+    if constexpr (BF) {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    } else {
+        return __half22float2(*reinterpret_cast<const __half2 *>(&w));
     }
 }
 
@@ -207,9 +222,10 @@ __global__ void tables_kernel(DevParams p, const float2 *__restrict__ taps, uint
                               float4 *utab)
 {
     constexpr int H = Cfg<PREC>::H;
+    constexpr bool U16 = Cfg<PREC>::U16;
     const int64_t nrow = (int64_t)p.P * p.OS;
     const int64_t nv = nrow * 8 * H * 2 * 3;
-    const int64_t nu = nrow * 8 * 3 * 4;
+    const int64_t nu = nrow * 8 * 3 * (U16 ? 2 : 4);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv + nu; e += stride) {
         if (e < nv) {
@@ -235,6 +251,24 @@ __global__ void tables_kernel(DevParams p, const float2 *__restrict__ taps, uint
                 w[t2] = pack_part<Cfg<PREC>::BF>(v[0], v[1], h);
             }
             vtab[e] = make_uint4(w[0], w[1], w[2], w[3]);
+        } else if constexpr (U16) {
+            // 16 bytes: taps 4 f .. 4 f + 3 of chunk j, (re, im) 16-bit pairs
+            int64_t q = e - nv;
+            const int f = (int)(q % 2);
+            q /= 2;
+            const int j = (int)(q % 3);
+            q /= 3;
+            const int s = (int)(q % 8);
+            q /= 8;
+            const float2 *row = taps + q * p.S;
+            uint32_t w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = 8 * j - s + 4 * f + u;
+                const float2 t = (k >= 0 && k < p.S) ? row[k] : make_float2(0.f, 0.f);
+                w[u] = pack_part<Cfg<PREC>::BF>(t.x, t.y, 0);
+            }
+            reinterpret_cast<uint4 *>(utab)[e - nv] = make_uint4(w[0], w[1], w[2], w[3]);
         } else {
             int64_t q = e - nv;
             const int f = (int)(q % 4);
@@ -522,7 +556,8 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                 } else {
                 // this slot's taps and value
                 uint4 va[H][2][3];
-                float4 ut[3][4];
+                float4 ut[3][4];  // FP32 u-taps (hi + lo forms)
+                uint4 uh[3][2];   // 16-bit u-taps (one-part forms): 8 (re, im) words a chunk
                 float2 x = make_float2(0.f, 0.f);
                 float wt = 0.f;
                 int lx = 0, ly = 0;
@@ -541,7 +576,7 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                     cjm = rec_conj(r[sl]) ? 0x80008000u : 0u;
                     const int64_t row = (int64_t)rec_plane(r[sl]) * p.OS;
                     const uint4 *pa = vtab + ((row + rec_ov(r[sl])) * 8 + (ly & 7)) * (H * 6);
-                    const float4 *pu = utab + ((row + rec_ou(r[sl])) * 8 + (lx & 7)) * 12;
+                    const int64_t urow = (row + rec_ou(r[sl])) * 8 + (lx & 7);
                     // the row's 6 H chunks ([h][component][j]) in 32-byte loads
 #pragma unroll
                     for (int h = 0; h < H; ++h) {
@@ -549,18 +584,26 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                         ldg32(pa + h * 6 + 2, va[h][0][2], va[h][1][0]);
                         ldg32(pa + h * 6 + 4, va[h][1][1], va[h][1][2]);
                     }
+                    if constexpr (C::U16) {
+                        const uint4 *pu = reinterpret_cast<const uint4 *>(utab) + urow * 6;
 #pragma unroll
-                    for (int j = 0; j < 3; ++j)
+                        for (int j = 0; j < 3; ++j)
+                            ldg32(pu + 2 * j, uh[j][0], uh[j][1]);
+                    } else {
+                        const float4 *pu = utab + urow * 12;
 #pragma unroll
-                        for (int f = 0; f < 4; f += 2) {
-                            uint4 a, bb;
-                            ldg32(pu + j * 4 + f, a, bb);
-                            ut[j][f] = make_float4(__uint_as_float(a.x), __uint_as_float(a.y),
-                                                   __uint_as_float(a.z), __uint_as_float(a.w));
-                            ut[j][f + 1] =
-                                make_float4(__uint_as_float(bb.x), __uint_as_float(bb.y),
-                                            __uint_as_float(bb.z), __uint_as_float(bb.w));
-                        }
+                        for (int j = 0; j < 3; ++j)
+#pragma unroll
+                            for (int f = 0; f < 4; f += 2) {
+                                uint4 a, bb;
+                                ldg32(pu + j * 4 + f, a, bb);
+                                ut[j][f] = make_float4(__uint_as_float(a.x), __uint_as_float(a.y),
+                                                       __uint_as_float(a.z), __uint_as_float(a.w));
+                                ut[j][f + 1] =
+                                    make_float4(__uint_as_float(bb.x), __uint_as_float(bb.y),
+                                                __uint_as_float(bb.z), __uint_as_float(bb.w));
+                            }
+                    }
                 }
                 if (sl == 0) {
                     // the pair's next stage: its records and indices now
@@ -616,7 +659,15 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                         float re[8], im[8];
 #pragma unroll
                         for (int f = 0; f < 4; ++f) {
-                            const float4 u = ut[j][f];
+                            float4 u;
+                            if constexpr (C::U16) {
+                                const uint4 q = uh[j][f >> 1];
+                                const float2 t0 = unpack_part<C::BF>((f & 1) ? q.z : q.x);
+                                const float2 t1 = unpack_part<C::BF>((f & 1) ? q.w : q.y);
+                                u = make_float4(t0.x, t0.y, t1.x, t1.y);
+                            } else {
+                                u = ut[j][f];
+                            }
                             // (wr + i wi)(tr + i s ti), s = -1 for w < 0
                             re[2 * f] = wr * u.x - wis * u.y;
                             im[2 * f] = wrs * u.y + wi * u.x;
