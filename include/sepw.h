@@ -63,6 +63,8 @@ extern "C" {
 #define SEPW_ENOTSUP (-5)  /* form not available for these parameters */
 #define SEPW_ENOPLAN (-6)  /* *_planned call without a current plan */
 #define SEPW_ETOOLARGE (-7) /* sepw_grid_noalloc: beyond its fixed scratch */
+#define SEPW_EBOUNDS (-8)   /* bounds-checked build: a kernel found a work item,
+                               plan record or index out of range and skipped it */
 
 /* kernel forms (sepw_params.form) */
 #define SEPW_FORM_PLAIN 0  /* plain FP32: one global atomic per cell update */
@@ -263,6 +265,40 @@ SEPW_API int sepw_set_wait_limit(sepw_ctx *ctx, uint64_t limit_ns);
  * effect at the next sepw_plan (the current plan is invalidated); results
  * do not depend on it beyond FP32 rounding order.  Host only. */
 SEPW_API int sepw_set_schedule(sepw_ctx *ctx, int32_t chunk, int32_t grid_parts);
+
+/* FP32 FMA rate probe (no counterpart in the paper): the scatter-form
+ * kernels are bound by FP32 fused multiply-adds, and their roofline is stated
+ * against the FMA peak derived from unit counts and the clock.  This launches,
+ * on `stream`, one kernel that does only FMAs: 4 CTAs of 256 threads per SM,
+ * each thread running 8 independent chains of `iters` (1 .. 2^30) FMAs,
+ * scalar FFMA (paired = 0) or paired FFMA2 on float2 operands (paired != 0).
+ * `out` is a device buffer of at least out_len >= SMs x 1024 floats that
+ * receives one per-thread sum (it keeps the chains live); *flops (host)
+ * receives the flop count of the launch (2 per FMA).  The caller times the
+ * launch with CUDA events on the stream.  Returns SEPW_EINVAL for bad
+ * arguments or a short buffer, SEPW_ECUDA if the launch fails. */
+SEPW_API int sepw_fma_probe(int paired, int64_t iters, float *out, int64_t out_len,
+                            int64_t *flops, sepw_stream_t stream);
+
+/* Bounds-checked build (no counterpart in the paper).  libsepw_checked.so is
+ * the same library compiled with SEPW_CHECKED=1: the tiled (scatter-form)
+ * gridder and degridder check every work item (tile, visibility range) and
+ * every plan record (visibility index, plane, oversample indices, footprint
+ * inside the tile and the grid) before use; a failed check records
+ * SEPW_EBOUNDS in the context's device status word (sepw_device_status) and
+ * the kernel skips that item or visibility instead of accessing out of
+ * range.  sepw_checked_build returns 1 in that build, 0 in the default one,
+ * which compiles the checks away. */
+SEPW_API int sepw_checked_build(void);
+
+/* Test hook of the checked build (no counterpart in the paper): overwrites,
+ * in the current plan of ctx, the slot -> visibility index of `slot`
+ * (which = 0) or the plane field of the slot's record (which = 1) with
+ * `value`, so that a test can see the checks catch it.  Synchronous.  Returns
+ * SEPW_ENOTSUP in the default build (nothing there guards such a value),
+ * SEPW_ENOPLAN without a tiled plan, SEPW_EINVAL for a slot outside the plan
+ * or another `which`. */
+SEPW_API int sepw_test_corrupt_plan(sepw_ctx *ctx, int which, int64_t slot, int32_t value);
 
 /* Test hook for the timeout path (no counterpart in the paper): with enable
  * != 0 the tensor-core kernels of this context issue no matrix operations and

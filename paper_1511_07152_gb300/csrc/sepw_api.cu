@@ -9,10 +9,24 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sepw_internal.cuh"
 #include "sepw_tc_ptx.cuh"
 
 using namespace sepw;
+
+namespace {
+// NVTX range over one entry point (host side: it brackets the launches the
+// call enqueues).  The header-only NVTX library does nothing unless a
+// profiler is attached.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+}  // namespace
 
 struct sepw_ctx {
     sepw_params p;
@@ -245,6 +259,7 @@ const char *sepw_strerror(int status)
     case SEPW_ENOTSUP: return "not supported for these parameters";
     case SEPW_ENOPLAN: return "no current plan";
     case SEPW_ETOOLARGE: return "size exceeds the fixed scratch of sepw_grid_noalloc";
+    case SEPW_EBOUNDS: return "a bounds check of the checked build failed";
     default: return "unknown status";
     }
 }
@@ -370,6 +385,7 @@ const char *sepw_last_error(const sepw_ctx *ctx) { return ctx ? ctx->err : "no c
 
 int sepw_make_taps(sepw_ctx *ctx, float *taps, sepw_stream_t stream)
 {
+    Range range_("sepw_make_taps");
     if (!ctx)
         return SEPW_EINVAL;
     int rc = check_dev(ctx, taps, "taps", false);
@@ -396,6 +412,7 @@ int sepw_locate(sepw_ctx *ctx, int64_t nvis, const double *u, const double *v,
                 const double *w, int32_t *cu, int32_t *cv, int32_t *ou, int32_t *ov,
                 int32_t *plane, uint8_t *conj, uint8_t *keep, sepw_stream_t stream)
 {
+    Range range_("sepw_locate");
     if (!ctx)
         return SEPW_EINVAL;
     if (nvis < 0)
@@ -414,6 +431,7 @@ int sepw_locate(sepw_ctx *ctx, int64_t nvis, const double *u, const double *v,
 static int plan_impl(sepw_ctx *ctx, int32_t ngrids, const int64_t *offsets_host, int64_t nvis,
                      const double *u, const double *v, const double *w, cudaStream_t s)
 {
+    Range range_("sepw_plan");
     ctx->plan.valid = false;
     if (nvis < 0 || nvis > (int64_t)INT32_MAX - 1)
         return fail(ctx, SEPW_EINVAL, "nvis out of range [0, 2^31 - 2]");
@@ -511,6 +529,7 @@ int sepw_plan_dropped(sepw_ctx *ctx, int64_t *n_dropped_host, sepw_stream_t stre
 int sepw_grid_planned(sepw_ctx *ctx, const float *taps, const float *vis,
                       const float *weight, float *grid, sepw_stream_t stream)
 {
+    Range range_("sepw_grid");
     if (!ctx)
         return SEPW_EINVAL;
     if (!ctx->plan.valid)
@@ -546,7 +565,9 @@ int sepw_grid_planned(sepw_ctx *ctx, const float *taps, const float *vis,
     } else {
         if (((uintptr_t)taps) & 15)
             return fail(ctx, SEPW_EINVAL, "taps must be 16-byte aligned");
-        SEPW_CUDA(ctx, launch_grid_tiled(ctx->dp, pl, (const float2 *)vis, weight,
+        DevParams dp = ctx->dp;
+        dp.chk_status = ctx->d_status;  // the checked build's bounds failures
+        SEPW_CUDA(ctx, launch_grid_tiled(dp, pl, (const float2 *)vis, weight,
                                          (const float2 *)taps, ctx->d_planar, (float2 *)grid,
                                          ctx->num_sms, s));
     }
@@ -556,6 +577,7 @@ int sepw_grid_planned(sepw_ctx *ctx, const float *taps, const float *vis,
 int sepw_degrid_planned(sepw_ctx *ctx, const float *taps, const float *grid,
                         const float *weight, float *vis_out, sepw_stream_t stream)
 {
+    Range range_("sepw_degrid");
     if (!ctx)
         return SEPW_EINVAL;
     if (!ctx->plan.valid)
@@ -589,10 +611,13 @@ int sepw_degrid_planned(sepw_ctx *ctx, const float *taps, const float *grid,
                                             (const float2 *)taps, (float2 *)vis_out,
                                             ctx->num_sms, tc_prec(pl.form), ctx->d_status,
                                             ctx->tc_ctl, s));
-        else
-            SEPW_CUDA(ctx, launch_degrid_tiled(ctx->dp, pl, (const float2 *)grid, weight,
+        else {
+            DevParams dp = ctx->dp;
+            dp.chk_status = ctx->d_status;  // the checked build's bounds failures
+            SEPW_CUDA(ctx, launch_degrid_tiled(dp, pl, (const float2 *)grid, weight,
                                                (const float2 *)taps, (float2 *)vis_out,
                                                ctx->num_sms, s));
+        }
     }
     return SEPW_OK;
 }
@@ -693,6 +718,34 @@ int sepw_set_schedule(sepw_ctx *ctx, int32_t chunk, int32_t grid_parts)
     return SEPW_OK;
 }
 
+int sepw_checked_build(void) { return SEPW_CHECKED ? 1 : 0; }
+
+int sepw_test_corrupt_plan(sepw_ctx *ctx, int which, int64_t slot, int32_t value)
+{
+    if (!SEPW_CHECKED)
+        return SEPW_ENOTSUP;  // nothing in the default build guards such a value
+    if (!ctx)
+        return SEPW_EINVAL;
+    const Plan &pl = ctx->plan;
+    if (!pl.valid || pl.form == SEPW_FORM_PLAIN || is_tc_form(pl.form))
+        return fail(ctx, SEPW_ENOPLAN, "no tiled plan");
+    if (slot < 0 || slot >= pl.nvis || (which != 0 && which != 1))
+        return fail(ctx, SEPW_EINVAL, "slot %lld or which %d out of range", (long long)slot,
+                    which);
+    cudaError_t e;
+    if (which == 0) {
+        e = cudaMemcpy(pl.d_perm + slot, &value, sizeof(int32_t), cudaMemcpyHostToDevice);
+    } else {
+        uint64_t r = 0;
+        e = cudaMemcpy(&r, pl.d_rec + slot, sizeof(r), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) {
+            r = (r & ~((uint64_t)32767 << 28)) | ((uint64_t)(value & 32767) << 28);
+            e = cudaMemcpy(pl.d_rec + slot, &r, sizeof(r), cudaMemcpyHostToDevice);
+        }
+    }
+    return e == cudaSuccess ? SEPW_OK : cuda_fail(ctx, e, "sepw_test_corrupt_plan");
+}
+
 int sepw_test_stall_mma(sepw_ctx *ctx, int enable)
 {
     if (!ctx)
@@ -703,6 +756,7 @@ int sepw_test_stall_mma(sepw_ctx *ctx, int enable)
 
 int sepw_image(sepw_ctx *ctx, int direction, float *buf, sepw_stream_t stream)
 {
+    Range range_("sepw_image");
     if (!ctx)
         return SEPW_EINVAL;
     if (direction != SEPW_GRID_TO_IMAGE && direction != SEPW_IMAGE_TO_GRID &&
@@ -825,6 +879,7 @@ int sepw_grid_residual_planned(sepw_ctx *ctx, int32_t support_r, int32_t oversam
                                const float *table, const float *vis, const float *weight,
                                float *grid, sepw_stream_t stream)
 {
+    Range range_("sepw_grid_residual");
     if (!ctx)
         return SEPW_EINVAL;
     int rc;
@@ -845,6 +900,7 @@ int sepw_degrid_residual_planned(sepw_ctx *ctx, int32_t support_r, int32_t overs
                                  const float *table, const float *grid, const float *weight,
                                  float *vis_out, sepw_stream_t stream)
 {
+    Range range_("sepw_degrid_residual");
     if (!ctx)
         return SEPW_EINVAL;
     int rc;
@@ -922,6 +978,7 @@ int sepw_wstack_plan(sepw_ctx *ctx, int32_t nslices, const double *w_centres, in
                      const double *u, const double *v, const double *w, int32_t *slice_out,
                      sepw_stream_t stream)
 {
+    Range range_("sepw_wstack_plan");
     if (!ctx)
         return SEPW_EINVAL;
     ctx->ws_centres.clear();
@@ -1012,6 +1069,7 @@ static int ensure_fft_batch(sepw_ctx *ctx, int L)
 
 int sepw_wstack_image(sepw_ctx *ctx, float *slice_grids, float *image, sepw_stream_t stream)
 {
+    Range range_("sepw_wstack_image");
     if (!ctx)
         return SEPW_EINVAL;
     if (ctx->ws_centres.empty())
@@ -1039,6 +1097,7 @@ int sepw_wstack_image(sepw_ctx *ctx, float *slice_grids, float *image, sepw_stre
 int sepw_wstack_model_grids(sepw_ctx *ctx, const float *image, float *slice_grids,
                             sepw_stream_t stream)
 {
+    Range range_("sepw_wstack_model_grids");
     if (!ctx)
         return SEPW_EINVAL;
     if (ctx->ws_centres.empty())

@@ -39,6 +39,12 @@ struct DevParams {
     int32_t grid_parts = 0;
     double l0 = 0.0, m0 = 0.0;
     double a2u = -0.5, a2v = -0.5;
+    // bounds of the current plan, read only by the checked build's checks
+    // (work_item_ok, record_ok): the status word they report into, the
+    // plan's visibility slots and its tile count over all grids
+    int32_t *chk_status = nullptr;
+    int64_t chk_nvis = 0;
+    int64_t chk_tiles = 0;
 };
 
 // Result of locating one visibility.
@@ -257,6 +263,45 @@ struct WorkItem {
     int32_t count;  // number of slots
     int32_t pad;
 };
+
+// Checked build (nvcc -DSEPW_CHECKED=1, libsepw_checked.so): the scatter-
+// form kernels check each work item and each plan record against the plan's
+// bounds before use; a failed check records SEPW_EBOUNDS in the context's
+// status word and the kernel skips the item or visibility.  The default build
+// compiles every check to `true`.
+#ifndef SEPW_CHECKED
+#define SEPW_CHECKED 0
+#endif
+
+__device__ __forceinline__ bool check_ok(const DevParams &p, bool ok)
+{
+#if SEPW_CHECKED
+    if (!ok && p.chk_status)
+        atomicExch(p.chk_status, SEPW_EBOUNDS);
+    return ok;
+#else
+    (void)p;
+    (void)ok;
+    return true;
+#endif
+}
+
+// the item's tile and slot range lie inside the plan
+__device__ __forceinline__ bool work_item_ok(const DevParams &p, const WorkItem &it)
+{
+    return check_ok(p, it.tile >= 0 && it.tile < p.chk_tiles && it.start >= 0 &&
+                           it.count >= 0 && (int64_t)it.start + it.count <= p.chk_nvis);
+}
+
+// the slot's visibility index, table rows and footprint (inside the tile's
+// window and the grid, the tile at grid origin (gy0, gx0)) are in range
+__device__ __forceinline__ bool record_ok(const DevParams &p, uint64_t r, int i, int64_t gy0,
+                                          int64_t gx0)
+{
+    return check_ok(p, i >= 0 && i < p.chk_nvis && rec_plane(r) < p.P && rec_ou(r) < p.OS &&
+                           rec_ov(r) < p.OS && rec_lx(r) < p.T && rec_ly(r) < p.T &&
+                           gx0 + rec_lx(r) + p.S <= p.N && gy0 + rec_ly(r) + p.S <= p.N);
+}
 
 constexpr int kChunk = 2048;      // largest work item (visibilities), the default
 constexpr int kMaxWindow = 64;    // T + S - 1 <= kMaxWindow

@@ -449,6 +449,8 @@ __global__ void __launch_bounds__(kTiledThreads, Blk<S>::BPS) degrid_tiled_block
         if (item >= n_items)
             break;
         const WorkItem it = items[item];
+        if (!work_item_ok(p, it))
+            continue;  // checked build only (uniform over the CTA)
         const TileOrigin o = tile_origin(p, it.tile);
         for (int rr = warp; rr < W; rr += kTiledWarps) {
             const int64_t gy = o.gy0 + rr;
@@ -475,10 +477,16 @@ __global__ void __launch_bounds__(kTiledThreads, Blk<S>::BPS) degrid_tiled_block
             if (s < v1) {
                 const uint64_t r = rec[s];
                 const int i = perm[s];
-                const int row = rec_plane(r) * p.OS;
-                meta[t] = make_int4((row + rec_ou(r)) * S, (row + rec_ov(r)) * S, i,
-                                    __float_as_int(weight ? __ldg(weight + i) : 1.0f));
-                keys[t] = ((rec_ly(r) * 64 + rec_lx(r)) << 1) | (rec_conj(r) ? 1 : 0);
+                if (record_ok(p, r, i, o.gy0, o.gx0)) {
+                    const int row = rec_plane(r) * p.OS;
+                    meta[t] = make_int4((row + rec_ou(r)) * S, (row + rec_ov(r)) * S, i,
+                                        __float_as_int(weight ? __ldg(weight + i) : 1.0f));
+                    keys[t] = ((rec_ly(r) * 64 + rec_lx(r)) << 1) | (rec_conj(r) ? 1 : 0);
+                } else {
+                    // checked build: taps of row 0 at window origin 0, no output
+                    meta[t] = make_int4(0, 0, -1, 0);
+                    keys[t] = 0;
+                }
             }
             __syncwarp();
             const int n = min(K, v1 - (v0 + base));  // may be <= 0
@@ -542,7 +550,8 @@ __global__ void __launch_bounds__(kTiledThreads, Blk<S>::BPS) degrid_tiled_block
                         const float wt = __int_as_float(m.w);
                         // plain-kernel groups computed conj(V / W)
                         const float vi_ = (keys[qb + e] & 1) ? im : -im;
-                        vis_out[m.z] = make_float2(wt * v[0], wt * vi_);
+                        if (!SEPW_CHECKED || m.z >= 0)  // m.z < 0: skipped slot
+                            vis_out[m.z] = make_float2(wt * v[0], wt * vi_);
                     }
                 }
             };
@@ -628,6 +637,8 @@ __global__ void __launch_bounds__(kTiledThreads, kGridBlkPerSM) grid_tiled_block
         if (item >= n_items)
             break;
         const WorkItem it = items[item];
+        if (!work_item_ok(p, it))
+            continue;  // checked build only
         const int len = (it.count + parts - 1) / parts;
         const int b0 = it.start + part * len;
         const int b1 = min(it.start + it.count, b0 + len);
@@ -678,14 +689,20 @@ __global__ void __launch_bounds__(kTiledThreads, kGridBlkPerSM) grid_tiled_block
             if (s < b1) {
                 const uint64_t r = rec[s];
                 const int i = perm[s];
-                const float wt = weight ? __ldg(weight + i) : 1.0f;
-                const float2 x = __ldg(vis + i);
-                const bool cj = rec_conj(r);
-                const int row = rec_plane(r) * p.OS;
-                kq = ((rec_ly(r) * 64 + rec_lx(r)) << 1) | (cj ? 1 : 0);
-                meta[lane] = make_int4((row + rec_ou(r)) * S, (row + rec_ov(r)) * S,
-                                       __float_as_int(wt * x.x),
-                                       __float_as_int(cj ? -wt * x.y : wt * x.y));
+                if (record_ok(p, r, i, o.gy0, o.gx0)) {
+                    const float wt = weight ? __ldg(weight + i) : 1.0f;
+                    const float2 x = __ldg(vis + i);
+                    const bool cj = rec_conj(r);
+                    const int row = rec_plane(r) * p.OS;
+                    kq = ((rec_ly(r) * 64 + rec_lx(r)) << 1) | (cj ? 1 : 0);
+                    meta[lane] = make_int4((row + rec_ou(r)) * S, (row + rec_ov(r)) * S,
+                                           __float_as_int(wt * x.x),
+                                           __float_as_int(cj ? -wt * x.y : wt * x.y));
+                } else {
+                    // checked build: a skipped slot adds zero under key -1,
+                    // which the flush never writes
+                    meta[lane] = make_int4(0, 0, 0, 0);
+                }
                 keys[lane] = kq;
             }
             __syncwarp();
@@ -886,10 +903,20 @@ static cudaError_t launch_degrid_S(const DevParams &p, const Plan &plan,
 #define SEPW_FOR_EACH_S(X) \
     X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24) X(26) X(28) X(30) X(32)
 
-cudaError_t launch_grid_tiled(const DevParams &p, const Plan &plan, const float2 *vis,
+// the plan's bounds for the checked build's checks (unused otherwise)
+static DevParams with_plan_bounds(const DevParams &p, const Plan &plan)
+{
+    DevParams q = p;
+    q.chk_nvis = plan.nvis;
+    q.chk_tiles = (int64_t)p.ntx * p.ntx * plan.ngrids;
+    return q;
+}
+
+cudaError_t launch_grid_tiled(const DevParams &p0, const Plan &plan, const float2 *vis,
                               const float *weight, const float2 *taps, float *planar,
                               float2 *grid, int num_sms, cudaStream_t s)
 {
+    const DevParams p = with_plan_bounds(p0, plan);
     switch (p.S) {
 #define X(SS) \
     case SS: return launch_grid_S<SS>(p, plan, vis, weight, taps, planar, grid, num_sms, s);
@@ -900,11 +927,12 @@ cudaError_t launch_grid_tiled(const DevParams &p, const Plan &plan, const float2
     }
 }
 
-cudaError_t launch_degrid_tiled(const DevParams &p, const Plan &plan,
+cudaError_t launch_degrid_tiled(const DevParams &p0, const Plan &plan,
                                 const float2 *grid, const float *weight,
                                 const float2 *taps, float2 *vis, int num_sms,
                                 cudaStream_t s)
 {
+    const DevParams p = with_plan_bounds(p0, plan);
     switch (p.S) {
 #define X(SS) \
     case SS: return launch_degrid_S<SS>(p, plan, grid, weight, taps, vis, num_sms, s);

@@ -26,6 +26,7 @@ IMAGE_TO_GRID = 1
 IMAGE_TO_GRID_ADJOINT = 2
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP, ENOPLAN, ETOOLARGE = 0, -1, -2, -3, -4, -5, -6, -7
+EBOUNDS = -8
 NOALLOC_MAX_VIS = 524288
 NOALLOC_MAX_TILES = 65536
 
@@ -84,6 +85,9 @@ _SIG = {
     "sepw_device_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), _P]),
     "sepw_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "sepw_test_stall_mma": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sepw_fma_probe": (ctypes.c_int, [ctypes.c_int, _I64, _P, _I64, ctypes.POINTER(_I64), _P]),
+    "sepw_checked_build": (ctypes.c_int, []),
+    "sepw_test_corrupt_plan": (ctypes.c_int, [_P, ctypes.c_int, _I64, ctypes.c_int32]),
     "sepw_set_schedule": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "sepw_plan_batched": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, _P]),
     "sepw_grid_batched": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P,
@@ -109,9 +113,11 @@ _SIG = {
 
 
 def _load():
-    path = _build.LIB
+    # SEPW_CHECKED=1: the bounds-checked build (build.build(checked=True))
+    checked = os.environ.get("SEPW_CHECKED", "0") not in ("", "0")
+    path = _build.LIB_CHECKED if checked else _build.LIB
     if not os.path.exists(path):
-        raise ImportError(f"libsepw.so is not built ({path}); run "
+        raise ImportError(f"{os.path.basename(path)} is not built ({path}); run "
                           "paper_1511_07152_gb300.build.build() first")
     lib = ctypes.CDLL(path)
     for name, (res, args) in _SIG.items():
@@ -395,6 +401,32 @@ def sepw_set_schedule(ctx: Context, chunk: int = 0, grid_parts: int = 0):
 def sepw_test_stall_mma(ctx: Context, enable: bool):
     """Test hook: the tensor-core kernels issue no MMAs, so their waits run out."""
     ctx.check(LIB.sepw_test_stall_mma(ctx.handle, 1 if enable else 0))
+
+
+def sepw_fma_probe(paired: bool, iters: int, out, stream=None) -> int:
+    """Launch the FP32 FMA rate probe on `stream` (scalar FFMA, or paired
+    FFMA2 when `paired`); `out` is a float32 CUDA tensor of at least
+    SMs x 1024 elements.  Returns the launch's flop count; the caller times
+    the launch with CUDA events."""
+    import torch
+    flops = _I64(0)
+    rc = LIB.sepw_fma_probe(1 if paired else 0, int(iters),
+                            _ptr(out, torch.float32, out.numel(), "out"), int(out.numel()),
+                            ctypes.byref(flops), _stream(stream))
+    if rc != OK:
+        raise SepwError(rc, "sepw_fma_probe")
+    return int(flops.value)
+
+
+def sepw_checked_build() -> bool:
+    """True when the loaded library is the bounds-checked build."""
+    return LIB.sepw_checked_build() != 0
+
+
+def sepw_test_corrupt_plan(ctx: Context, which: int, slot: int, value: int):
+    """Test hook of the checked build: overwrite the plan's slot -> visibility
+    index (which = 0) or a record's plane field (which = 1) at `slot`."""
+    ctx.check(LIB.sepw_test_corrupt_plan(ctx.handle, int(which), int(slot), int(value)))
 
 
 def sepw_image(ctx: Context, direction: int, buf, stream=None):

@@ -96,6 +96,15 @@ def test_null_arguments_rejected_without_gpu(sepw):
         sepw.EINVAL
     assert L.sepw_image(None, 0, None, None) == sepw.EINVAL
     assert L.sepw_strerror(sepw.EINVAL) == b"invalid argument"
+    # the FMA probe checks its arguments before any CUDA call
+    flops = ctypes.c_int64(-1)
+    dummy = ctypes.c_float(0.0)
+    for paired, iters in ((0, 0), (1, -5), (0, (1 << 30) + 1)):
+        assert L.sepw_fma_probe(paired, iters, ctypes.byref(dummy), 1 << 20,
+                                ctypes.byref(flops), None) == sepw.EINVAL
+    assert L.sepw_fma_probe(0, 10, None, 1 << 20, ctypes.byref(flops), None) == sepw.EINVAL
+    assert L.sepw_fma_probe(0, 10, ctypes.byref(dummy), 1 << 20, None, None) == sepw.EINVAL
+    assert flops.value == -1
 
 
 def test_params_struct_layout(sepw):
