@@ -750,15 +750,15 @@ def run_ours(args):
                                        "measured (fp16 same; tf32: x 1.1/2.25, the "
                                        "nominal ratio)"}}
             if tc_dg:
-                # degridding: one M128 x N64 x K128 product per 128 visibilities
-                # of a work item (Q = conj(Av) X over the item's 32-column window)
-                dg_flops = 2 * 64 * 128 * nkept
+                # degridding: one M128 x N64 x K64 product per 128 visibilities
+                # of a work item (Q = conj(Av) X over the item's 32-cell window)
+                dg_flops = 2 * 64 * 64 * nkept
                 forms[name]["degrid_tensor_roofline"] = {
                     "bound": "tensor", "unit": "TFLOP/s",
                     "achieved": dg_flops / (fd * 1e-3) / 1e12,
                     "peak": float(peaks["bf16_tflops"]),
                     "frac": dg_flops / (fd * 1e-3) / 1e12 / float(peaks["bf16_tflops"]),
-                    "note": "dense MMA flops per kept visibility (2 x 64 x 128; "
+                    "note": "dense MMA flops per kept visibility (2 x 64 x 64; "
                             "ragged stages not counted) over the degrid kernel"}
             c2.close()
 

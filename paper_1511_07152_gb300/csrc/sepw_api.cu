@@ -101,6 +101,18 @@ int tc_prec(int form)
          : form == SEPW_FORM_TC_FP16X2 ? 2 : form == SEPW_FORM_TC_BF16X2 ? 3 : 4;
 }
 
+// tensor-core workspace: the gridder's tables, then (256-byte aligned) the
+// degridder's
+size_t tc_grid_part_bytes(const DevParams &dp, int64_t items_capacity)
+{
+    return (tc2_tables_bytes(dp, items_capacity) + 255) & ~(size_t)255;
+}
+
+size_t tc_workspace_bytes(const DevParams &dp, int64_t items_capacity)
+{
+    return tc_grid_part_bytes(dp, items_capacity) + tc_degrid_tables_bytes(dp, items_capacity);
+}
+
 int effective_tile(const sepw_params *p)
 {
     if (p->tile != 0)
@@ -471,7 +483,7 @@ static int plan_impl(sepw_ctx *ctx, int32_t ngrids, const int64_t *offsets_host,
             // the contraction gridder's per-call tables and per-item scales:
             // allocated here, so that the *_planned calls allocate nothing and
             // can be captured in a CUDA graph
-            const size_t need = tc2_tables_bytes(ctx->dp, pl.items_capacity);
+            const size_t need = tc_workspace_bytes(ctx->dp, pl.items_capacity);
             if (ctx->tc2_cap < need) {
                 ctx->tc2_cap = 0;
                 if ((rc = grow(ctx, &ctx->d_tc2, need)))
@@ -556,7 +568,7 @@ int sepw_grid_planned(sepw_ctx *ctx, const float *taps, const float *vis,
                                              nullptr, s));
         }
     } else if (is_tc_form(pl.form)) {
-        if (ctx->tc2_cap < tc2_tables_bytes(ctx->dp, pl.items_capacity))
+        if (ctx->tc2_cap < tc_workspace_bytes(ctx->dp, pl.items_capacity))
             return fail(ctx, SEPW_ENOPLAN, "tensor-core workspace missing (plan first)");
         SEPW_CUDA(ctx, launch_grid_tc2(ctx->dp, pl, (const float2 *)vis, weight,
                                        (const float2 *)taps, ctx->d_tc2, (float2 *)grid,
@@ -606,12 +618,16 @@ int sepw_degrid_planned(sepw_ctx *ctx, const float *taps, const float *grid,
         if (((uintptr_t)taps) & 15)
             return fail(ctx, SEPW_EINVAL, "taps must be 16-byte aligned");
         SEPW_CUDA(ctx, launch_zero_dropped(pl, (float2 *)vis_out, s));
-        if (pl.form == SEPW_FORM_TC_BF16 || pl.form == SEPW_FORM_TC_FP16)
+        if (pl.form == SEPW_FORM_TC_BF16 || pl.form == SEPW_FORM_TC_FP16) {
+            if (ctx->tc2_cap < tc_workspace_bytes(ctx->dp, pl.items_capacity))
+                return fail(ctx, SEPW_ENOPLAN, "tensor-core workspace missing (plan first)");
             SEPW_CUDA(ctx, launch_degrid_tc(ctx->dp, pl, (const float2 *)grid, weight,
-                                            (const float2 *)taps, (float2 *)vis_out,
-                                            ctx->num_sms, tc_prec(pl.form), ctx->d_status,
-                                            ctx->tc_ctl, s));
-        else {
+                                            (const float2 *)taps,
+                                            ctx->d_tc2 + tc_grid_part_bytes(ctx->dp,
+                                                                            pl.items_capacity),
+                                            (float2 *)vis_out, ctx->num_sms, tc_prec(pl.form),
+                                            ctx->d_status, ctx->tc_ctl, s));
+        } else {
             DevParams dp = ctx->dp;
             dp.chk_status = ctx->d_status;  // the checked build's bounds failures
             SEPW_CUDA(ctx, launch_degrid_tiled(dp, pl, (const float2 *)grid, weight,

@@ -440,9 +440,12 @@ struct TcControl {
 };
 
 // sepw_tc.cu: contraction-form degridder, prec 0 = BF16, 1 = FP16 (scaled
-// per item); T + S - 1 <= 64
+// per item); T + S - 1 <= 32, S <= 16.  tables: tc_degrid_tables_bytes(p,
+// plan.items_capacity) bytes of device workspace (per-call tap tables and
+// per-item scale exponents).
+size_t tc_degrid_tables_bytes(const DevParams &p, int64_t items_capacity);
 cudaError_t launch_degrid_tc(const DevParams &p, const Plan &plan, const float2 *grid,
-                             const float *weight, const float2 *taps, float2 *vis,
+                             const float *weight, const float2 *taps, void *tables, float2 *vis,
                              int num_sms, int prec, int32_t *status, TcControl ctl,
                              cudaStream_t s);
 

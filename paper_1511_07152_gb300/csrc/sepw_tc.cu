@@ -1,10 +1,57 @@
 // Tensor-core (tcgen05) contraction form of the degridder (the adjoint of the
 // contraction gridder of sepw_tc_grid.cu), for BF16 and FP16 operands with
-// FP32 accumulation in tensor memory.  Every mbarrier wait is bounded; on
-// expiry the kernel records SEPW_ETIMEOUT in the device status word, stops
-// issuing work, waits (bounded) for its own MMAs and frees its tensor memory.
+// FP32 accumulation in tensor memory.
+//
+// Per work item (one tile; its window X of W = T + S - 1 <= 32 cells a side)
+// and stage of 128 visibilities (Sec. 2, the adjoint of gridding):
+//     Q[i][x] = sum_y conj(a_i[y]) X[y][x]           (tcgen05.mma)
+//     V_i = W_i sum_j tu'_i[j] Q[i][lx_i + j]         (epilogue, FP32)
+// with a_i the v-taps of visibility i at its row offset (conjugated for
+// w < 0) and tu' = conj(tu) (tu for w < 0).  In real arithmetic with
+// K = (y, re/im) and N = (x, re/im), 32 window cells a side:
+//     A[i][(y,0)] = a_r    A[i][(y,1)] = a_i
+//     B[(y,0)][(x,0)] = X_r    B[(y,1)][(x,0)] = X_i
+//     B[(y,0)][(x,1)] = X_i    B[(y,1)][(x,1)] = -X_r
+// one MMA of M = 128 (visibilities), N = 64, K = 16, four per stage.  FP16
+// operands take a power-of-two scale per item so that the window's largest
+// component is below 1 (a small kernel finds it per item first).
+//
+// Operands are K-major (8 K elements, one row of a core matrix, in 16 bytes):
+//   - A, per stage, from a table built per call: per (plane, oversample,
+//     row offset mod 4) five 16-byte chunks of (re, im) pairs of the v-taps,
+//     pre-shifted so that chunk j holds rows 4 j .. 4 j + 3 of a footprint
+//     starting at row offset ly (mod 4).  A visibility's row of A is eight
+//     16-byte stores: chunk j at K chunk j + ly / 4, zeros elsewhere, so no
+//     row needs clearing.  Slot i of a stage is row i; the 8 lanes of a
+//     quarter warp write 8 different rows of one core matrix column: no bank
+//     conflicts, whatever chunk each lane writes.
+//   - B, the window, once per item, two 4-byte (re, im) pairs per cell.
+//
+// Roles (work items assigned to CTAs round robin, so every role walks the
+// same items and stages without a shared counter):
+//   - eight producer warps in two groups of four, group g owning stage buffer
+//     g: it writes the CTA's stages t = g, g + 2, ... (one lane per
+//     visibility).  Owning its buffer, a group has itself filled the
+//     buffer's previous stage, so its wait for that stage's MMAs is never two
+//     mbarrier phases behind.  All eight build each item's window (two
+//     buffers, item n in buffer n mod 2) and wait until it is complete
+//     before they declare a stage full;
+//   - one MMA thread: per stage it waits for "full" and for the accumulator,
+//     issues the four MMAs and commits them to the stage's "done" barrier,
+//     which both the producers (buffer free) and the epilogue (accumulator
+//     ready) wait on: one commit per stage;
+//   - four epilogue warps (one per tensor-memory lane quarter), one thread
+//     per visibility: it reads its accumulator row, stores it column-major in
+//     shared memory (its own column: conflict-free, no barrier), releases the
+//     accumulator, and takes the u-direction dot product at its column offset
+//     with the u-taps of a second 16-bit table.
+// Every mbarrier wait is bounded; on expiry the kernel records SEPW_ETIMEOUT
+// in the device status word, every role leaves its loop, the MMA thread waits
+// (bounded) for its own MMAs and the tensor memory is freed.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+
+#include <algorithm>
 
 #include "sepw_internal.cuh"
 #include "sepw_tc_ptx.cuh"
@@ -14,12 +61,32 @@ namespace {
 
 using namespace tcx;
 
-constexpr int kM = 128;                         // MMA rows (visibilities)
-// K-major canonical layout of a K = 128 operand: K-adjacent core matrices 128
-// bytes apart, 8-row groups kSBO bytes apart
-constexpr int kSBO = (128 / 8) * 128;
+constexpr int kDgWin = 32;                               // window edge
+constexpr int kDgVis = 128;                              // visibilities per stage (M)
+constexpr int kDgK = 2 * kDgWin;                         // K = (y, re/im)
+constexpr int kDgN = 2 * kDgWin;                         // N = (x, re/im)
+constexpr int kDgGroups = 2;                             // producer groups = buffers
+constexpr int kDgGroupWarps = kDgVis / 32;               // warps per group
+constexpr int kDgProdWarps = kDgGroups * kDgGroupWarps;  // 8
+constexpr int kDgProducers = 32 * kDgProdWarps;          // 256
+constexpr int kDgMmaWarp = kDgProdWarps;
+constexpr int kDgEpiWarps = 4;
+constexpr int kDgBlock = kDgProducers + 32 + 32 * kDgEpiWarps;  // 416
+constexpr uint32_t kDgLbo = 128;                 // K-adjacent core matrices
+constexpr uint32_t kDgSbo = (kDgK / 8) * 128;    // 8-row groups
+constexpr int kDgABytes = kDgVis * kDgK * 2;     // 16 KiB
+constexpr int kDgBBytes = kDgN * kDgK * 2;       // 8 KiB
+constexpr int kDgStgBytes = kDgN * kDgVis * 4;   // 32 KiB, column-major
+constexpr uint32_t kDgTmemCols = kDgGroups * kDgN;  // two accumulators
+constexpr int kDgVChunks = 6;   // v-table chunks per row: 5 used, 1 pad (32-byte loads)
+constexpr int kDgUChunks = 4;   // u-table chunks per row: 16 (re, im) pairs
+constexpr size_t kDgSmem = 2 * (size_t)kDgABytes + 2 * (size_t)kDgBBytes + kDgStgBytes +
+                           16 * sizeof(uint64_t);
+static_assert(kDgSmem <= 227 * 1024, "shared memory per CTA");
 
-// Packs (x, y) as a BF16 (PREC 0) or FP16 (PREC 1) pair.
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Packs (x, y) as a BF16 (PREC 0) or FP16 (PREC 1) pair, x in the low half.
 template <int PREC>
 __device__ __forceinline__ uint32_t pack_pair(float x, float y)
 {
@@ -32,87 +99,131 @@ __device__ __forceinline__ uint32_t pack_pair(float x, float y)
     }
 }
 
-// ---------------------------------------------------------------------------
-// Tensor-core contraction form of the degridder (the adjoint, Sec. 2).
-//
-// Per tile window X (64 x 64 cells) and 128 visibilities of a stage,
-//     Q[i][x] = sum_y conj(Av[i][y]) X[y][x]
-// with Av[i][y] the v-taps of visibility i at its row offset (conjugated for
-// w < 0), then V_i = W_i sum_j tu'[j] Q[i][lx_i + j] with tu' = conj(tu)
-// (tu for w < 0).  In real arithmetic with K = (y, re/im) and N = (x, re/im):
-//     A[i][(y,0)] = Av_r, A[i][(y,1)] = Av_i;
-//     B[(y,0)][(x,0)] = X_r, B[(y,1)][(x,0)] = X_i,
-//     B[(y,0)][(x,1)] = X_i, B[(y,1)][(x,1)] = -X_r,
-// one tcgen05.mma shape M = 128 (visibilities), N = 128, K = 16 per step,
-// eight steps per stage; a stage inside one sub-block of the tile contracts
-// only the 32 window columns its footprints reach (N = 64).  B (the window) is built once per work item in one
-// of two buffers; A (2 S values per visibility, cleared after use) in one of
-// two stage buffers; a window buffer is rebuilt only after the epilogue has
-// finished the item before last.  Roles: 8 producer warps (two threads per
-// visibility), one MMA warp (two TMEM accumulators of 128 columns), 4 epilogue warps,
-// one thread per visibility: each reads its accumulator row, stages it in
-// shared memory and takes the u-direction dot product at its own column
-// offset.  FP16 operands take a power-of-two scale per item so that the
-// window's largest component is below 1.  Work items are assigned to CTAs
-// statically (item = CTA, CTA + grid, ...), so every role walks the same
-// sequence without a shared counter.  All mbarrier waits are bounded.
-// ---------------------------------------------------------------------------
-constexpr int kDgWin = 64;  // window edge, T + S - 1 <= 64
-constexpr int kDgProducers = 256;
-constexpr int kDgProdWarps = kDgProducers / 32;
-constexpr int kDgVis = 128;
-constexpr int kDgEpiWarps = 4;
-constexpr int kDgMmaWarp = kDgProdWarps;
-constexpr int kDgBlock = kDgProducers + 32 + 32 * kDgEpiWarps;
-constexpr int kDgK = 128, kDgN = 128;
-constexpr int kDgABytes = kDgVis * kDgK * 2;  // 32 KiB
-constexpr int kDgBBytes = kDgN * kDgK * 2;    // 32 KiB
-constexpr int kDgStgBytes = kDgVis * kDgN * 4;  // 64 KiB
-constexpr uint32_t kDgTmemCols = 256;
-
-constexpr size_t degrid_tc_smem_bytes()
+template <int PREC>
+__device__ __forceinline__ float2 unpack_pair(uint32_t w)
 {
-    return 2 * (size_t)kDgABytes + 2 * (size_t)kDgBBytes + kDgStgBytes + 12 * sizeof(uint64_t);
+    if constexpr (PREC == 0) {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    } else {
+        return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+    }
 }
 
-// Instruction descriptor: A and B K-major, M = 128, N = n.
-__host__ __device__ constexpr uint32_t instr_desc_n(uint32_t ab_fmt, int n)
+__device__ __forceinline__ void st16(unsigned char *p, uint4 v)
 {
-    return instr_desc(ab_fmt, false, false, kM, n);
+    *reinterpret_cast<uint4 *>(p) = v;
 }
 
-// K-major no-swizzle descriptor of a K = 128 operand
-__device__ __forceinline__ uint64_t kdesc(uint32_t addr) { return smem_desc(addr, 128, kSBO); }
+__device__ __forceinline__ void ldg32(const void *p, uint4 &a, uint4 &b)
+{
+    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z),
+                   "=r"(b.w)
+                 : "l"(p));
+}
 
-// byte offset of element pair k, k + 1 (k even) of row `row` in a K = 128
+// byte offset of the element pair k, k + 1 (k even) of row `row` of a K = 64
 // K-major operand
 __device__ __forceinline__ uint32_t dg_off(int row, int k)
 {
-    return (uint32_t)((row >> 3) * kSBO + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+    return (uint32_t)((row >> 3) * kDgSbo + (k >> 3) * kDgLbo + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// First window column x0 of a stage whose visibilities all lie in one column
-// of sub-blocks of the tile (the plan keeps the bins of a column consecutive
-// inside an item, so the first and last slot decide), when their footprints
-// fit the 32 columns x0 .. x0 + 31: the stage then contracts only those
-// (N = 64).  -1: the whole window (N = 128).  x0 is a multiple of 4 (the
-// operand's 8-row core-matrix groups) and at most 32.
-__device__ __forceinline__ int dg_stage_x0(const DevParams &p, const WorkItem &it, int st,
-                                           const uint64_t *__restrict__ rec, int S)
+// Workspace layout (from the start of the degridder's part): v-table, u-table,
+// then one scale exponent per work item.
+struct DgTables {
+    uint4 *vtab;
+    uint4 *utab;
+    int32_t *item_exp;
+};
+
+DgTables dg_tables(const DevParams &p, void *base)
 {
-    if (p.T + S - 1 <= 32)
-        return 0;  // the whole window fits the 32 columns
-    const int first = it.start + st * kDgVis;
-    const int last = min(first + kDgVis, it.start + it.count) - 1;
-    const uint64_t r0 = __ldg(reinterpret_cast<const unsigned long long *>(rec) + first);
-    const uint64_t r1 = __ldg(reinterpret_cast<const unsigned long long *>(rec) + last);
-    const int sx = sub_bin(rec_lx(r0), rec_ly(r0), rec_conj(r0), p) >> 3;
-    if (sx != sub_bin(rec_lx(r1), rec_ly(r1), rec_conj(r1), p) >> 3)
-        return -1;
-    const int lo = (sx * p.T + 3) >> 2;            // first column of the sub-block
-    const int hi = (((sx + 1) * p.T + 3) >> 2) - 1;  // last column
-    const int x0 = min(lo & ~3, 32);
-    return hi + S <= x0 + 32 ? x0 : -1;
+    const int64_t nrow = (int64_t)p.P * p.OS;
+    unsigned char *b = reinterpret_cast<unsigned char *>(base);
+    DgTables t;
+    t.vtab = reinterpret_cast<uint4 *>(b);
+    t.utab = t.vtab + nrow * 4 * kDgVChunks;
+    t.item_exp = reinterpret_cast<int32_t *>(
+        b + align256((size_t)nrow * (4 * kDgVChunks + kDgUChunks) * 16));
+    return t;
+}
+
+// Per-call tables from the caller's complex64 taps (v taps at p.voff).
+template <int PREC>
+__global__ void dg_tables_kernel(DevParams p, const float2 *__restrict__ taps, uint4 *vtab,
+                                 uint4 *utab)
+{
+    const int64_t nrow = (int64_t)p.P * p.OS;
+    const int64_t nv = nrow * 4 * kDgVChunks, nu = nrow * kDgUChunks;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv + nu; e += stride) {
+        uint32_t w[4];
+        if (e < nv) {
+            const int j = (int)(e % kDgVChunks);
+            const int s = (int)((e / kDgVChunks) % 4);
+            const int64_t row = e / (kDgVChunks * 4);
+            const float2 *tv = taps + p.voff + row * p.S;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = 4 * j - s + q;  // tap of window row 4 j + q (offset s)
+                const float2 t = (j < 5 && k >= 0 && k < p.S) ? tv[k] : make_float2(0.f, 0.f);
+                w[q] = pack_pair<PREC>(t.x, t.y);
+            }
+            vtab[e] = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+            const int64_t q0 = e - nv;
+            const int j = (int)(q0 % kDgUChunks);
+            const int64_t row = q0 / kDgUChunks;
+            const float2 *tu = taps + row * p.S;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = 4 * j + q;
+                const float2 t = k < p.S ? tu[k] : make_float2(0.f, 0.f);
+                w[q] = pack_pair<PREC>(t.x, t.y);
+            }
+            utab[q0] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// Power-of-two exponent a per work item such that the largest component of
+// its window is below 2^a (the FP16 form scales the window by 2^-a).
+__global__ void dg_item_scale_kernel(DevParams p, const WorkItem *__restrict__ items,
+                                     const int32_t *__restrict__ nitems,
+                                     const float2 *__restrict__ grid, int32_t *item_exp)
+{
+    __shared__ float s_red[8];
+    const int n_items = *nitems;
+    const int W = p.T + p.S - 1;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const TileOrigin o = tile_origin(p, items[item].tile);
+        float m = 0.f;
+        for (int e = threadIdx.x; e < kDgWin * kDgWin; e += blockDim.x) {
+            const int y = e >> 5, x = e & 31;
+            if (y < W && x < W && o.gy0 + y < p.N && o.gx0 + x < p.N) {
+                const float2 g = __ldg(grid + o.base + (o.gy0 + y) * p.N + o.gx0 + x);
+                m = fmaxf(m, fmaxf(fabsf(g.x), fabsf(g.y)));
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if ((threadIdx.x & 31) == 0)
+            s_red[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+                m = fmaxf(m, s_red[w]);
+            int a = 0;
+            if (m > 0.f && m <= 3.0e38f) {
+                frexpf(m, &a);  // m = f 2^a, f in [0.5, 1)
+                a = max(-126, min(126, a));
+            }
+            item_exp[item] = a;
+        }
+        __syncthreads();
+    }
 }
 
 template <int S, int PREC>
@@ -120,25 +231,21 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
     DevParams p, const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems,
     const uint64_t *__restrict__ rec, const int32_t *__restrict__ perm,
     const float2 *__restrict__ grid, const float *__restrict__ weight,
-    const float2 *__restrict__ taps, float2 *__restrict__ vis_out, int32_t *status,
+    const uint4 *__restrict__ vtab, const uint4 *__restrict__ utab,
+    const int32_t *__restrict__ item_exp, float2 *__restrict__ vis_out, int32_t *status,
     TcControl ctl)
 {
-    constexpr int NT = (S + 1) / 2 < 8 ? (S + 1) / 2 : 8;  // taps per producer thread
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *const Abuf = smem;                          // [2] stage operands
-    unsigned char *const Bbuf = smem + 2 * kDgABytes;          // [2] window operands
+    unsigned char *const Abuf = smem;                      // [2] stage operands
+    unsigned char *const Bbuf = smem + 2 * kDgABytes;      // [2] window operands
     float *const stg = reinterpret_cast<float *>(Bbuf + 2 * kDgBBytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(Bbuf + 2 * kDgBBytes + kDgStgBytes);
-    uint64_t *full = bars, *empty = bars + 2, *accf = bars + 4, *tfree = bars + 6,
-             *efree = bars + 8, *bready = bars + 10;
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(Bbuf + 2 * kDgBBytes + kDgStgBytes);
+    uint64_t *const full = bars, *const done = bars + 2, *const tfree = bars + 4,
+                    *const efree = bars + 6, *const bready = bars + 8, *const drain = bars + 10;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
-    __shared__ int s_aexp[2];
-    __shared__ float s_red[kDgProdWarps];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr uint32_t idesc = instr_desc_n(PREC == 0 ? 1u : 0u, kDgN);
-    constexpr uint32_t idesc64 = instr_desc_n(PREC == 0 ? 1u : 0u, kDgN / 2);
     const int n_items = *nitems;
     const int W = p.T + S - 1;
 
@@ -146,23 +253,18 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
         reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
-            mbar_init(full + b, kDgProdWarps);
-            mbar_init(empty + b, 1);
-            mbar_init(accf + b, 1);
+            mbar_init(full + b, kDgGroupWarps);
+            mbar_init(done + b, 1);
             mbar_init(tfree + b, kDgEpiWarps);
             mbar_init(efree + b, kDgEpiWarps);
             mbar_init(bready + b, kDgProdWarps);
         }
+        mbar_init(drain, 1);
         s_abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_init_fence();
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&s_tmem)),
-                     "r"(kDgTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    if (warp == 0)
+        tmem_alloc(&s_tmem, kDgTmemCols);
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -177,9 +279,11 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
     };
 
     if (warp < kDgProdWarps) {
-        // ---------------- producers: window operand per item, A per stage
-        const int ii = tid >> 1, h = tid & 1;
-        int oldly[2] = {-1, -1};
+        // ------------------------------------------------------------ producers
+        const int grp = warp / kDgGroupWarps;  // the stage buffer this group owns
+        const int ii = tid & (kDgVis - 1);     // slot of a stage (row of A)
+        unsigned char *const A = Abuf + grp * kDgABytes;
+        const uint32_t arow = (uint32_t)((ii >> 3) * kDgSbo + (ii & 7) * 16);
         int tg = 0;
         for (int n = 0;; ++n) {
             const int item = blockIdx.x + n * gridDim.x;
@@ -188,171 +292,128 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
             const WorkItem it = items[item];
             const int nst = (it.count + kDgVis - 1) / kDgVis;
             const int ib = n & 1;
-            // window buffer ib and its scale are free once the epilogue has
-            // finished item n - 2 (all of whose MMAs it has waited for)
+            // window buffer ib is free once the epilogue has finished item
+            // n - 2, all of whose MMAs it has waited for
             if (n >= 2)
                 warp_wait(efree + ib, ((n - 2) >> 1) & 1);
             tc_fence_after();
-            // the window, scaled by 2^-a for FP16
             const TileOrigin o = tile_origin(p, it.tile);
-            float2 xv[16];
-            float m = 0.f;
+            float scale = 1.f;
+            if constexpr (PREC == 1)
+                scale = ldexpf(1.0f, -__ldg(item_exp + item));
+            unsigned char *const B = Bbuf + ib * kDgBBytes;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int e = tid + q * kDgProducers;  // 4096 cells
-                const int y = e >> 6, x = e & 63;
+            for (int q = 0; q < kDgWin * kDgWin / kDgProducers; ++q) {
+                const int e = tid + q * kDgProducers;
+                const int y = e >> 5, x = e & 31;
                 float2 g = make_float2(0.f, 0.f);
                 if (y < W && x < W && o.gy0 + y < p.N && o.gx0 + x < p.N)
                     g = __ldg(grid + o.base + (o.gy0 + y) * p.N + o.gx0 + x);
-                xv[q] = g;
-                m = fmaxf(m, fmaxf(fabsf(g.x), fabsf(g.y)));
-            }
-            int a_exp = 0;
-            float scale = 1.f;
-            if constexpr (PREC == 1) {
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1)
-                    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-                if (lane == 0)
-                    s_red[warp] = m;
-                asm volatile("bar.sync 1, %0;" ::"n"(kDgProducers) : "memory");
-                m = s_red[0];
-#pragma unroll
-                for (int w2 = 1; w2 < kDgProdWarps; ++w2)
-                    m = fmaxf(m, s_red[w2]);
-                if (m > 0.f && m <= 3.0e38f) {
-                    frexpf(m, &a_exp);
-                    a_exp = max(-126, min(126, a_exp));
-                    scale = ldexpf(1.0f, -a_exp);
-                }
-            }
-            unsigned char *B = Bbuf + ib * kDgBBytes;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int e = tid + q * kDgProducers;
-                const int y = e >> 6, x = e & 63;
-                const float xr = xv[q].x * scale, xi = xv[q].y * scale;
+                const float xr = g.x * scale, xi = g.y * scale;
                 // row (x, re): (X_r, X_i) at K = (y, 0), (y, 1); row (x, im): (X_i, -X_r)
                 *reinterpret_cast<uint32_t *>(B + dg_off(2 * x, 2 * y)) = pack_pair<PREC>(xr, xi);
                 *reinterpret_cast<uint32_t *>(B + dg_off(2 * x + 1, 2 * y)) =
                     pack_pair<PREC>(xi, -xr);
             }
-            if (tid == 0)
-                s_aexp[ib] = a_exp;
             fence_proxy_async();
             __syncwarp();
             if (lane == 0)
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bready + ib))
-                             : "memory");
-            // records and taps run one stage ahead of the operand writes, so
-            // their load latency overlaps the wait for the stage buffer
-            auto stage_rec = [&](int st) -> uint64_t {
-                return st < nst && st * kDgVis + ii < it.count
-                           ? __ldg(reinterpret_cast<const unsigned long long *>(rec) +
-                                   it.start + st * kDgVis + ii)
-                           : ~0ull;
-            };
-            float2 tv[NT];
-            auto stage_taps = [&](uint64_t r) {
-                if (r != ~0ull) {
-                    const float2 *pv = taps + p.voff + (rec_plane(r) * p.OS + rec_ov(r)) * S;
-#pragma unroll
-                    for (int j = 0; j < NT; ++j) {
-                        const int k = NT * h + j;
-                        tv[j] = k < S ? __ldg(pv + k) : make_float2(0.f, 0.f);
-                    }
-                }
-            };
-            uint64_t rcur = stage_rec(0);
-            stage_taps(rcur);
-            for (int st = 0; st < nst; ++st) {
-                const int t = tg + st, b = t & 1;
-                const uint64_t rnext = stage_rec(st + 1);
-                const bool valid = rcur != ~0ull;
-                const int ly = valid ? rec_ly(rcur) : -1;
-                const bool cj = valid && rec_conj(rcur);
-                if (t >= 2)
-                    warp_wait(empty + b, ((t - 2) >> 1) & 1);
-                tc_fence_after();
-                unsigned char *A = Abuf + b * kDgABytes;
-                if (oldly[b] >= 0) {
-#pragma unroll
-                    for (int j = 0; j < NT; ++j) {
-                        const int k = NT * h + j;
-                        if (k < S)
-                            *reinterpret_cast<uint32_t *>(A + dg_off(ii, 2 * (oldly[b] + k))) = 0u;
-                    }
-                }
+                mbar_arrive(bready + ib);
+            // the whole window is written (and fenced) before any stage of
+            // the item is declared full
+            warp_wait(bready + ib, (n >> 1) & 1);
+            for (int st = grp ^ (tg & 1); st < nst && !s_abort; st += 2) {
+                const int t = tg + st;  // t mod 2 == grp
+                const int e = st * kDgVis + ii;
+                const bool valid = e < it.count;
+                uint4 c[kDgVChunks];
+                int ly = 0;
+                uint32_t cjm = 0;
                 if (valid) {
-#pragma unroll
-                    for (int j = 0; j < NT; ++j) {
-                        const int k = NT * h + j;
-                        if (k < S)
-                            *reinterpret_cast<uint32_t *>(A + dg_off(ii, 2 * (ly + k))) =
-                                pack_pair<PREC>(tv[j].x, cj ? -tv[j].y : tv[j].y);
-                    }
+                    const uint64_t r =
+                        __ldg(reinterpret_cast<const unsigned long long *>(rec) + it.start + e);
+                    ly = rec_ly(r);
+                    cjm = rec_conj(r) ? 0x80000000u : 0u;  // conj(a): the im halves
+                    const uint4 *pv =
+                        vtab + (((int64_t)rec_plane(r) * p.OS + rec_ov(r)) * 4 + (ly & 3)) *
+                                   kDgVChunks;
+                    ldg32(pv, c[0], c[1]);
+                    ldg32(pv + 2, c[2], c[3]);
+                    ldg32(pv + 4, c[4], c[5]);
                 }
-                oldly[b] = ly;
+                // buffer grp held stage t - 2: wait for its MMAs
+                if (t >= 2)
+                    warp_wait(done + grp, ((t - 2) >> 1) & 1);
+                tc_fence_after();
+                const int oy4 = valid ? (ly >> 2) : 8;
+#pragma unroll
+                for (int j = 0; j < 5; ++j) {
+                    const int ca = j + oy4;  // K chunk of table chunk j
+                    if (ca < 8)
+                        st16(A + arow + ca * kDgLbo,
+                             make_uint4(c[j].x ^ cjm, c[j].y ^ cjm, c[j].z ^ cjm, c[j].w ^ cjm));
+                }
+#pragma unroll
+                for (int ca = 0; ca < 8; ++ca)
+                    if (ca < oy4 || ca > oy4 + 4)
+                        st16(A + arow + ca * kDgLbo, make_uint4(0, 0, 0, 0));
                 fence_proxy_async();
                 __syncwarp();
                 if (lane == 0)
-                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(full + b))
-                                 : "memory");
-                rcur = rnext;
-                stage_taps(rcur);
+                    mbar_arrive(full + grp);
             }
             tg += nst;
         }
     } else if (warp == kDgMmaWarp) {
-        // ---------------- MMA issue (one thread)
-        int tg = 0;
-        int last_t = -1;  // last stage whose MMAs were committed
-        for (int n = 0;; ++n) {
-            const int item = blockIdx.x + n * gridDim.x;
-            if (item >= n_items || s_abort)
-                break;
-            const WorkItem it = items[item];
-            const int nst = (it.count + kDgVis - 1) / kDgVis;
-            if (lane == 0) {
-                for (int st = 0; st < nst && !s_abort; ++st) {
+        // ------------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            constexpr uint32_t idesc = instr_desc(PREC == 0 ? 1u : 0u, false, false, kDgVis, kDgN);
+            const uint64_t da0 = smem_desc(smem_u32(Abuf), kDgLbo, kDgSbo);
+            const uint64_t db0 = smem_desc(smem_u32(Bbuf), kDgLbo, kDgSbo);
+            constexpr uint64_t kStep = (2 * kDgLbo) >> 4;  // K = 16: two core matrices
+            int tg = 0;
+            bool ok = true, issued = false;
+            for (int n = 0; ok; ++n) {
+                const int item = blockIdx.x + n * gridDim.x;
+                if (item >= n_items)
+                    break;
+                const int nst = (items[item].count + kDgVis - 1) / kDgVis;
+                const uint64_t db = db0 + (uint64_t)((n & 1) * kDgBBytes >> 4);
+                for (int st = 0; st < nst; ++st) {
                     const int t = tg + st, b = t & 1;
-                    const int x0 = dg_stage_x0(p, it, st, rec, S);
                     if (!mbar_wait(full + b, (t >> 1) & 1, ctl.wait_ns) ||
                         (t >= 2 && !mbar_wait(tfree + b, ((t - 2) >> 1) & 1, ctl.wait_ns))) {
-                        s_abort = 1;
+                        ok = false;
                         break;
                     }
                     if (ctl.stall)
                         continue;  // test hook: issue and signal nothing
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(Abuf + b * kDgABytes);
-                    // rows 2 x0 .. 2 x0 + 63 of the window operand: x0 / 4
-                    // groups of 8 rows (kSBO bytes each) in
-                    const uint32_t b0 = smem_u32(Bbuf + (n & 1) * kDgBBytes) +
-                                        (x0 >= 0 ? (uint32_t)(x0 / 4) * kSBO : 0u);
-                    const uint32_t id = x0 >= 0 ? idesc64 : idesc;
+                    const uint64_t da = da0 + (uint64_t)((b * kDgABytes) >> 4);
                     const uint32_t d = tmem + (uint32_t)(b * kDgN);
 #pragma unroll
                     for (int kq = 0; kq < kDgK / 16; ++kq)
-                        mma_f16(d, kdesc(a0 + 256 * kq), kdesc(b0 + 256 * kq), id,
-                                kq > 0 ? 1u : 0u);
-                    mma_commit(empty + b);
-                    mma_commit(accf + b);
-                    last_t = t;
+                        mma_f16(d, da + kStep * kq, db + kStep * kq, idesc, kq > 0 ? 1u : 0u);
+                    mma_commit(done + b);
+                    issued = true;
+                }
+                tg += nst;
+            }
+            if (!ok) {
+                s_abort = 1;
+                // bounded wait for every MMA this thread issued before the
+                // tensor memory is released
+                if (issued) {
+                    mma_commit(drain);
+                    mbar_wait(drain, 0, ctl.wait_ns);
                 }
             }
-            __syncwarp();
-            tg += nst;
         }
-        // after a timeout, wait (bounded) for this CTA's own MMAs before the
-        // tensor memory is released
-        if (s_abort && lane == 0 && last_t >= 0)
-            mbar_wait(accf + (last_t & 1), (last_t >> 1) & 1, ctl.wait_ns);
     } else {
-        // ---------------- epilogue: one thread per visibility of a stage
-        const int qq = warp & 3;  // TMEM lane quarter this warp may read
+        // ------------------------------------------------------------ epilogue
+        const int qq = warp & 3;  // tensor-memory lane quarter of this warp
         const int ii = 32 * qq + lane;
-        float *const row = stg + ii * kDgN;
+        float *const col = stg + ii;  // accumulator column c at col[c * kDgVis]
         int tg = 0;
         for (int n = 0;; ++n) {
             const int item = blockIdx.x + n * gridDim.x;
@@ -361,131 +422,130 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
             const WorkItem it = items[item];
             const int nst = (it.count + kDgVis - 1) / kDgVis;
             const int ib = n & 1;
-            // the records, output index and u-taps of a stage are loaded one
-            // stage ahead, before the wait for its accumulator
-            auto stage_rec = [&](int st, int &io) -> uint64_t {
-                if (st < nst && st * kDgVis + ii < it.count) {
-                    const int slot = it.start + st * kDgVis + ii;
-                    io = __ldg(perm + slot);
-                    return __ldg(reinterpret_cast<const unsigned long long *>(rec) + slot);
-                }
-                return ~0ull;
-            };
-            float2 tu[S];
-            float wcur = 1.f;
-            auto stage_taps = [&](uint64_t r, int io) {
-                if (r != ~0ull) {
-                    const float2 *pu = taps + (rec_plane(r) * p.OS + rec_ou(r)) * S;
-#pragma unroll
-                    for (int j = 0; j < S; ++j)
-                        tu[j] = __ldg(pu + j);
-                    wcur = weight ? __ldg(weight + io) : 1.0f;
-                }
-            };
-            int iout = 0;
-            uint64_t rcur = stage_rec(0, iout);
-            stage_taps(rcur, iout);
-            warp_wait(bready + ib, (n >> 1) & 1);
-            const float back = ldexpf(1.0f, s_aexp[ib]);
+            float back = 1.0f;
+            if constexpr (PREC == 1)
+                back = ldexpf(1.0f, __ldg(item_exp + item));
             for (int st = 0; st < nst; ++st) {
                 const int t = tg + st, b = t & 1;
-                int inext = 0;
-                const uint64_t rnext = stage_rec(st + 1, inext);
-                const int x0 = dg_stage_x0(p, it, st, rec, S);
-                const int nc = x0 >= 0 ? kDgN / 64 : kDgN / 32;  // accumulator chunks
-                const int xb = x0 >= 0 ? x0 : 0;                  // window column of chunk 0
-                warp_wait(accf + b, (t >> 1) & 1);
+                // this slot's record, output index, weight and u-taps, loaded
+                // before the wait for the accumulator
+                const int e = st * kDgVis + ii;
+                const bool valid = e < it.count;
+                int iout = 0, lx = 0;
+                float wt = 0.f, sg = 1.f;
+                uint4 u0, u1, u2, u3;
+                if (valid) {
+                    const int slot = it.start + e;
+                    const uint64_t r = __ldg(reinterpret_cast<const unsigned long long *>(rec) + slot);
+                    iout = __ldg(perm + slot);
+                    wt = (weight ? __ldg(weight + iout) : 1.0f) * back;
+                    lx = rec_lx(r);
+                    sg = rec_conj(r) ? 1.f : -1.f;  // tu' = conj(tu) unless w < 0
+                    const uint4 *pu = utab + ((int64_t)rec_plane(r) * p.OS + rec_ou(r)) * kDgUChunks;
+                    ldg32(pu, u0, u1);
+                    ldg32(pu + 2, u2, u3);
+                }
+                warp_wait(done + b, (t >> 1) & 1);
                 if (s_abort)
                     break;
                 tc_fence_after();
 #pragma unroll
-                for (int c = 0; c < kDgN / 32; ++c) {
-                    if (c >= nc)
-                        break;
+                for (int h = 0; h < kDgN / 32; ++h) {
                     uint32_t rr[32];
-                    SEPW_TMEM_LD32(tmem + ((uint32_t)(32 * qq) << 16) + (uint32_t)(b * kDgN + 32 * c),
+                    SEPW_TMEM_LD32(tmem + ((uint32_t)(32 * qq) << 16) + (uint32_t)(b * kDgN + 32 * h),
                                    rr);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    tmem_wait_ld();
 #pragma unroll
-                    for (int x = 0; x < 32; ++x)
-                        row[(32 * c + x) ^ lane] = __uint_as_float(rr[x]);
+                    for (int xx = 0; xx < 32; ++xx)
+                        col[(32 * h + xx) * kDgVis] = __uint_as_float(rr[xx]);
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0)
-                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tfree + b))
-                                 : "memory");
-                if (rcur != ~0ull) {
-                    const uint64_t r = rcur;
-                    const int i = iout;
-                    const float sg = rec_conj(r) ? 1.f : -1.f;  // tu' = conj(tu) unless w < 0
-                    const int lx = rec_lx(r);
+                    mbar_arrive(tfree + b);
+                if (valid) {
+                    const uint32_t uw[16] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w,
+                                             u2.x, u2.y, u2.z, u2.w, u3.x, u3.y, u3.z, u3.w};
                     float vr = 0.f, vi = 0.f;
 #pragma unroll
                     for (int j = 0; j < S; ++j) {
-                        const float ur = tu[j].x, ui = sg * tu[j].y;
-                        const int col = 2 * (lx - xb + j);
-                        const float qr = row[col ^ lane], qi = row[(col + 1) ^ lane];
+                        const float2 u = unpack_pair<PREC>(uw[j]);
+                        const float ur = u.x, ui = sg * u.y;
+                        const float *q = col + 2 * (lx + j) * kDgVis;
+                        const float qr = q[0], qi = q[kDgVis];
                         vr += ur * qr - ui * qi;
                         vi += ur * qi + ui * qr;
                     }
-                    const float wt = wcur * back;
-                    vis_out[i] = make_float2(wt * vr, wt * vi);
+                    vis_out[iout] = make_float2(wt * vr, wt * vi);
                 }
-                rcur = rnext;
-                iout = inext;
-                stage_taps(rcur, iout);
             }
             __syncwarp();
             if (lane == 0 && !s_abort)
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(efree + ib))
-                             : "memory");
+                mbar_arrive(efree + ib);
             tg += nst;
         }
     }
 
+    __syncthreads();
     if (s_abort && tid == 0)
         atomicExch(status, SEPW_ETIMEOUT);
-    tc_fence_before();
-    __syncthreads();
     tc_fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kDgTmemCols)
-                     : "memory");
+        tmem_dealloc(tmem, kDgTmemCols);
 }
 
 template <int S, int PREC>
 cudaError_t launch_degrid_tc_S(const DevParams &p, const Plan &plan, const float2 *grid,
-                               const float *weight, const float2 *taps, float2 *vis,
-                               int num_sms, int32_t *status, TcControl ctl, cudaStream_t s)
+                               const float *weight, const float2 *taps, void *tables,
+                               float2 *vis, int num_sms, int32_t *status, TcControl ctl,
+                               cudaStream_t s)
 {
-    constexpr size_t shm = degrid_tc_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(degrid_tc_kernel<S, PREC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const DgTables t = dg_tables(p, tables);
+    const int64_t nrow = (int64_t)p.P * p.OS;
+    const int64_t n = nrow * (4 * kDgVChunks + kDgUChunks);
+    dg_tables_kernel<PREC><<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(
+        p, taps, t.vtab, t.utab);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    degrid_tc_kernel<S, PREC><<<num_sms, kDgBlock, shm, s>>>(
-        p, plan.d_items, plan.d_nitems, plan.d_rec, plan.d_perm, grid, weight, taps, vis,
-        status, ctl);
+    if constexpr (PREC == 1) {
+        dg_item_scale_kernel<<<std::max(1, std::min(plan.items_capacity, 8 * num_sms)), 256, 0,
+                               s>>>(p, plan.d_items, plan.d_nitems, grid, t.item_exp);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+    }
+    e = cudaFuncSetAttribute(degrid_tc_kernel<S, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kDgSmem);
+    if (e != cudaSuccess)
+        return e;
+    degrid_tc_kernel<S, PREC><<<num_sms, kDgBlock, kDgSmem, s>>>(
+        p, plan.d_items, plan.d_nitems, plan.d_rec, plan.d_perm, grid, weight, t.vtab, t.utab,
+        t.item_exp, vis, status, ctl);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+size_t tc_degrid_tables_bytes(const DevParams &p, int64_t items_capacity)
+{
+    const size_t nrow = (size_t)p.P * p.OS;
+    return align256(nrow * (4 * kDgVChunks + kDgUChunks) * 16) +
+           sizeof(int32_t) * (size_t)std::max<int64_t>(items_capacity, 1);
+}
+
 cudaError_t launch_degrid_tc(const DevParams &p, const Plan &plan, const float2 *grid,
-                             const float *weight, const float2 *taps, float2 *vis,
+                             const float *weight, const float2 *taps, void *tables, float2 *vis,
                              int num_sms, int prec, int32_t *status, TcControl ctl,
                              cudaStream_t s)
 {
-    if (p.T + p.S - 1 > kDgWin || (prec != 0 && prec != 1))
+    if (p.T + p.S - 1 > kDgWin || p.S > 16 || (prec != 0 && prec != 1))
         return cudaErrorInvalidValue;
 #define SEPW_DG_CASE(SS)                                                                     \
     case SS:                                                                                 \
-        return prec ? launch_degrid_tc_S<SS, 1>(p, plan, grid, weight, taps, vis, num_sms,   \
-                                                status, ctl, s)                              \
-                    : launch_degrid_tc_S<SS, 0>(p, plan, grid, weight, taps, vis, num_sms,   \
-                                                status, ctl, s);
+        return prec ? launch_degrid_tc_S<SS, 1>(p, plan, grid, weight, taps, tables, vis,    \
+                                                num_sms, status, ctl, s)                     \
+                    : launch_degrid_tc_S<SS, 0>(p, plan, grid, weight, taps, tables, vis,    \
+                                                num_sms, status, ctl, s);
     switch (p.S) {
         SEPW_DG_CASE(2) SEPW_DG_CASE(4) SEPW_DG_CASE(6) SEPW_DG_CASE(8) SEPW_DG_CASE(10)
         SEPW_DG_CASE(12) SEPW_DG_CASE(14) SEPW_DG_CASE(16)
