@@ -322,16 +322,25 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
             // the whole window is written (and fenced) before any stage of
             // the item is declared full
             warp_wait(bready + ib, (n >> 1) & 1);
-            for (int st = grp ^ (tg & 1); st < nst && !s_abort; st += 2) {
-                const int t = tg + st;  // t mod 2 == grp
+            // the slot's record of the group's next stage is loaded one stage
+            // ahead (records stream from HBM; the table rows are L2 hits)
+            auto rec_of = [&](int st) -> uint64_t {
                 const int e = st * kDgVis + ii;
-                const bool valid = e < it.count;
+                return st < nst && e < it.count
+                           ? __ldg(reinterpret_cast<const unsigned long long *>(rec) + it.start + e)
+                           : ~0ull;
+            };
+            int st0 = grp ^ (tg & 1);
+            uint64_t rcur = rec_of(st0);
+            for (int st = st0; st < nst && !s_abort; st += 2) {
+                const int t = tg + st;  // t mod 2 == grp
+                const uint64_t rnext = rec_of(st + 2);
+                const bool valid = rcur != ~0ull;  // no record has its top bits set
                 uint4 c[kDgVChunks];
                 int ly = 0;
                 uint32_t cjm = 0;
                 if (valid) {
-                    const uint64_t r =
-                        __ldg(reinterpret_cast<const unsigned long long *>(rec) + it.start + e);
+                    const uint64_t r = rcur;
                     ly = rec_ly(r);
                     cjm = rec_conj(r) ? 0x80000000u : 0u;  // conj(a): the im halves
                     const uint4 *pv =
@@ -361,6 +370,7 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
                 __syncwarp();
                 if (lane == 0)
                     mbar_arrive(full + grp);
+                rcur = rnext;
             }
             tg += nst;
         }
@@ -425,19 +435,29 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
             float back = 1.0f;
             if constexpr (PREC == 1)
                 back = ldexpf(1.0f, __ldg(item_exp + item));
+            // the slot's record and output index one stage ahead; its weight
+            // and u-taps (which depend on them) before the accumulator wait
+            auto rec_of = [&](int st, int &io) -> uint64_t {
+                const int e = st * kDgVis + ii;
+                if (st < nst && e < it.count) {
+                    io = __ldg(perm + it.start + e);
+                    return __ldg(reinterpret_cast<const unsigned long long *>(rec) + it.start + e);
+                }
+                return ~0ull;
+            };
+            int inext = 0;
+            uint64_t rnext = rec_of(0, inext);
             for (int st = 0; st < nst; ++st) {
                 const int t = tg + st, b = t & 1;
-                // this slot's record, output index, weight and u-taps, loaded
-                // before the wait for the accumulator
-                const int e = st * kDgVis + ii;
-                const bool valid = e < it.count;
+                const uint64_t r = rnext;
+                const int io = inext;
+                rnext = rec_of(st + 1, inext);
+                const bool valid = r != ~0ull;
                 int iout = 0, lx = 0;
                 float wt = 0.f, sg = 1.f;
                 uint4 u0, u1, u2, u3;
                 if (valid) {
-                    const int slot = it.start + e;
-                    const uint64_t r = __ldg(reinterpret_cast<const unsigned long long *>(rec) + slot);
-                    iout = __ldg(perm + slot);
+                    iout = io;
                     wt = (weight ? __ldg(weight + iout) : 1.0f) * back;
                     lx = rec_lx(r);
                     sg = rec_conj(r) ? 1.f : -1.f;  // tu' = conj(tu) unless w < 0
