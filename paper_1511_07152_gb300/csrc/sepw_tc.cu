@@ -14,7 +14,7 @@
 //     B[(y,0)][(x,1)] = X_i    B[(y,1)][(x,1)] = -X_r
 // one MMA of M = 128 (visibilities), N = 64, K = 16, four per stage.  FP16
 // operands take a power-of-two scale per item so that the window's largest
-// component is below 1 (a small kernel finds it per item first).
+// component is below 1 (the producers find it while they load the window).
 //
 // Operands are K-major (8 K elements, one row of a core matrix, in 16 bytes):
 //   - A, per stage, from a table built per call: per (plane, oversample,
@@ -129,12 +129,11 @@ __device__ __forceinline__ uint32_t dg_off(int row, int k)
     return (uint32_t)((row >> 3) * kDgSbo + (k >> 3) * kDgLbo + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// Workspace layout (from the start of the degridder's part): v-table, u-table,
-// then one scale exponent per work item.
+// Workspace layout (from the start of the degridder's part): v-table, then
+// u-table.
 struct DgTables {
     uint4 *vtab;
     uint4 *utab;
-    int32_t *item_exp;
 };
 
 DgTables dg_tables(const DevParams &p, void *base)
@@ -144,8 +143,6 @@ DgTables dg_tables(const DevParams &p, void *base)
     DgTables t;
     t.vtab = reinterpret_cast<uint4 *>(b);
     t.utab = t.vtab + nrow * 4 * kDgVChunks;
-    t.item_exp = reinterpret_cast<int32_t *>(
-        b + align256((size_t)nrow * (4 * kDgVChunks + kDgUChunks) * 16));
     return t;
 }
 
@@ -187,43 +184,20 @@ __global__ void dg_tables_kernel(DevParams p, const float2 *__restrict__ taps, u
     }
 }
 
-// Power-of-two exponent a per work item such that the largest component of
-// its window is below 2^a (the FP16 form scales the window by 2^-a).
-__global__ void dg_item_scale_kernel(DevParams p, const WorkItem *__restrict__ items,
-                                     const int32_t *__restrict__ nitems,
-                                     const float2 *__restrict__ grid, int32_t *item_exp)
+// Power-of-two exponent a with the window's largest component (the maximum
+// of the producer warps' maxima) below 2^a: the FP16 form's scale 2^-a.
+__device__ __forceinline__ int window_exp(const float *wm)
 {
-    __shared__ float s_red[8];
-    const int n_items = *nitems;
-    const int W = p.T + p.S - 1;
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const TileOrigin o = tile_origin(p, items[item].tile);
-        float m = 0.f;
-        for (int e = threadIdx.x; e < kDgWin * kDgWin; e += blockDim.x) {
-            const int y = e >> 5, x = e & 31;
-            if (y < W && x < W && o.gy0 + y < p.N && o.gx0 + x < p.N) {
-                const float2 g = __ldg(grid + o.base + (o.gy0 + y) * p.N + o.gx0 + x);
-                m = fmaxf(m, fmaxf(fabsf(g.x), fabsf(g.y)));
-            }
-        }
+    float m = 0.f;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-        if ((threadIdx.x & 31) == 0)
-            s_red[threadIdx.x >> 5] = m;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-                m = fmaxf(m, s_red[w]);
-            int a = 0;
-            if (m > 0.f && m <= 3.0e38f) {
-                frexpf(m, &a);  // m = f 2^a, f in [0.5, 1)
-                a = max(-126, min(126, a));
-            }
-            item_exp[item] = a;
-        }
-        __syncthreads();
+    for (int w = 0; w < kDgProdWarps; ++w)
+        m = fmaxf(m, wm[w]);
+    int a = 0;
+    if (m > 0.f && m <= 3.0e38f) {
+        frexpf(m, &a);  // m = f 2^a, f in [0.5, 1)
+        a = max(-126, min(126, a));
     }
+    return a;
 }
 
 template <int S, int PREC>
@@ -232,8 +206,7 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
     const uint64_t *__restrict__ rec, const int32_t *__restrict__ perm,
     const float2 *__restrict__ grid, const float *__restrict__ weight,
     const uint4 *__restrict__ vtab, const uint4 *__restrict__ utab,
-    const int32_t *__restrict__ item_exp, float2 *__restrict__ vis_out, int32_t *status,
-    TcControl ctl)
+    float2 *__restrict__ vis_out, int32_t *status, TcControl ctl)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *const Abuf = smem;                      // [2] stage operands
@@ -241,9 +214,11 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
     float *const stg = reinterpret_cast<float *>(Bbuf + 2 * kDgBBytes);
     uint64_t *const bars = reinterpret_cast<uint64_t *>(Bbuf + 2 * kDgBBytes + kDgStgBytes);
     uint64_t *const full = bars, *const done = bars + 2, *const tfree = bars + 4,
-                    *const efree = bars + 6, *const bready = bars + 8, *const drain = bars + 10;
+                    *const efree = bars + 6, *const bready = bars + 8, *const drain = bars + 10,
+                    *const wmax = bars + 11;  // [2]
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
+    __shared__ float s_wmax[2][kDgProdWarps];  // FP16: per-warp window maxima
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_items = *nitems;
@@ -258,6 +233,7 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
             mbar_init(tfree + b, kDgEpiWarps);
             mbar_init(efree + b, kDgEpiWarps);
             mbar_init(bready + b, kDgProdWarps);
+            mbar_init(wmax + b, kDgProdWarps);
         }
         mbar_init(drain, 1);
         s_abort = 0;
@@ -298,18 +274,40 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
                 warp_wait(efree + ib, ((n - 2) >> 1) & 1);
             tc_fence_after();
             const TileOrigin o = tile_origin(p, it.tile);
-            float scale = 1.f;
-            if constexpr (PREC == 1)
-                scale = ldexpf(1.0f, -__ldg(item_exp + item));
-            unsigned char *const B = Bbuf + ib * kDgBBytes;
+            constexpr int kCells = kDgWin * kDgWin / kDgProducers;
+            float2 gv[kCells];
 #pragma unroll
-            for (int q = 0; q < kDgWin * kDgWin / kDgProducers; ++q) {
+            for (int q = 0; q < kCells; ++q) {
                 const int e = tid + q * kDgProducers;
                 const int y = e >> 5, x = e & 31;
-                float2 g = make_float2(0.f, 0.f);
+                gv[q] = make_float2(0.f, 0.f);
                 if (y < W && x < W && o.gy0 + y < p.N && o.gx0 + x < p.N)
-                    g = __ldg(grid + o.base + (o.gy0 + y) * p.N + o.gx0 + x);
-                const float xr = g.x * scale, xi = g.y * scale;
+                    gv[q] = __ldg(grid + o.base + (o.gy0 + y) * p.N + o.gx0 + x);
+            }
+            float scale = 1.f;
+            if constexpr (PREC == 1) {
+                // the window's largest component, over the eight producer
+                // warps: scale 2^-a with that maximum below 2^a
+                float m = 0.f;
+#pragma unroll
+                for (int q = 0; q < kCells; ++q)
+                    m = fmaxf(m, fmaxf(fabsf(gv[q].x), fabsf(gv[q].y)));
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+                    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+                if (lane == 0) {
+                    s_wmax[ib][warp] = m;
+                    mbar_arrive(wmax + ib);
+                }
+                warp_wait(wmax + ib, (n >> 1) & 1);
+                scale = ldexpf(1.0f, -window_exp(s_wmax[ib]));
+            }
+            unsigned char *const B = Bbuf + ib * kDgBBytes;
+#pragma unroll
+            for (int q = 0; q < kCells; ++q) {
+                const int e = tid + q * kDgProducers;
+                const int y = e >> 5, x = e & 31;
+                const float xr = gv[q].x * scale, xi = gv[q].y * scale;
                 // row (x, re): (X_r, X_i) at K = (y, 0), (y, 1); row (x, im): (X_i, -X_r)
                 *reinterpret_cast<uint32_t *>(B + dg_off(2 * x, 2 * y)) = pack_pair<PREC>(xr, xi);
                 *reinterpret_cast<uint32_t *>(B + dg_off(2 * x + 1, 2 * y)) =
@@ -433,8 +431,13 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
             const int nst = (it.count + kDgVis - 1) / kDgVis;
             const int ib = n & 1;
             float back = 1.0f;
-            if constexpr (PREC == 1)
-                back = ldexpf(1.0f, __ldg(item_exp + item));
+            if constexpr (PREC == 1) {
+                // every producer warp writes its maximum before it arrives on
+                // wmax; s_wmax[ib] is rewritten only for item n + 2, after
+                // this warp has finished item n
+                warp_wait(wmax + ib, (n >> 1) & 1);
+                back = ldexpf(1.0f, window_exp(s_wmax[ib]));
+            }
             // the slot's record and output index one stage ahead; its weight
             // and u-taps (which depend on them) before the accumulator wait
             auto rec_of = [&](int st, int &io) -> uint64_t {
@@ -528,19 +531,13 @@ cudaError_t launch_degrid_tc_S(const DevParams &p, const Plan &plan, const float
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    if constexpr (PREC == 1) {
-        dg_item_scale_kernel<<<std::max(1, std::min(plan.items_capacity, 8 * num_sms)), 256, 0,
-                               s>>>(p, plan.d_items, plan.d_nitems, grid, t.item_exp);
-        if ((e = cudaGetLastError()) != cudaSuccess)
-            return e;
-    }
     e = cudaFuncSetAttribute(degrid_tc_kernel<S, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kDgSmem);
     if (e != cudaSuccess)
         return e;
     degrid_tc_kernel<S, PREC><<<num_sms, kDgBlock, kDgSmem, s>>>(
         p, plan.d_items, plan.d_nitems, plan.d_rec, plan.d_perm, grid, weight, t.vtab, t.utab,
-        t.item_exp, vis, status, ctl);
+        vis, status, ctl);
     return cudaGetLastError();
 }
 
@@ -548,9 +545,9 @@ cudaError_t launch_degrid_tc_S(const DevParams &p, const Plan &plan, const float
 
 size_t tc_degrid_tables_bytes(const DevParams &p, int64_t items_capacity)
 {
+    (void)items_capacity;
     const size_t nrow = (size_t)p.P * p.OS;
-    return align256(nrow * (4 * kDgVChunks + kDgUChunks) * 16) +
-           sizeof(int32_t) * (size_t)std::max<int64_t>(items_capacity, 1);
+    return align256(nrow * (4 * kDgVChunks + kDgUChunks) * 16);
 }
 
 cudaError_t launch_degrid_tc(const DevParams &p, const Plan &plan, const float2 *grid,
