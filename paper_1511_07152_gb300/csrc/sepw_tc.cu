@@ -41,10 +41,10 @@
 //     which both the producers (buffer free) and the epilogue (accumulator
 //     ready) wait on: one commit per stage;
 //   - four epilogue warps (one per tensor-memory lane quarter), one thread
-//     per visibility: it reads its accumulator row, stores it column-major in
-//     shared memory (its own column: conflict-free, no barrier), releases the
-//     accumulator, and takes the u-direction dot product at its column offset
-//     with the u-taps of a second 16-bit table.
+//     per visibility: it reads its accumulator row into registers, releases
+//     the accumulator, shifts the row to its column offset with a barrel
+//     shift in registers and takes the u-direction dot product with the
+//     u-taps of a second 16-bit table.
 // Every mbarrier wait is bounded; on expiry the kernel records SEPW_ETIMEOUT
 // in the device status word, every role leaves its loop, the MMA thread waits
 // (bounded) for its own MMAs and the tensor memory is freed.
@@ -76,12 +76,10 @@ constexpr uint32_t kDgLbo = 128;                 // K-adjacent core matrices
 constexpr uint32_t kDgSbo = (kDgK / 8) * 128;    // 8-row groups
 constexpr int kDgABytes = kDgVis * kDgK * 2;     // 16 KiB
 constexpr int kDgBBytes = kDgN * kDgK * 2;       // 8 KiB
-constexpr int kDgStgBytes = kDgN * kDgVis * 4;   // 32 KiB, column-major
 constexpr uint32_t kDgTmemCols = kDgGroups * kDgN;  // two accumulators
 constexpr int kDgVChunks = 6;   // v-table chunks per row: 5 used, 1 pad (32-byte loads)
 constexpr int kDgUChunks = 4;   // u-table chunks per row: 16 (re, im) pairs
-constexpr size_t kDgSmem = 2 * (size_t)kDgABytes + 2 * (size_t)kDgBBytes + kDgStgBytes +
-                           16 * sizeof(uint64_t);
+constexpr size_t kDgSmem = 2 * (size_t)kDgABytes + 2 * (size_t)kDgBBytes + 16 * sizeof(uint64_t);
 static_assert(kDgSmem <= 227 * 1024, "shared memory per CTA");
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -184,6 +182,27 @@ __global__ void dg_tables_kernel(DevParams p, const float2 *__restrict__ taps, u
     }
 }
 
+// bits of the footprint column offset lx (0 .. T - 1, T <= 33 - S)
+template <int S>
+constexpr int kShiftBits = ((33 - S) & ~1) > 16 ? 5 : ((33 - S) & ~1) > 8 ? 4 : 3;
+
+// q[k] <- q[k + 2 lx] for k < 2 S: levels BIT .. 0 of a barrel shift, level
+// b moving by 2^(b+1) entries when bit b of lx is set and keeping only the
+// entries the lower levels and the taps read.
+template <int S, int BIT>
+__device__ __forceinline__ void barrel_shift(float (&q)[kDgN], int lx)
+{
+    if constexpr (BIT >= 0) {
+        constexpr int kSh = 2 << BIT;
+        constexpr int kLen = 2 * S + 2 * ((1 << BIT) - 1);
+        const bool on = (lx >> BIT) & 1;
+#pragma unroll
+        for (int k = 0; k < kLen; ++k)
+            q[k] = on ? (k + kSh < kDgN ? q[k + kSh] : 0.f) : q[k];
+        barrel_shift<S, BIT - 1>(q, lx);
+    }
+}
+
 // Power-of-two exponent a with the window's largest component (the maximum
 // of the producer warps' maxima) below 2^a: the FP16 form's scale 2^-a.
 __device__ __forceinline__ int window_exp(const float *wm)
@@ -211,8 +230,7 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *const Abuf = smem;                      // [2] stage operands
     unsigned char *const Bbuf = smem + 2 * kDgABytes;      // [2] window operands
-    float *const stg = reinterpret_cast<float *>(Bbuf + 2 * kDgBBytes);
-    uint64_t *const bars = reinterpret_cast<uint64_t *>(Bbuf + 2 * kDgBBytes + kDgStgBytes);
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(Bbuf + 2 * kDgBBytes);
     uint64_t *const full = bars, *const done = bars + 2, *const tfree = bars + 4,
                     *const efree = bars + 6, *const bready = bars + 8, *const drain = bars + 10,
                     *const wmax = bars + 11;  // [2]
@@ -421,7 +439,6 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
         // ------------------------------------------------------------ epilogue
         const int qq = warp & 3;  // tensor-memory lane quarter of this warp
         const int ii = 32 * qq + lane;
-        float *const col = stg + ii;  // accumulator column c at col[c * kDgVis]
         int tg = 0;
         for (int n = 0;; ++n) {
             const int item = blockIdx.x + n * gridDim.x;
@@ -472,6 +489,8 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
                 if (s_abort)
                     break;
                 tc_fence_after();
+                // this row's 64 accumulator columns (x, re/im)
+                float q[kDgN];
 #pragma unroll
                 for (int h = 0; h < kDgN / 32; ++h) {
                     uint32_t rr[32];
@@ -480,13 +499,17 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
                     tmem_wait_ld();
 #pragma unroll
                     for (int xx = 0; xx < 32; ++xx)
-                        col[(32 * h + xx) * kDgVis] = __uint_as_float(rr[xx]);
+                        q[32 * h + xx] = __uint_as_float(rr[xx]);
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0)
                     mbar_arrive(tfree + b);
                 if (valid) {
+                    // q[k] <- q[k + 2 lx]: a barrel shift in registers, one
+                    // level per bit of lx, each keeping only the entries the
+                    // later levels and the 2 S taps still read
+                    barrel_shift<S, kShiftBits<S> - 1>(q, lx);
                     const uint32_t uw[16] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w,
                                              u2.x, u2.y, u2.z, u2.w, u3.x, u3.y, u3.z, u3.w};
                     float vr = 0.f, vi = 0.f;
@@ -494,8 +517,7 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
                     for (int j = 0; j < S; ++j) {
                         const float2 u = unpack_pair<PREC>(uw[j]);
                         const float ur = u.x, ui = sg * u.y;
-                        const float *q = col + 2 * (lx + j) * kDgVis;
-                        const float qr = q[0], qi = q[kDgVis];
+                        const float qr = q[2 * j], qi = q[2 * j + 1];
                         vr += ur * qr - ui * qi;
                         vi += ur * qi + ui * qr;
                     }
