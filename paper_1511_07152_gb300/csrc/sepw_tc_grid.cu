@@ -180,6 +180,28 @@ __device__ __forceinline__ float2 unpack_part(uint32_t w)
     }
 }
 
+// Moves 16 packed 16-bit values v[0..15] (pairs in in[0..7], zero beyond) to
+// positions s .. s + 15 of 24 (pairs in out[0..11]), s = 0..7: two
+// conditional word shifts and one half-word step (__byte_perm takes the high
+// half of the lower word and the low half of the higher).
+__device__ __forceinline__ void shift16(const uint32_t (&in)[8], int s, uint32_t (&out)[12])
+{
+    uint32_t t[12];
+#pragma unroll
+    for (int w = 0; w < 12; ++w)
+        t[w] = w < 8 ? in[w] : 0u;
+    const int m = s >> 1;
+#pragma unroll
+    for (int w = 11; w >= 0; --w)
+        t[w] = (m & 2) ? (w >= 2 ? t[w - 2] : 0u) : t[w];
+#pragma unroll
+    for (int w = 11; w >= 0; --w)
+        t[w] = (m & 1) ? (w >= 1 ? t[w - 1] : 0u) : t[w];
+#pragma unroll
+    for (int w = 0; w < 12; ++w)
+        out[w] = (s & 1) ? __byte_perm(w >= 1 ? t[w - 1] : 0u, t[w], 0x5432) : t[w];
+}
+
 // sign flip of the 16-bit values of a chunk selected by mask (exact)
 __device__ __forceinline__ uint4 xor4(uint4 v, uint32_t m)
 {
@@ -224,9 +246,41 @@ __global__ void tables_kernel(DevParams p, const float2 *__restrict__ taps, uint
     constexpr int H = Cfg<PREC>::H;
     constexpr bool U16 = Cfg<PREC>::U16;
     const int64_t nrow = (int64_t)p.P * p.OS;
-    const int64_t nv = nrow * 8 * H * 2 * 3;
-    const int64_t nu = nrow * 8 * 3 * (U16 ? 2 : 4);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if constexpr (U16) {
+        // unshifted rows, 16-bit: v per (plane, oversample): [component][8
+        // words of tap pairs (2 w, 2 w + 1)]; u: 16 words of (re, im)
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nrow * 8;
+             e += stride) {
+            const int64_t row = e >> 3;
+            const int q = (int)(e & 7);
+            uint32_t w[4];
+            if (q < 4) {  // v: component q / 2, words 4 (q & 1) .. + 3
+                const float2 *tv = taps + p.voff + row * p.S;
+                const int comp = q >> 1;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int t0 = 2 * (4 * (q & 1) + k);
+                    const float a = t0 < p.S ? (comp ? tv[t0].y : tv[t0].x) : 0.f;
+                    const float b = t0 + 1 < p.S ? (comp ? tv[t0 + 1].y : tv[t0 + 1].x) : 0.f;
+                    w[k] = pack_part<Cfg<PREC>::BF>(a, b, 0);
+                }
+                vtab[row * 4 + q] = make_uint4(w[0], w[1], w[2], w[3]);
+            } else {  // u: taps 4 (q - 4) .. + 3 as (re, im)
+                const float2 *tu = taps + row * p.S;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int t0 = 4 * (q - 4) + k;
+                    const float2 t = t0 < p.S ? tu[t0] : make_float2(0.f, 0.f);
+                    w[k] = pack_part<Cfg<PREC>::BF>(t.x, t.y, 0);
+                }
+                reinterpret_cast<uint4 *>(utab)[row * 4 + (q - 4)] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        return;
+    }
+    const int64_t nv = nrow * 8 * H * 2 * 3;
+    const int64_t nu = nrow * 8 * 3 * 4;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv + nu; e += stride) {
         if (e < nv) {
             int64_t q = e;
@@ -251,24 +305,6 @@ __global__ void tables_kernel(DevParams p, const float2 *__restrict__ taps, uint
                 w[t2] = pack_part<Cfg<PREC>::BF>(v[0], v[1], h);
             }
             vtab[e] = make_uint4(w[0], w[1], w[2], w[3]);
-        } else if constexpr (U16) {
-            // 16 bytes: taps 4 f .. 4 f + 3 of chunk j, (re, im) 16-bit pairs
-            int64_t q = e - nv;
-            const int f = (int)(q % 2);
-            q /= 2;
-            const int j = (int)(q % 3);
-            q /= 3;
-            const int s = (int)(q % 8);
-            q /= 8;
-            const float2 *row = taps + q * p.S;
-            uint32_t w[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int k = 8 * j - s + 4 * f + u;
-                const float2 t = (k >= 0 && k < p.S) ? row[k] : make_float2(0.f, 0.f);
-                w[u] = pack_part<Cfg<PREC>::BF>(t.x, t.y, 0);
-            }
-            reinterpret_cast<uint4 *>(utab)[e - nv] = make_uint4(w[0], w[1], w[2], w[3]);
         } else {
             int64_t q = e - nv;
             const int f = (int)(q % 4);
@@ -555,9 +591,10 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                     }
                 } else {
                 // this slot's taps and value
-                uint4 va[H][2][3];
-                float4 ut[3][4];  // FP32 u-taps (hi + lo forms)
-                uint4 uh[3][2];   // 16-bit u-taps (one-part forms): 8 (re, im) words a chunk
+                uint4 va[H][2][3];  // pre-shifted v chunks (hi + lo forms)
+                float4 ut[3][4];    // FP32 u-taps, pre-shifted (hi + lo forms)
+                uint4 vq[4];        // one-part forms: unshifted v words [component][8]
+                uint4 uq[4];        // one-part forms: 16 unshifted (re, im) u words
                 float2 x = make_float2(0.f, 0.f);
                 float wt = 0.f;
                 int lx = 0, ly = 0;
@@ -575,21 +612,25 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                     ly = rec_ly(r[sl]);
                     cjm = rec_conj(r[sl]) ? 0x80008000u : 0u;
                     const int64_t row = (int64_t)rec_plane(r[sl]) * p.OS;
-                    const uint4 *pa = vtab + ((row + rec_ov(r[sl])) * 8 + (ly & 7)) * (H * 6);
-                    const int64_t urow = (row + rec_ou(r[sl])) * 8 + (lx & 7);
-                    // the row's 6 H chunks ([h][component][j]) in 32-byte loads
-#pragma unroll
-                    for (int h = 0; h < H; ++h) {
-                        ldg32(pa + h * 6, va[h][0][0], va[h][0][1]);
-                        ldg32(pa + h * 6 + 2, va[h][0][2], va[h][1][0]);
-                        ldg32(pa + h * 6 + 4, va[h][1][1], va[h][1][2]);
-                    }
                     if constexpr (C::U16) {
-                        const uint4 *pu = reinterpret_cast<const uint4 *>(utab) + urow * 6;
-#pragma unroll
-                        for (int j = 0; j < 3; ++j)
-                            ldg32(pu + 2 * j, uh[j][0], uh[j][1]);
+                        // unshifted 64-byte rows, shifted in registers below
+                        const uint4 *pv = vtab + (row + rec_ov(r[sl])) * 4;
+                        const uint4 *pu = reinterpret_cast<const uint4 *>(utab) +
+                                          (row + rec_ou(r[sl])) * 4;
+                        ldg32(pv, vq[0], vq[1]);
+                        ldg32(pv + 2, vq[2], vq[3]);
+                        ldg32(pu, uq[0], uq[1]);
+                        ldg32(pu + 2, uq[2], uq[3]);
                     } else {
+                        const uint4 *pa = vtab + ((row + rec_ov(r[sl])) * 8 + (ly & 7)) * (H * 6);
+                        const int64_t urow = (row + rec_ou(r[sl])) * 8 + (lx & 7);
+                        // the row's 6 H chunks ([h][component][j]) in 32-byte loads
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            ldg32(pa + h * 6, va[h][0][0], va[h][0][1]);
+                            ldg32(pa + h * 6 + 2, va[h][0][2], va[h][1][0]);
+                            ldg32(pa + h * 6 + 4, va[h][1][1], va[h][1][2]);
+                        }
                         const float4 *pu = utab + urow * 12;
 #pragma unroll
                         for (int j = 0; j < 3; ++j)
@@ -603,6 +644,20 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                                     make_float4(__uint_as_float(bb.x), __uint_as_float(bb.y),
                                                 __uint_as_float(bb.z), __uint_as_float(bb.w));
                             }
+                    }
+                }
+                if constexpr (C::U16) {
+                    // v chunks at row offset ly mod 8, from the unshifted words
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const uint32_t in[8] = {vq[2 * c].x, vq[2 * c].y, vq[2 * c].z, vq[2 * c].w,
+                                                vq[2 * c + 1].x, vq[2 * c + 1].y, vq[2 * c + 1].z,
+                                                vq[2 * c + 1].w};
+                        uint32_t o[12];
+                        shift16(in, ly & 7, o);
+#pragma unroll
+                        for (int j = 0; j < 3; ++j)
+                            va[0][c][j] = make_uint4(o[4 * j], o[4 * j + 1], o[4 * j + 2], o[4 * j + 3]);
                     }
                 }
                 if (sl == 0) {
@@ -652,6 +707,36 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                 const float wi = (wt * x.y) * scale;
                 const float wis = cjm ? -wi : wi;      // conj(u-taps) for w < 0
                 const float wrs = cjm ? -wr : wr;
+                if constexpr (C::U16) {
+                    // all 16 products, rounded, packed in pairs and shifted to
+                    // the column offset lx mod 8
+                    const uint32_t uw[16] = {uq[0].x, uq[0].y, uq[0].z, uq[0].w, uq[1].x, uq[1].y,
+                                             uq[1].z, uq[1].w, uq[2].x, uq[2].y, uq[2].z, uq[2].w,
+                                             uq[3].x, uq[3].y, uq[3].z, uq[3].w};
+                    uint32_t rp[8], ip[8];
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) {
+                        const float2 u0 = unpack_part<C::BF>(uw[2 * w]);
+                        const float2 u1 = unpack_part<C::BF>(uw[2 * w + 1]);
+                        // (wr + i wi)(tr + i s ti), s = -1 for w < 0
+                        rp[w] = pack_part<C::BF>(wr * u0.x - wis * u0.y, wr * u1.x - wis * u1.y, 0);
+                        ip[w] = pack_part<C::BF>(wrs * u0.y + wi * u0.x, wrs * u1.y + wi * u1.x, 0);
+                    }
+                    uint32_t rs[12], is[12];
+                    shift16(rp, lx & 7, rs);
+                    shift16(ip, lx & 7, is);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const int xq = j + ox8;
+                        if (xq < 4) {
+                            const uint32_t gb = xq * C::kSboB;
+                            st16(B + b_off + gb,
+                                 make_uint4(rs[4 * j], rs[4 * j + 1], rs[4 * j + 2], rs[4 * j + 3]));
+                            st16(B + b_off + gb + 4 * C::kSboB,
+                                 make_uint4(is[4 * j], is[4 * j + 1], is[4 * j + 2], is[4 * j + 3]));
+                        }
+                    }
+                } else {
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     const int xq = j + ox8;
@@ -659,15 +744,7 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                         float re[8], im[8];
 #pragma unroll
                         for (int f = 0; f < 4; ++f) {
-                            float4 u;
-                            if constexpr (C::U16) {
-                                const uint4 q = uh[j][f >> 1];
-                                const float2 t0 = unpack_part<C::BF>((f & 1) ? q.z : q.x);
-                                const float2 t1 = unpack_part<C::BF>((f & 1) ? q.w : q.y);
-                                u = make_float4(t0.x, t0.y, t1.x, t1.y);
-                            } else {
-                                u = ut[j][f];
-                            }
+                            const float4 u = ut[j][f];
                             // (wr + i wi)(tr + i s ti), s = -1 for w < 0
                             re[2 * f] = wr * u.x - wis * u.y;
                             im[2 * f] = wrs * u.y + wi * u.x;
@@ -690,6 +767,7 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                             st16(B + b_off + gb + 4 * C::kSboB, pi);
                         }
                     }
+                }
                 }
 #pragma unroll
                 for (int xq = 0; xq < 4; ++xq) {
