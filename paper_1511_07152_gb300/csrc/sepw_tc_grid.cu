@@ -237,92 +237,55 @@ __device__ __forceinline__ void st8(unsigned char *p, uint32_t a, uint32_t b)
     *reinterpret_cast<uint2 *>(p) = make_uint2(a, b);
 }
 
-// Per-call tables (layouts in the file comment).  vtab from the v-direction
-// taps (voff), utab from the u-direction taps.
+// Per-call tables (layouts in the file comment): unshifted rows per (plane,
+// oversample).  v (from the v-direction taps at voff): KV = 4 H uint4 =
+// [part h][component][8 words of tap pairs (2 w, 2 w + 1)], zero beyond S;
+// u: KU uint4 = 16 (re, im) 16-bit words (one-part forms) or 16 complex64
+// taps (hi + lo forms).
 template <int PREC>
 __global__ void tables_kernel(DevParams p, const float2 *__restrict__ taps, uint4 *vtab,
-                              float4 *utab)
+                              uint4 *utab)
 {
     constexpr int H = Cfg<PREC>::H;
     constexpr bool U16 = Cfg<PREC>::U16;
+    constexpr int KV = 4 * H, KU = U16 ? 4 : 8;
     const int64_t nrow = (int64_t)p.P * p.OS;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if constexpr (U16) {
-        // unshifted rows, 16-bit: v per (plane, oversample): [component][8
-        // words of tap pairs (2 w, 2 w + 1)]; u: 16 words of (re, im)
-        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nrow * 8;
-             e += stride) {
-            const int64_t row = e >> 3;
-            const int q = (int)(e & 7);
-            uint32_t w[4];
-            if (q < 4) {  // v: component q / 2, words 4 (q & 1) .. + 3
-                const float2 *tv = taps + p.voff + row * p.S;
-                const int comp = q >> 1;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nrow * (KV + KU);
+         e += stride) {
+        const int64_t row = e / (KV + KU);
+        const int q = (int)(e % (KV + KU));
+        uint32_t w[4];
+        if (q < KV) {
+            const int h = q >> 2, comp = (q >> 1) & 1, half = q & 1;
+            const float2 *tv = taps + p.voff + row * p.S;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int t0 = 2 * (4 * half + k);
+                const float a = t0 < p.S ? (comp ? tv[t0].y : tv[t0].x) : 0.f;
+                const float b = t0 + 1 < p.S ? (comp ? tv[t0 + 1].y : tv[t0 + 1].x) : 0.f;
+                w[k] = pack_part<Cfg<PREC>::BF>(a, b, h);
+            }
+            vtab[row * KV + q] = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+            const int qu = q - KV;
+            const float2 *tu = taps + row * p.S;
+            if constexpr (U16) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const int t0 = 2 * (4 * (q & 1) + k);
-                    const float a = t0 < p.S ? (comp ? tv[t0].y : tv[t0].x) : 0.f;
-                    const float b = t0 + 1 < p.S ? (comp ? tv[t0 + 1].y : tv[t0 + 1].x) : 0.f;
-                    w[k] = pack_part<Cfg<PREC>::BF>(a, b, 0);
-                }
-                vtab[row * 4 + q] = make_uint4(w[0], w[1], w[2], w[3]);
-            } else {  // u: taps 4 (q - 4) .. + 3 as (re, im)
-                const float2 *tu = taps + row * p.S;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int t0 = 4 * (q - 4) + k;
+                    const int t0 = 4 * qu + k;
                     const float2 t = t0 < p.S ? tu[t0] : make_float2(0.f, 0.f);
                     w[k] = pack_part<Cfg<PREC>::BF>(t.x, t.y, 0);
                 }
-                reinterpret_cast<uint4 *>(utab)[row * 4 + (q - 4)] = make_uint4(w[0], w[1], w[2], w[3]);
+            } else {
+                const float2 t0 = 2 * qu < p.S ? tu[2 * qu] : make_float2(0.f, 0.f);
+                const float2 t1 = 2 * qu + 1 < p.S ? tu[2 * qu + 1] : make_float2(0.f, 0.f);
+                w[0] = __float_as_uint(t0.x);
+                w[1] = __float_as_uint(t0.y);
+                w[2] = __float_as_uint(t1.x);
+                w[3] = __float_as_uint(t1.y);
             }
-        }
-        return;
-    }
-    const int64_t nv = nrow * 8 * H * 2 * 3;
-    const int64_t nu = nrow * 8 * 3 * 4;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv + nu; e += stride) {
-        if (e < nv) {
-            int64_t q = e;
-            const int j = (int)(q % 3);
-            q /= 3;
-            const int comp = (int)(q % 2);
-            q /= 2;
-            const int h = (int)(q % H);
-            q /= H;
-            const int s = (int)(q % 8);
-            q /= 8;
-            const float2 *row = taps + p.voff + q * p.S;
-            uint32_t w[4];
-#pragma unroll
-            for (int t2 = 0; t2 < 4; ++t2) {
-                float v[2];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int k = 8 * j - s + 2 * t2 + u;
-                    v[u] = (k >= 0 && k < p.S) ? (comp ? row[k].y : row[k].x) : 0.f;
-                }
-                w[t2] = pack_part<Cfg<PREC>::BF>(v[0], v[1], h);
-            }
-            vtab[e] = make_uint4(w[0], w[1], w[2], w[3]);
-        } else {
-            int64_t q = e - nv;
-            const int f = (int)(q % 4);
-            q /= 4;
-            const int j = (int)(q % 3);
-            q /= 3;
-            const int s = (int)(q % 8);
-            q /= 8;
-            const float2 *row = taps + q * p.S;
-            float o[4];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int k = 8 * j - s + 2 * f + u;
-                const float2 t = (k >= 0 && k < p.S) ? row[k] : make_float2(0.f, 0.f);
-                o[2 * u] = t.x;
-                o[2 * u + 1] = t.y;
-            }
-            utab[e - nv] = make_float4(o[0], o[1], o[2], o[3]);
+            utab[row * KU + qu] = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
@@ -411,7 +374,7 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
     DevParams p, const WorkItem *__restrict__ items, const int32_t *__restrict__ nitems,
     const uint64_t *__restrict__ rec, const int32_t *__restrict__ perm,
     const float2 *__restrict__ vis, const float *__restrict__ weight,
-    const uint4 *__restrict__ vtab, const float4 *__restrict__ utab,
+    const uint4 *__restrict__ vtab, const uint4 *__restrict__ utab,
     const float2 *__restrict__ taps, const int32_t *__restrict__ item_exp, float2 *grid,
     int32_t *status, TcControl ctl)
 {
@@ -590,11 +553,11 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                             st8(Bk + roff(xq), 0u, 0u);
                     }
                 } else {
-                // this slot's taps and value
-                uint4 va[H][2][3];  // pre-shifted v chunks (hi + lo forms)
-                float4 ut[3][4];    // FP32 u-taps, pre-shifted (hi + lo forms)
-                uint4 vq[4];        // one-part forms: unshifted v words [component][8]
-                uint4 uq[4];        // one-part forms: 16 unshifted (re, im) u words
+                // this slot's taps and value: unshifted table rows (v: 16-bit
+                // words [h][component][8]; u: 16 (re, im) 16-bit words for the
+                // one-part forms, 16 complex64 taps for the hi + lo forms)
+                uint4 vq[H][4];
+                uint4 uq[C::U16 ? 4 : 8];
                 float2 x = make_float2(0.f, 0.f);
                 float wt = 0.f;
                 int lx = 0, ly = 0;
@@ -612,53 +575,17 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                     ly = rec_ly(r[sl]);
                     cjm = rec_conj(r[sl]) ? 0x80008000u : 0u;
                     const int64_t row = (int64_t)rec_plane(r[sl]) * p.OS;
-                    if constexpr (C::U16) {
-                        // unshifted 64-byte rows, shifted in registers below
-                        const uint4 *pv = vtab + (row + rec_ov(r[sl])) * 4;
-                        const uint4 *pu = reinterpret_cast<const uint4 *>(utab) +
-                                          (row + rec_ou(r[sl])) * 4;
-                        ldg32(pv, vq[0], vq[1]);
-                        ldg32(pv + 2, vq[2], vq[3]);
-                        ldg32(pu, uq[0], uq[1]);
-                        ldg32(pu + 2, uq[2], uq[3]);
-                    } else {
-                        const uint4 *pa = vtab + ((row + rec_ov(r[sl])) * 8 + (ly & 7)) * (H * 6);
-                        const int64_t urow = (row + rec_ou(r[sl])) * 8 + (lx & 7);
-                        // the row's 6 H chunks ([h][component][j]) in 32-byte loads
+                    const uint4 *pv = vtab + (row + rec_ov(r[sl])) * (4 * H);
 #pragma unroll
-                        for (int h = 0; h < H; ++h) {
-                            ldg32(pa + h * 6, va[h][0][0], va[h][0][1]);
-                            ldg32(pa + h * 6 + 2, va[h][0][2], va[h][1][0]);
-                            ldg32(pa + h * 6 + 4, va[h][1][1], va[h][1][2]);
-                        }
-                        const float4 *pu = utab + urow * 12;
-#pragma unroll
-                        for (int j = 0; j < 3; ++j)
-#pragma unroll
-                            for (int f = 0; f < 4; f += 2) {
-                                uint4 a, bb;
-                                ldg32(pu + j * 4 + f, a, bb);
-                                ut[j][f] = make_float4(__uint_as_float(a.x), __uint_as_float(a.y),
-                                                       __uint_as_float(a.z), __uint_as_float(a.w));
-                                ut[j][f + 1] =
-                                    make_float4(__uint_as_float(bb.x), __uint_as_float(bb.y),
-                                                __uint_as_float(bb.z), __uint_as_float(bb.w));
-                            }
+                    for (int h = 0; h < H; ++h) {
+                        ldg32(pv + 4 * h, vq[h][0], vq[h][1]);
+                        ldg32(pv + 4 * h + 2, vq[h][2], vq[h][3]);
                     }
-                }
-                if constexpr (C::U16) {
-                    // v chunks at row offset ly mod 8, from the unshifted words
+                    constexpr int kU = C::U16 ? 4 : 8;  // uint4 per u row
+                    const uint4 *pu = reinterpret_cast<const uint4 *>(utab) + (row + rec_ou(r[sl])) * kU;
 #pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const uint32_t in[8] = {vq[2 * c].x, vq[2 * c].y, vq[2 * c].z, vq[2 * c].w,
-                                                vq[2 * c + 1].x, vq[2 * c + 1].y, vq[2 * c + 1].z,
-                                                vq[2 * c + 1].w};
-                        uint32_t o[12];
-                        shift16(in, ly & 7, o);
-#pragma unroll
-                        for (int j = 0; j < 3; ++j)
-                            va[0][c][j] = make_uint4(o[4 * j], o[4 * j + 1], o[4 * j + 2], o[4 * j + 3]);
-                    }
+                    for (int k = 0; k < kU; k += 2)
+                        ldg32(pu + k, uq[k], uq[k + 1]);
                 }
                 if (sl == 0) {
                     // the pair's next stage: its records and indices now
@@ -677,107 +604,81 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                 // byte offsets of this slot's K row in A and B (chunk row 0)
                 const uint32_t a_off = (i >> 3) * C::kLboA + (i & 7) * 16;
                 const uint32_t b_off = (i >> 3) * C::kLboB + (i & 7) * 16;
-                // A: chunk j of part h goes to chunk row j + ly / 8 of the
-                // (h, re) and (h, im) row blocks
+                // A: the v words of part h, component c, shifted to the row
+                // offset ly mod 8; chunk j goes to chunk row j + ly / 8 of the
+                // (h, c) row block
                 const int oy8 = valid ? (ly >> 3) : 8;
 #pragma unroll
                 for (int h = 0; h < H; ++h) {
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        const int xq = j + oy8;
-                        if (xq < 4) {
-                            const uint32_t g0 = (h * 8 + xq) * kSboA;
-                            st16(A + a_off + g0, va[h][0][j]);
-                            st16(A + a_off + g0 + 4 * kSboA, xor4(va[h][1][j], cjm));  // conj(a), w < 0
-                        }
-                    }
+                    for (int c = 0; c < 2; ++c) {
+                        const uint32_t in[8] = {vq[h][2 * c].x,     vq[h][2 * c].y,
+                                                vq[h][2 * c].z,     vq[h][2 * c].w,
+                                                vq[h][2 * c + 1].x, vq[h][2 * c + 1].y,
+                                                vq[h][2 * c + 1].z, vq[h][2 * c + 1].w};
+                        uint32_t o[12];
+                        shift16(in, ly & 7, o);
+                        const uint32_t m = c ? cjm : 0u;  // conj(a) for w < 0
 #pragma unroll
-                    for (int xq = 0; xq < 4; ++xq) {
-                        if (xq < oy8 || xq > oy8 + 2) {
-                            const uint32_t g0 = (h * 8 + xq) * kSboA;
-                            st16(A + a_off + g0, z);
-                            st16(A + a_off + g0 + 4 * kSboA, z);
+                        for (int j = 0; j < 3; ++j) {
+                            const int xq = j + oy8;
+                            if (xq < 4)
+                                st16(A + a_off + (h * 8 + 4 * c + xq) * kSboA,
+                                     make_uint4(o[4 * j] ^ m, o[4 * j + 1] ^ m, o[4 * j + 2] ^ m,
+                                                o[4 * j + 3] ^ m));
                         }
+#pragma unroll
+                        for (int xq = 0; xq < 4; ++xq)
+                            if (xq < oy8 || xq > oy8 + 2)
+                                st16(A + a_off + (h * 8 + 4 * c + xq) * kSboA, z);
                     }
                 }
-                // B: W V times the u-taps, chunk j to chunk row j + lx / 8 of the
-                // (g, re) and (g, im) column blocks
+                // B: W V times the u-taps (FP32), each split part g rounded and
+                // packed in pairs, shifted to the column offset lx mod 8; chunk j
+                // to chunk row j + lx / 8 of the (g, re) and (g, im) blocks
                 const int ox8 = valid ? (lx >> 3) : 8;
                 const float wr = (wt * x.x) * scale;  // exact power-of-two scaling
                 const float wi = (wt * x.y) * scale;
                 const float wis = cjm ? -wi : wi;      // conj(u-taps) for w < 0
                 const float wrs = cjm ? -wr : wr;
-                if constexpr (C::U16) {
-                    // all 16 products, rounded, packed in pairs and shifted to
-                    // the column offset lx mod 8
-                    const uint32_t uw[16] = {uq[0].x, uq[0].y, uq[0].z, uq[0].w, uq[1].x, uq[1].y,
-                                             uq[1].z, uq[1].w, uq[2].x, uq[2].y, uq[2].z, uq[2].w,
-                                             uq[3].x, uq[3].y, uq[3].z, uq[3].w};
-                    uint32_t rp[8], ip[8];
+                float re[16], im[16];
 #pragma unroll
-                    for (int w = 0; w < 8; ++w) {
-                        const float2 u0 = unpack_part<C::BF>(uw[2 * w]);
-                        const float2 u1 = unpack_part<C::BF>(uw[2 * w + 1]);
-                        // (wr + i wi)(tr + i s ti), s = -1 for w < 0
-                        rp[w] = pack_part<C::BF>(wr * u0.x - wis * u0.y, wr * u1.x - wis * u1.y, 0);
-                        ip[w] = pack_part<C::BF>(wrs * u0.y + wi * u0.x, wrs * u1.y + wi * u1.x, 0);
+                for (int e = 0; e < 16; ++e) {
+                    float2 u;
+                    if constexpr (C::U16) {
+                        const uint4 q = uq[e >> 2];
+                        u = unpack_part<C::BF>((e & 3) == 0 ? q.x : (e & 3) == 1 ? q.y
+                                                     : (e & 3) == 2 ? q.z : q.w);
+                    } else {
+                        const uint4 q = uq[e >> 1];
+                        u = (e & 1) ? make_float2(__uint_as_float(q.z), __uint_as_float(q.w))
+                                    : make_float2(__uint_as_float(q.x), __uint_as_float(q.y));
                     }
-                    uint32_t rs[12], is[12];
-                    shift16(rp, lx & 7, rs);
-                    shift16(ip, lx & 7, is);
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        const int xq = j + ox8;
-                        if (xq < 4) {
-                            const uint32_t gb = xq * C::kSboB;
-                            st16(B + b_off + gb,
-                                 make_uint4(rs[4 * j], rs[4 * j + 1], rs[4 * j + 2], rs[4 * j + 3]));
-                            st16(B + b_off + gb + 4 * C::kSboB,
-                                 make_uint4(is[4 * j], is[4 * j + 1], is[4 * j + 2], is[4 * j + 3]));
-                        }
-                    }
-                } else {
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const int xq = j + ox8;
-                    if (xq < 4) {
-                        float re[8], im[8];
-#pragma unroll
-                        for (int f = 0; f < 4; ++f) {
-                            const float4 u = ut[j][f];
-                            // (wr + i wi)(tr + i s ti), s = -1 for w < 0
-                            re[2 * f] = wr * u.x - wis * u.y;
-                            im[2 * f] = wrs * u.y + wi * u.x;
-                            re[2 * f + 1] = wr * u.z - wis * u.w;
-                            im[2 * f + 1] = wrs * u.w + wi * u.z;
-                        }
-#pragma unroll
-                        for (int g = 0; g < H; ++g) {
-                            uint4 pr, pi;
-                            pr.x = pack_part<C::BF>(re[0], re[1], g);
-                            pr.y = pack_part<C::BF>(re[2], re[3], g);
-                            pr.z = pack_part<C::BF>(re[4], re[5], g);
-                            pr.w = pack_part<C::BF>(re[6], re[7], g);
-                            pi.x = pack_part<C::BF>(im[0], im[1], g);
-                            pi.y = pack_part<C::BF>(im[2], im[3], g);
-                            pi.z = pack_part<C::BF>(im[4], im[5], g);
-                            pi.w = pack_part<C::BF>(im[6], im[7], g);
-                            const uint32_t gb = (g * 8 + xq) * C::kSboB;
-                            st16(B + b_off + gb, pr);
-                            st16(B + b_off + gb + 4 * C::kSboB, pi);
-                        }
-                    }
-                }
+                    // (wr + i wi)(tr + i s ti), s = -1 for w < 0
+                    re[e] = wr * u.x - wis * u.y;
+                    im[e] = wrs * u.y + wi * u.x;
                 }
 #pragma unroll
-                for (int xq = 0; xq < 4; ++xq) {
-                    if (xq < ox8 || xq > ox8 + 2) {
+                for (int g = 0; g < H; ++g) {
 #pragma unroll
-                        for (int g = 0; g < H; ++g) {
-                            const uint32_t gb = (g * 8 + xq) * C::kSboB;
-                            st16(B + b_off + gb, z);
-                            st16(B + b_off + gb + 4 * C::kSboB, z);
+                    for (int c = 0; c < 2; ++c) {
+                        const float *v = c ? im : re;
+                        uint32_t pk[8], o[12];
+#pragma unroll
+                        for (int w = 0; w < 8; ++w)
+                            pk[w] = pack_part<C::BF>(v[2 * w], v[2 * w + 1], g);
+                        shift16(pk, lx & 7, o);
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            const int xq = j + ox8;
+                            if (xq < 4)
+                                st16(B + b_off + (g * 8 + 4 * c + xq) * C::kSboB,
+                                     make_uint4(o[4 * j], o[4 * j + 1], o[4 * j + 2], o[4 * j + 3]));
                         }
+#pragma unroll
+                        for (int xq = 0; xq < 4; ++xq)
+                            if (xq < ox8 || xq > ox8 + 2)
+                                st16(B + b_off + (g * 8 + 4 * c + xq) * C::kSboB, z);
                     }
                 }
                 }
@@ -979,12 +880,13 @@ cudaError_t launch_prec(const DevParams &p, const Plan &plan, const float2 *vis,
 {
     using C = Cfg<PREC>;
     const int64_t nrow = (int64_t)p.P * p.OS;
+    constexpr int KV = 4 * C::H, KU = C::U16 ? 4 : 8;  // uint4 per v and u row
     uint4 *vtab = reinterpret_cast<uint4 *>(tables);
-    float4 *utab = reinterpret_cast<float4 *>(vtab + nrow * 8 * C::H * 2 * 3);
-    int32_t *item_exp = reinterpret_cast<int32_t *>(utab + nrow * 8 * 3 * 4);
+    uint4 *utab = vtab + nrow * KV;
+    int32_t *item_exp = reinterpret_cast<int32_t *>(utab + nrow * KU);
     cudaError_t e;
     if constexpr (!C::TF32) {  // TF32 reads the caller's taps directly
-        const int64_t n = nrow * 8 * (C::H * 6 + 12);
+        const int64_t n = nrow * (KV + KU);
         const int nb = (int)std::min<int64_t>((n + 255) / 256, 4096);
         tables_kernel<PREC><<<nb, 256, 0, s>>>(p, taps, vtab, utab);
         if ((e = cudaGetLastError()) != cudaSuccess)
@@ -1015,9 +917,9 @@ int tc2_tile_for_support(int S)
 
 size_t tc2_tables_bytes(const DevParams &p, int64_t items_capacity)
 {
-    // vtab sized for the two-part forms (2 * 6 chunks per (plane, oversample,
-    // shift)), utab 12 float4, then one exponent per work item
-    return (size_t)p.P * p.OS * 8 * (2 * 6 + 12) * 16 +
+    // v and u rows sized for the hi + lo forms (8 + 8 uint4 per (plane,
+    // oversample)), then one exponent per work item
+    return (size_t)p.P * p.OS * (8 + 8) * 16 +
            sizeof(int32_t) * (size_t)std::max<int64_t>(items_capacity, 1);
 }
 
