@@ -260,9 +260,10 @@ __global__ void __launch_bounds__(kSortThreads) item_sort_kernel(
     __shared__ uint64_t s_rec[kChunk];
     __shared__ int32_t s_perm[kChunk];
     __shared__ int32_t s_wsum[32];
-    const int item = blockIdx.x;
-    if (item >= *nitems)
-        return;
+    // blocks stride over the plan's items (sparse plans have far fewer items
+    // than their capacity, so the grid is sized by the SM count, not by it)
+    const int n_items = *nitems;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     const WorkItem it = items[item];
     const int n = it.count;
     const int E = (p.T + 3) / 4;
@@ -352,6 +353,8 @@ __global__ void __launch_bounds__(kSortThreads) item_sort_kernel(
             perm[it.start + dst] = s_perm[q];
         }
     }
+    __syncthreads();  // shared memory is reused by the next item
+    }
 }
 
 // Degridding writes 0 for every dropped visibility of the plan.
@@ -402,6 +405,12 @@ cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
             plan.d_perm, plan.d_rec);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
+        // the per-item sort by (sub-block, conj, origin) serves the kernels
+        // that walk runs of one origin (the tiled FP32 gridder and
+        // degridder); the BF16 and FP16 tensor-core forms grid and degrid
+        // in any order within an item and skip it
+        if (plan.form == SEPW_FORM_TC_BF16 || plan.form == SEPW_FORM_TC_FP16)
+            return cudaSuccess;
         const int E = (p.T + 3) / 4;
         const int nb = 32 * E * E;
         const size_t shm =
@@ -410,8 +419,13 @@ cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
                                  (int)shm);
         if (e != cudaSuccess)
             return e;
-        item_sort_kernel<<<plan.items_capacity, kSortThreads, shm, s>>>(
-            p, plan.d_items, plan.d_nitems, plan.d_perm, plan.d_rec);
+        int dev = 0, sms = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return e;
+        const int nblk = std::max(1, std::min(plan.items_capacity, 16 * sms));
+        item_sort_kernel<<<nblk, kSortThreads, shm, s>>>(p, plan.d_items, plan.d_nitems,
+                                                         plan.d_perm, plan.d_rec);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
     }
