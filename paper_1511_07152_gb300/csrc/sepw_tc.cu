@@ -17,12 +17,12 @@
 // component is below 1 (the producers find it while they load the window).
 //
 // Operands are K-major (8 K elements, one row of a core matrix, in 16 bytes):
-//   - A, per stage, from a table built per call: per (plane, oversample,
-//     row offset mod 4) five 16-byte chunks of (re, im) pairs of the v-taps,
-//     pre-shifted so that chunk j holds rows 4 j .. 4 j + 3 of a footprint
-//     starting at row offset ly (mod 4).  A visibility's row of A is eight
-//     16-byte stores: chunk j at K chunk j + ly / 4, zeros elsewhere, so no
-//     row needs clearing.  Slot i of a stage is row i; the 8 lanes of a
+//   - A, per stage, from a table built per call: per (plane, oversample)
+//     the S v-taps as (re, im) pairs in the 16-bit format (64 bytes), shifted
+//     in registers by ly mod 4 words into five 16-byte chunks, chunk j holding
+//     rows 4 j .. 4 j + 3 of the footprint relative to 4 (ly / 4).  A
+//     visibility's row of A is eight 16-byte stores: chunk j at K chunk
+//     j + ly / 4, zeros elsewhere, so no row needs clearing.  Slot i of a stage is row i; the 8 lanes of a
 //     quarter warp write 8 different rows of one core matrix column: no bank
 //     conflicts, whatever chunk each lane writes.
 //   - B, the window, once per item, two 4-byte (re, im) pairs per cell.
@@ -77,7 +77,7 @@ constexpr uint32_t kDgSbo = (kDgK / 8) * 128;    // 8-row groups
 constexpr int kDgABytes = kDgVis * kDgK * 2;     // 16 KiB
 constexpr int kDgBBytes = kDgN * kDgK * 2;       // 8 KiB
 constexpr uint32_t kDgTmemCols = kDgGroups * kDgN;  // two accumulators
-constexpr int kDgVChunks = 6;   // v-table chunks per row: 5 used, 1 pad (32-byte loads)
+constexpr int kDgVChunks = 4;   // v-table chunks per row: 16 (re, im) pairs, unshifted
 constexpr int kDgUChunks = 4;   // u-table chunks per row: 16 (re, im) pairs
 constexpr size_t kDgSmem = 2 * (size_t)kDgABytes + 2 * (size_t)kDgBBytes + 16 * sizeof(uint64_t);
 static_assert(kDgSmem <= 227 * 1024, "shared memory per CTA");
@@ -140,7 +140,7 @@ DgTables dg_tables(const DevParams &p, void *base)
     unsigned char *b = reinterpret_cast<unsigned char *>(base);
     DgTables t;
     t.vtab = reinterpret_cast<uint4 *>(b);
-    t.utab = t.vtab + nrow * 4 * kDgVChunks;
+    t.utab = t.vtab + nrow * kDgVChunks;
     return t;
 }
 
@@ -150,19 +150,18 @@ __global__ void dg_tables_kernel(DevParams p, const float2 *__restrict__ taps, u
                                  uint4 *utab)
 {
     const int64_t nrow = (int64_t)p.P * p.OS;
-    const int64_t nv = nrow * 4 * kDgVChunks, nu = nrow * kDgUChunks;
+    const int64_t nv = nrow * kDgVChunks, nu = nrow * kDgUChunks;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nv + nu; e += stride) {
         uint32_t w[4];
         if (e < nv) {
             const int j = (int)(e % kDgVChunks);
-            const int s = (int)((e / kDgVChunks) % 4);
-            const int64_t row = e / (kDgVChunks * 4);
+            const int64_t row = e / kDgVChunks;
             const float2 *tv = taps + p.voff + row * p.S;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int k = 4 * j - s + q;  // tap of window row 4 j + q (offset s)
-                const float2 t = (j < 5 && k >= 0 && k < p.S) ? tv[k] : make_float2(0.f, 0.f);
+                const int k = 4 * j + q;
+                const float2 t = k < p.S ? tv[k] : make_float2(0.f, 0.f);
                 w[q] = pack_pair<PREC>(t.x, t.y);
             }
             vtab[e] = make_uint4(w[0], w[1], w[2], w[3]);
@@ -352,7 +351,7 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
                 const int t = tg + st;  // t mod 2 == grp
                 const uint64_t rnext = rec_of(st + 2);
                 const bool valid = rcur != ~0ull;  // no record has its top bits set
-                uint4 c[kDgVChunks];
+                uint4 c4[4];  // the 16 unshifted (re, im) v-tap words
                 int ly = 0;
                 uint32_t cjm = 0;
                 if (valid) {
@@ -360,17 +359,31 @@ __global__ void __launch_bounds__(kDgBlock, 1) degrid_tc_kernel(
                     ly = rec_ly(r);
                     cjm = rec_conj(r) ? 0x80000000u : 0u;  // conj(a): the im halves
                     const uint4 *pv =
-                        vtab + (((int64_t)rec_plane(r) * p.OS + rec_ov(r)) * 4 + (ly & 3)) *
-                                   kDgVChunks;
-                    ldg32(pv, c[0], c[1]);
-                    ldg32(pv + 2, c[2], c[3]);
-                    ldg32(pv + 4, c[4], c[5]);
+                        vtab + ((int64_t)rec_plane(r) * p.OS + rec_ov(r)) * kDgVChunks;
+                    ldg32(pv, c4[0], c4[1]);
+                    ldg32(pv + 2, c4[2], c4[3]);
                 }
                 // buffer grp held stage t - 2: wait for its MMAs
                 if (t >= 2)
                     warp_wait(done + grp, ((t - 2) >> 1) & 1);
                 tc_fence_after();
                 const int oy4 = valid ? (ly >> 2) : 8;
+                // shift the words by ly mod 4: word q of chunk j holds the tap
+                // of window row 4 (j + ly / 4) + q
+                uint32_t tw[20];
+#pragma unroll
+                for (int k = 0; k < 20; ++k)
+                    tw[k] = k < 16 ? (&c4[k >> 2].x)[k & 3] : 0u;
+#pragma unroll
+                for (int k = 19; k >= 0; --k)
+                    tw[k] = (ly & 2) ? (k >= 2 ? tw[k - 2] : 0u) : tw[k];
+#pragma unroll
+                for (int k = 19; k >= 0; --k)
+                    tw[k] = (ly & 1) ? (k >= 1 ? tw[k - 1] : 0u) : tw[k];
+                uint4 c[5];
+#pragma unroll
+                for (int j = 0; j < 5; ++j)
+                    c[j] = make_uint4(tw[4 * j], tw[4 * j + 1], tw[4 * j + 2], tw[4 * j + 3]);
 #pragma unroll
                 for (int j = 0; j < 5; ++j) {
                     const int ca = j + oy4;  // K chunk of table chunk j
@@ -547,7 +560,7 @@ cudaError_t launch_degrid_tc_S(const DevParams &p, const Plan &plan, const float
 {
     const DgTables t = dg_tables(p, tables);
     const int64_t nrow = (int64_t)p.P * p.OS;
-    const int64_t n = nrow * (4 * kDgVChunks + kDgUChunks);
+    const int64_t n = nrow * (kDgVChunks + kDgUChunks);
     dg_tables_kernel<PREC><<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(
         p, taps, t.vtab, t.utab);
     cudaError_t e = cudaGetLastError();
@@ -569,7 +582,7 @@ size_t tc_degrid_tables_bytes(const DevParams &p, int64_t items_capacity)
 {
     (void)items_capacity;
     const size_t nrow = (size_t)p.P * p.OS;
-    return align256(nrow * (4 * kDgVChunks + kDgUChunks) * 16);
+    return align256(nrow * (kDgVChunks + kDgUChunks) * 16);
 }
 
 cudaError_t launch_degrid_tc(const DevParams &p, const Plan &plan, const float2 *grid,
