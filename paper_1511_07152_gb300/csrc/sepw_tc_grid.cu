@@ -107,10 +107,10 @@ struct Cfg {
     static constexpr bool SCALED = PREC == 1 || PREC == 2;
     static constexpr bool BF = PREC == 0 || PREC == 3;
     // TF32: K-major operands of 4-byte elements (MN-major TF32 operands gave
-    // zeros on the GB300), written from the caller's taps; K = 8 per MMA
+    // zeros on the GB300); K = 8 per MMA
     static constexpr bool TF32 = PREC == 4;
-    // N: columns (g, d, x), 64 H; TF32: x only
-    static constexpr int N = TF32 ? 32 : 64 * H;
+    // N: columns (g, d, x)
+    static constexpr int N = 64 * H;
     // M = 64 H rows: (h, c, y).  An M = 64 accumulator puts row m in tensor-
     // memory lane 32 (m / 16) + m % 16 (measured), the first 16 lanes of each
     // warp quarter.
@@ -118,22 +118,23 @@ struct Cfg {
     static constexpr int SV = 32 * kWps;                   // visibilities per stage
     static constexpr int SLOTS = 1;                        // per lane
     // core matrices along K per stage: 8 visibilities each (16-bit forms), or
-    // 4 K elements = 2 visibilities (TF32)
-    static constexpr int KG = TF32 ? SV / 2 : SV / 8;
-    static constexpr int VPK = TF32 ? 4 : 16;              // visibilities per MMA
-    // values and weights loaded one stage ahead (the one-part 16-bit forms;
-    // the others have no registers to spare: measured slower)
-    static constexpr bool PRE = H == 1 && !TF32;
+    // 4 (TF32)
+    static constexpr int KG = TF32 ? SV / 4 : SV / 8;
+    static constexpr int VPK = TF32 ? 8 : 16;              // visibilities per MMA
+    // values and weights loaded one stage ahead (the one-part forms; the hi +
+    // lo forms have no registers to spare: measured slower)
+    static constexpr bool PRE = H == 1;
     // u-side table in the 16-bit format (the one-part forms: W V times the
     // rounded taps, rounded again); FP32 for the hi + lo forms
     static constexpr bool U16 = H == 1 && !TF32;
     // K-adjacent core matrices: 128-byte aligned for the 16-bit forms; TF32
-    // pads by 16 bytes (its lanes store 8 bytes along K)
+    // pads by 16 bytes, so that 32 lanes storing 4 bytes of one row each
+    // (four lanes a core-matrix row) hit eight different 16-byte bank groups
     static constexpr uint32_t kPad = TF32 ? 16 : 0;
     static constexpr uint32_t kLboA = (M / 8) * 128 + kPad;
     static constexpr int kABytes = KG * kLboA;
-    // staged accumulator row: (d, x) summed over g, or x (TF32); padded
-    static constexpr int kStgStride = TF32 ? 33 : 65;
+    // staged accumulator row: (d, x) summed over g; padded
+    static constexpr int kStgStride = 65;
     static constexpr int kStgBytes = M * kStgStride * 4;
     static constexpr uint32_t kSboB = 128;
     static constexpr uint32_t kLboB = (N / 8) * 128 + kPad;
@@ -202,12 +203,6 @@ __device__ __forceinline__ void shift16(const uint32_t (&in)[8], int s, uint32_t
         out[w] = (s & 1) ? __byte_perm(w >= 1 ? t[w - 1] : 0u, t[w], 0x5432) : t[w];
 }
 
-// sign flip of the 16-bit values of a chunk selected by mask (exact)
-__device__ __forceinline__ uint4 xor4(uint4 v, uint32_t m)
-{
-    return make_uint4(v.x ^ m, v.y ^ m, v.z ^ m, v.w ^ m);
-}
-
 __device__ __forceinline__ void st16(unsigned char *p, uint4 v)
 {
     *reinterpret_cast<uint4 *>(p) = v;
@@ -232,23 +227,43 @@ __device__ __forceinline__ uint32_t to_tf32(float x)
     return r;
 }
 
-__device__ __forceinline__ void st8(unsigned char *p, uint32_t a, uint32_t b)
+__device__ __forceinline__ void st4(unsigned char *p, uint32_t a)
 {
-    *reinterpret_cast<uint2 *>(p) = make_uint2(a, b);
+    *reinterpret_cast<uint32_t *>(p) = a;
+}
+
+// byte offset of row m of a K-major core-matrix column (8 rows of 16 bytes,
+// 8-row groups 128 bytes apart)
+__device__ __forceinline__ uint32_t tf32_row_off(int m)
+{
+    return (uint32_t)((m & 7) * 16 + (m >> 3) * 128);
+}
+
+// v[k] <- v[k - s] (zero below s), s = 0..31: one conditional shift per bit
+__device__ __forceinline__ void shift_right32(float (&v)[32], int s)
+{
+#pragma unroll
+    for (int b = 4; b >= 0; --b) {
+        const int sh = 1 << b;
+        const bool on = (s >> b) & 1;
+#pragma unroll
+        for (int k = 31; k >= 0; --k)
+            v[k] = on ? (k >= sh ? v[k - sh] : 0.f) : v[k];
+    }
 }
 
 // Per-call tables (layouts in the file comment): unshifted rows per (plane,
 // oversample).  v (from the v-direction taps at voff): KV = 4 H uint4 =
-// [part h][component][8 words of tap pairs (2 w, 2 w + 1)], zero beyond S;
-// u: KU uint4 = 16 (re, im) 16-bit words (one-part forms) or 16 complex64
-// taps (hi + lo forms).
+// [part h][component][8 words of tap pairs (2 w, 2 w + 1)], zero beyond S,
+// or 16 complex64 taps (TF32); u: KU uint4 = 16 (re, im) 16-bit words
+// (one-part 16-bit forms) or 16 complex64 taps (hi + lo forms, TF32).
 template <int PREC>
 __global__ void tables_kernel(DevParams p, const float2 *__restrict__ taps, uint4 *vtab,
                               uint4 *utab)
 {
     constexpr int H = Cfg<PREC>::H;
-    constexpr bool U16 = Cfg<PREC>::U16;
-    constexpr int KV = 4 * H, KU = U16 ? 4 : 8;
+    constexpr bool U16 = Cfg<PREC>::U16, TF32 = Cfg<PREC>::TF32;
+    constexpr int KV = TF32 ? 8 : 4 * H, KU = U16 ? 4 : 8;
     const int64_t nrow = (int64_t)p.P * p.OS;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nrow * (KV + KU);
@@ -256,7 +271,13 @@ __global__ void tables_kernel(DevParams p, const float2 *__restrict__ taps, uint
         const int64_t row = e / (KV + KU);
         const int q = (int)(e % (KV + KU));
         uint32_t w[4];
-        if (q < KV) {
+        if (TF32 && q < KV) {  // complex64 v taps 2 q, 2 q + 1
+            const float2 *tv = taps + p.voff + row * p.S;
+            const float2 t0 = 2 * q < p.S ? tv[2 * q] : make_float2(0.f, 0.f);
+            const float2 t1 = 2 * q + 1 < p.S ? tv[2 * q + 1] : make_float2(0.f, 0.f);
+            vtab[row * KV + q] = make_uint4(__float_as_uint(t0.x), __float_as_uint(t0.y),
+                                            __float_as_uint(t1.x), __float_as_uint(t1.y));
+        } else if (q < KV) {
             const int h = q >> 2, comp = (q >> 1) & 1, half = q & 1;
             const float2 *tv = taps + p.voff + row * p.S;
 #pragma unroll
@@ -482,27 +503,28 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
             for (int sl = 0; sl < C::SLOTS; ++sl) {
                 const int i = slot0 + 32 * sl + lane;  // slot in the stage
                 if constexpr (C::TF32) {
-                    // K-major, 4-byte elements: slot i's two K elements (re, im
-                    // components) are 8 adjacent bytes of every row
-                    float2 tv[16], tu[16];
+                    // K-major, 4-byte elements: slot i is K = i; its column of A
+                    // (rows (c, y)) and row of B (columns (d, x)) are one 4-byte
+                    // element in each of 64 rows, which all lanes store together
+                    uint4 vq[8], uq[8];  // 16 complex64 v- and u-taps, unshifted
                     float2 x = make_float2(0.f, 0.f);
                     float wt = 0.f;
-                    int lx = 64, ly = 64;
+                    int lx = 0, ly = 0;
                     bool cj = false;
                     const bool valid = vi[sl] >= 0;
                     if (valid) {
-                        x = __ldg(vis + vi[sl]);
-                        wt = weight ? __ldg(weight + vi[sl]) : 1.0f;
+                        x = xv[sl];
+                        wt = wv[sl];
                         lx = rec_lx(r[sl]);
                         ly = rec_ly(r[sl]);
                         cj = rec_conj(r[sl]);
                         const int64_t row = (int64_t)rec_plane(r[sl]) * p.OS;
-                        const float2 *pv = taps + p.voff + (row + rec_ov(r[sl])) * p.S;
-                        const float2 *pu = taps + (row + rec_ou(r[sl])) * p.S;
+                        const uint4 *pv = vtab + (row + rec_ov(r[sl])) * 8;
+                        const uint4 *pu = utab + (row + rec_ou(r[sl])) * 8;
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            tv[j] = j < p.S ? __ldg(pv + j) : make_float2(0.f, 0.f);
-                            tu[j] = j < p.S ? __ldg(pu + j) : make_float2(0.f, 0.f);
+                        for (int k = 0; k < 8; k += 2) {
+                            ldg32(pv + k, vq[k], vq[k + 1]);
+                            ldg32(pu + k, uq[k], uq[k + 1]);
                         }
                     }
                     if (sl == 0) {
@@ -518,39 +540,48 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                         tc_fence_after();
                     }
                     // element (m, k) at (k % 4) 4 + (k / 4) LBO + (m % 8) 16 + (m / 8) 128
-                    unsigned char *const Ak = A + (i & 1) * 8 + (i >> 1) * C::kLboA;
-                    unsigned char *const Bk = B + (i & 1) * 8 + (i >> 1) * C::kLboB;
-                    auto roff = [](int m) { return (uint32_t)((m & 7) * 16 + (m >> 3) * 128); };
-                    const int S = p.S;
+                    unsigned char *const Ak = A + (i & 3) * 4 + (i >> 2) * C::kLboA;
+                    unsigned char *const Bk = B + (i & 3) * 4 + (i >> 2) * C::kLboB;
+                    auto tap = [](const uint4 (&q)[8], int j) {  // complex tap j
+                        const uint4 w = q[j >> 1];
+                        return (j & 1) ? make_float2(__uint_as_float(w.z), __uint_as_float(w.w))
+                                       : make_float2(__uint_as_float(w.x), __uint_as_float(w.y));
+                    };
+                    // A: component c of a (conj for w < 0) at rows ly .. ly + S - 1
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        if (valid && j < S) {
-                            const int y = ly + j;  // rows (0, y): re of G, (1, y): im
-                            const float ar = tv[j].x, ai = cj ? -tv[j].y : tv[j].y;
-                            st8(Ak + roff(y), to_tf32(ar), to_tf32(-ai));
-                            st8(Ak + roff(32 + y), to_tf32(ai), to_tf32(ar));
-                        }
-                    }
+                    for (int c = 0; c < 2; ++c) {
+                        float col[32];
 #pragma unroll
-                    for (int y = 0; y < 32; ++y) {
-                        if (y < ly || y >= ly + S) {
-                            st8(Ak + roff(y), 0u, 0u);
-                            st8(Ak + roff(32 + y), 0u, 0u);
+                        for (int j = 0; j < 32; ++j) {
+                            const float2 a = j < 16 ? tap(vq, j) : make_float2(0.f, 0.f);
+                            col[j] = !valid ? 0.f : c ? (cj ? -a.y : a.y) : a.x;
                         }
+                        shift_right32(col, ly);
+#pragma unroll
+                        for (int y = 0; y < 32; ++y)
+                            st4(Ak + tf32_row_off(32 * c + y), to_tf32(col[y]));
                     }
+                    // B: W V times the u-taps (conj for w < 0), component d at
+                    // columns lx .. lx + S - 1
                     const float wr = wt * x.x, wi = wt * x.y;
+                    float bre[16], bim[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        if (valid && j < S) {
-                            const float ur = tu[j].x, ui = cj ? -tu[j].y : tu[j].y;
-                            st8(Bk + roff(lx + j), to_tf32(wr * ur - wi * ui),
-                                to_tf32(wr * ui + wi * ur));
-                        }
+                        const float2 u = tap(uq, j);
+                        const float ur = u.x, ui = cj ? -u.y : u.y;
+                        bre[j] = wr * ur - wi * ui;
+                        bim[j] = wr * ui + wi * ur;
                     }
 #pragma unroll
-                    for (int xq = 0; xq < 32; ++xq) {
-                        if (xq < lx || xq >= lx + S)
-                            st8(Bk + roff(xq), 0u, 0u);
+                    for (int d = 0; d < 2; ++d) {
+                        float col[32];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            col[j] = (!valid || j >= 16) ? 0.f : d ? bim[j] : bre[j];
+                        shift_right32(col, lx);
+#pragma unroll
+                        for (int xx = 0; xx < 32; ++xx)
+                            st4(Bk + tf32_row_off(32 * d + xx), to_tf32(col[xx]));
                     }
                 } else {
                 // this slot's taps and value: unshifted table rows (v: 16-bit
@@ -780,7 +811,7 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
         const bool holds = C::M == 128 || lane < 16;
         float *const row =
             stg + (C::M == 128 ? 32 * qq + lane : 16 * qq + (lane & 15)) * C::kStgStride;
-        constexpr int NC = C::TF32 ? 32 : 64;  // staged columns: x, or (d, x)
+        constexpr int NC = 64;  // staged columns (d, x)
         Cursor cur;
         int ne = 0;
         while (cursor_next<SV>(cur, items, n_items)) {
@@ -841,21 +872,14 @@ __global__ void __launch_bounds__(Cfg<PREC>::kBlock, 1) grid_tc2_kernel(
                 const int y = e >> 5, xx = e & 31;
                 if (y >= W || xx >= W)
                     continue;
-                float re, im;
-                if constexpr (C::TF32) {  // rows (c, y) of G itself
-                    re = stg[y * C::kStgStride + xx];
-                    im = stg[(32 + y) * C::kStgStride + xx];
-                } else {
-                    // rows (h, c, y), columns (d, x): Re = rr - ii, Im = ri + ir
-                    re = 0.f;
-                    im = 0.f;
+                // rows (h, c, y), columns (d, x): Re = rr - ii, Im = ri + ir
+                float re = 0.f, im = 0.f;
 #pragma unroll
-                    for (int h = 0; h < H; ++h) {
-                        const float *r0 = stg + (64 * h + y) * C::kStgStride;
-                        const float *r1 = r0 + 32 * C::kStgStride;
-                        re += r0[xx] - r1[32 + xx];
-                        im += r0[32 + xx] + r1[xx];
-                    }
+                for (int h = 0; h < H; ++h) {
+                    const float *r0 = stg + (64 * h + y) * C::kStgStride;
+                    const float *r1 = r0 + 32 * C::kStgStride;
+                    re += r0[xx] - r1[32 + xx];
+                    im += r0[32 + xx] + r1[xx];
                 }
                 if (re != 0.f || im != 0.f)
                     atomicAdd(grid + o.base + (o.gy0 + y) * p.N + o.gx0 + xx, make_float2(re, im));
@@ -880,12 +904,12 @@ cudaError_t launch_prec(const DevParams &p, const Plan &plan, const float2 *vis,
 {
     using C = Cfg<PREC>;
     const int64_t nrow = (int64_t)p.P * p.OS;
-    constexpr int KV = 4 * C::H, KU = C::U16 ? 4 : 8;  // uint4 per v and u row
+    constexpr int KV = C::TF32 ? 8 : 4 * C::H, KU = C::U16 ? 4 : 8;  // uint4 per row
     uint4 *vtab = reinterpret_cast<uint4 *>(tables);
     uint4 *utab = vtab + nrow * KV;
     int32_t *item_exp = reinterpret_cast<int32_t *>(utab + nrow * KU);
     cudaError_t e;
-    if constexpr (!C::TF32) {  // TF32 reads the caller's taps directly
+    {
         const int64_t n = nrow * (KV + KU);
         const int nb = (int)std::min<int64_t>((n + 255) / 256, 4096);
         tables_kernel<PREC><<<nb, 256, 0, s>>>(p, taps, vtab, utab);

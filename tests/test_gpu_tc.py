@@ -331,3 +331,25 @@ def test_tc_schedule_item_sizes(env, prec, chunk):
     S.sepw_grid(ctx, taps, d["u"], d["v"], d["w"], d["vis"], d["weight"], g)
     assert S.sepw_device_status(ctx) == S.OK
     assert rel_l2(g.cpu().numpy(), want) <= TOL[prec]
+
+
+@pytest.mark.parametrize("support", [2, 4, 6, 10, 14])
+@pytest.mark.parametrize("prec", PRECS)
+def test_tc_other_supports(env, support, prec):
+    """Supports whose taps do not fill the 16-tap table rows (zero padding,
+    shifts of every residue, the largest tile T = 33 - S rounded to even):
+    gridding and degridding against the oracle at the form's bar."""
+    torch, S = env
+    wl = synth.random_case(40 + support, 4000, 128, support, 8, 9, edge_fraction=0.1)
+    p = O.params_from(wl.params())
+    want, loc = _oracle(wl)
+    got, _, ctx, taps, d = _grid(torch, S, wl, _form(S, prec))
+    assert rel_l2(got, want) <= TOL[prec], (support, prec)
+    N = wl.grid_size
+    rng = np.random.default_rng(support)
+    X = (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))).astype(np.complex64)
+    want_p = O.degrid_separable(p, loc, X, wl.weight, O.taps(p))
+    out = torch.zeros(wl.nvis, dtype=torch.complex64, device="cuda")
+    S.sepw_degrid(ctx, taps, d["u"], d["v"], d["w"], torch.from_numpy(X).cuda(), d["weight"], out)
+    assert S.sepw_device_status(ctx) == S.OK
+    assert rel_l2(out.cpu().numpy(), want_p) <= TOL[prec], (support, prec)
