@@ -19,13 +19,12 @@
 //     Im G = sum_h,g D[(h,0,y)][(g,1,x)] + D[(h,1,y)][(g,0,x)].
 // a_h (b'_g) is the h-th (g-th) part of the 16-bit split of the taps (of W V
 // times the taps): H = 1 for the one-part forms, H = 2 for the hi + lo forms,
-// where one MMA yields all four products of the splits.  The TF32 form keeps
-// K = (visibility, re/im) with M = 64 rows (c, y) and N = 32 columns x:
-//     A[(0,y)][(i,0)] = a_r   A[(0,y)][(i,1)] = -a_i
-//     A[(1,y)][(i,0)] = a_i   A[(1,y)][(i,1)] =  a_r
-//     B[(i,0)][x] = b'_r      B[(i,1)][x] = b'_i
-// (the accumulator is G itself), with K-major operands: MN-major TF32
-// operands gave zeros on the GB300.
+// where one MMA yields all four products of the splits.  The TF32 form uses
+// the same embedding (H = 1, K = 8 visibilities per MMA) with K-major
+// operands, since MN-major TF32 operands gave zeros on the GB300: a
+// visibility's column of A and row of B are one 4-byte element in each of 64
+// rows, so every lane shifts its taps to absolute rows (columns) in registers
+// and the warp stores one row at a time.
 //
 // The 16-bit operands are MN-major: a visibility's column of A (and its row
 // of B) is contiguous along M (N) in 16-byte pieces of 8 values, so it is
