@@ -1,5 +1,5 @@
 // Tensor-core (tcgen05) contraction form of the separable gridder with
-// MN-major operands built by 16-byte stores from pre-shifted tap tables.
+// MN-major operands built by 16-byte stores from unshifted tap tables.
 //
 // Sec. 5 writes the update of a visibility as the separable product
 // W V F1(u - u_i) F1(v - v_i).  Summed over the visibilities of one tile it is
@@ -28,19 +28,20 @@
 //
 // The 16-bit operands are MN-major: a visibility's column of A (and its row
 // of B) is contiguous along M (N) in 16-byte pieces of 8 values, so it is
-// written as whole 16-byte chunks.  The chunks come from tables built per call from the
-// caller's complex64 taps:
-//   vtab: per (plane, oversample, shift s = row offset mod 8, part h,
-//         component): three chunks holding taps 8 j - s .. 8 j - s + 7
-//         (zero outside 0 .. S-1), rounded to the 16-bit format;
-//   utab: per (plane, oversample, shift, chunk j): the same eight taps of
-//         the u side, complex64 for the hi + lo forms and (re, im) pairs in
-//         the 16-bit format for the one-part forms, multiplied by W V in FP32
-//         before rounding.
-// Chunk j of a visibility whose footprint starts at row ly goes to chunk row
-// j + ly / 8 of its column: the placement is a computed store address, and the
-// chunk rows its footprint misses get zeros, so each stage overwrites every
-// byte its visibilities own and no buffer ever needs clearing.
+// written as whole 16-byte chunks.  They come from tables built per call from
+// the caller's complex64 taps, one unshifted row per (plane, oversample):
+//   vtab: the S v-taps as 16-bit pairs (2 w, 2 w + 1) per split part and
+//         component (zero beyond S);
+//   utab: the S u-taps, as (re, im) 16-bit pairs (one-part forms) or
+//         complex64 (hi + lo forms), multiplied by W V in FP32 before
+//         rounding.
+// A lane moves its 16 v values to the row offset ly mod 8 within three
+// 8-value chunks in registers (shift16: two word shifts and a half-word step),
+// and likewise its W V u products to the column offset lx mod 8.  Chunk j of a
+// visibility whose footprint starts at row ly goes to chunk row j + ly / 8 of
+// its column: the placement is a computed store address, and the chunk rows
+// its footprint misses get zeros, so each stage overwrites every byte its
+// visibilities own and no buffer ever needs clearing.
 //
 // One lane per visibility: a stage is 64 visibilities, written by a pair of
 // producer warps (32 each).  Slot i is K row i % 8 of core-matrix group i / 8,
