@@ -45,7 +45,8 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("form,tol", [(1, 1e-5), (3, 1.5e-3), (0, 1e-5)])
+@pytest.mark.parametrize("form,tol", [(1, 1e-5), (3, 1.5e-3), (0, 1e-5), (2, 1e-2), (5, 1e-5),
+                                      (6, 1.5e-3)])
 def test_batched_matches_oracle_per_grid(env, form, tol):
     torch, S = env
     wl, offs, parts = _batch()
@@ -113,6 +114,37 @@ def test_batched_degrid_and_graph_replay(env):
         loc = O.locate(p, part.u, part.v, part.w)
         want = O.degrid_separable(p, loc, X[gi], part.weight, T)
         assert rel_l2(got[offs[gi]:offs[gi + 1]], want) <= 1e-5
+
+
+@pytest.mark.parametrize("form,tol", [(2, 1e-2), (3, 1.5e-3), (5, 1e-5)])
+def test_batched_tc_degrid_matches_oracle_per_grid(env, form, tol):
+    """Degridding a batched plan in the tensor-core forms (BF16 and FP16 on
+    the contraction degridder, whose windows carry each grid's base offset;
+    BF16 hi + lo on the tiled FP32 degridder): per-grid predictions against
+    the oracle at the form's bar, the empty grid included."""
+    torch, S = env
+    wl, offs, parts = _batch(seed=4)
+    ctx = S.sepw_create(S.make_params(**wl.params(), form=form))
+    taps = S.sepw_make_taps(ctx)
+    d = {k: torch.from_numpy(getattr(wl, k)).cuda() for k in ("u", "v", "w", "vis", "weight")}
+    ng = len(offs) - 1
+    N = wl.grid_size
+    S.sepw_plan_batched(ctx, offs, d["u"], d["v"], d["w"])
+    rng = np.random.default_rng(5)
+    X = (rng.standard_normal((ng, N, N)) + 1j * rng.standard_normal((ng, N, N))
+         ).astype(np.complex64)
+    out = torch.full((wl.nvis,), complex(7, 7), dtype=torch.complex64, device="cuda")
+    S.sepw_degrid_planned(ctx, taps, torch.from_numpy(X).cuda(), d["weight"], out)
+    assert S.sepw_device_status(ctx) == S.OK
+    got = out.cpu().numpy()
+    p = O.params_from(wl.params())
+    T = O.taps(p)
+    for gi, part in enumerate(parts):
+        if part.nvis == 0:
+            continue
+        loc = O.locate(p, part.u, part.v, part.w)
+        want = O.degrid_separable(p, loc, X[gi], part.weight, T)
+        assert rel_l2(got[offs[gi]:offs[gi + 1]], want) <= tol, (form, gi)
 
 
 def test_batched_rejects_bad_offsets(env):
