@@ -718,17 +718,18 @@ def run_ours(args):
                             "phases_ms": {"plan": plan_ms, "grid": grid_ms,
                                           "degrid": degrid_ms}}}
 
-    # ---- tensor-core contraction forms (grid on tcgen05; degrid on tcgen05 for
-    # bf16 / fp16, tiled FP32 for the hi + lo form) ----
+    # ---- tensor-core contraction forms (grid on tcgen05; degrid on tcgen05
+    # for the 16-bit forms, one-part and hi + lo; tiled FP32 for TF32) ----
     peaks, peak_src = _peaks()
     if not args.skip_tc:
-        # (name, form, split parts H, peak / bf16 peak, degrid on tensor cores)
+        # (name, form, split parts H, peak / bf16 peak, products per degrid
+        # contraction on tensor cores (0: tiled FP32 degrid))
         for name, form, H, pratio, tc_dg in (
-                ("tc_bf16", S.FORM_TC_BF16, 1, 1.0, True),
-                ("tc_fp16", S.FORM_TC_FP16, 1, 1.0, True),
-                ("tc_fp16x2", S.FORM_TC_FP16X2, 2, 1.0, False),
-                ("tc_bf16x2", S.FORM_TC_BF16X2, 2, 1.0, False),
-                ("tc_tf32", S.FORM_TC_TF32, 1, 1.1 / 2.25, False)):
+                ("tc_bf16", S.FORM_TC_BF16, 1, 1.0, 1),
+                ("tc_fp16", S.FORM_TC_FP16, 1, 1.0, 1),
+                ("tc_fp16x2", S.FORM_TC_FP16X2, 2, 1.0, 3),
+                ("tc_bf16x2", S.FORM_TC_BF16X2, 2, 1.0, 3),
+                ("tc_tf32", S.FORM_TC_TF32, 1, 1.1 / 2.25, 0)):
             c2 = S.sepw_create(S.make_params(**wl.params(), form=form))
             fms, fp, fg, fd = _time_form(S, torch, c2, taps, dev, grid, out,
                                          max(3, args.steps // 2), 2, stream)
@@ -751,15 +752,16 @@ def run_ours(args):
                                        "nominal ratio)"}}
             if tc_dg:
                 # degridding: one M128 x N64 x K64 product per 128 visibilities
-                # of a work item (Q = conj(Av) X over the item's 32-cell window)
-                dg_flops = 2 * 64 * 64 * nkept
+                # of a work item (Q = conj(Av) X over the item's 32-cell window),
+                # three for the hi + lo forms
+                dg_flops = 2 * 64 * 64 * nkept * tc_dg
                 forms[name]["degrid_tensor_roofline"] = {
                     "bound": "tensor", "unit": "TFLOP/s",
                     "achieved": dg_flops / (fd * 1e-3) / 1e12,
                     "peak": float(peaks["bf16_tflops"]),
                     "frac": dg_flops / (fd * 1e-3) / 1e12 / float(peaks["bf16_tflops"]),
-                    "note": "dense MMA flops per kept visibility (2 x 64 x 64; "
-                            "ragged stages not counted) over the degrid kernel"}
+                    "note": "dense MMA flops per kept visibility (2 x 64 x 64 per "
+                            "product; ragged stages not counted) over the degrid kernel"}
             c2.close()
 
     # ---- plain FP32 form on the same data (the comparator) ----

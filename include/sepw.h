@@ -84,11 +84,15 @@ extern "C" {
 #define SEPW_FORM_TC_FP16X2 4 /* as SEPW_FORM_TC_FP16 with each operand split into
                                  FP16 hi + lo (all four products of the
                                  splits): FP32-class accuracy.  Degridding
-                                 uses the tiled FP32 form. */
+                                 is the contraction form with the v-taps and
+                                 the window split (three products) and FP32
+                                 u-taps. */
 #define SEPW_FORM_TC_BF16X2 5 /* as SEPW_FORM_TC_BF16 with each operand split into
                                  BF16 hi + lo (all four products; no scale:
                                  BF16 has the FP32 exponent range).
-                                 Degridding uses the tiled FP32 form. */
+                                 Degridding is the contraction form with the
+                                 v-taps and the window split (three
+                                 products) and FP32 u-taps. */
 #define SEPW_FORM_TC_TF32 6   /* as SEPW_FORM_TC_BF16 with TF32 operands (10-bit
                                  mantissa, FP32 range: no scale), rounded from
                                  the caller's FP32 taps and W V times them;

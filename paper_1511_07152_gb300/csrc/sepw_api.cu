@@ -618,7 +618,8 @@ int sepw_degrid_planned(sepw_ctx *ctx, const float *taps, const float *grid,
         if (((uintptr_t)taps) & 15)
             return fail(ctx, SEPW_EINVAL, "taps must be 16-byte aligned");
         SEPW_CUDA(ctx, launch_zero_dropped(pl, (float2 *)vis_out, s));
-        if (pl.form == SEPW_FORM_TC_BF16 || pl.form == SEPW_FORM_TC_FP16) {
+        if (pl.form == SEPW_FORM_TC_BF16 || pl.form == SEPW_FORM_TC_FP16 ||
+            pl.form == SEPW_FORM_TC_FP16X2 || pl.form == SEPW_FORM_TC_BF16X2) {
             if (ctx->tc2_cap < tc_workspace_bytes(ctx->dp, pl.items_capacity))
                 return fail(ctx, SEPW_ENOPLAN, "tensor-core workspace missing (plan first)");
             SEPW_CUDA(ctx, launch_degrid_tc(ctx->dp, pl, (const float2 *)grid, weight,

@@ -407,9 +407,10 @@ cudaError_t launch_plan(const DevParams &p, int64_t nvis, const double *u,
             return e;
         // the per-item sort by (sub-block, conj, origin) serves the kernels
         // that walk runs of one origin (the tiled FP32 gridder and
-        // degridder); the BF16 and FP16 tensor-core forms grid and degrid
-        // in any order within an item and skip it
-        if (plan.form == SEPW_FORM_TC_BF16 || plan.form == SEPW_FORM_TC_FP16)
+        // degridder); the 16-bit tensor-core forms (one-part and hi + lo)
+        // grid and degrid in any order within an item and skip it
+        if (plan.form == SEPW_FORM_TC_BF16 || plan.form == SEPW_FORM_TC_FP16 ||
+            plan.form == SEPW_FORM_TC_FP16X2 || plan.form == SEPW_FORM_TC_BF16X2)
             return cudaSuccess;
         const int E = (p.T + 3) / 4;
         const int nb = 32 * E * E;

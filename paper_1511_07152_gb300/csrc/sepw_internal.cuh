@@ -440,7 +440,8 @@ struct TcControl {
 };
 
 // sepw_tc.cu: contraction-form degridder, prec 0 = BF16, 1 = FP16 (scaled
-// per item); T + S - 1 <= 32, S <= 16.  tables: tc_degrid_tables_bytes(p,
+// per item), 2 = FP16 hi + lo (scaled), 3 = BF16 hi + lo; T + S - 1 <= 32,
+// S <= 16.  tables: tc_degrid_tables_bytes(p,
 // plan.items_capacity) bytes of device workspace (per-call tap tables and
 // per-item scale exponents).
 size_t tc_degrid_tables_bytes(const DevParams &p, int64_t items_capacity);

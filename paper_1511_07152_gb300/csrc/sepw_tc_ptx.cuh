@@ -89,6 +89,19 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
 }
 
+// Shared-memory matrix descriptor, K-major with 128-byte swizzle: each row of
+// the operand is 128 bytes (64 16-bit K elements), 8-row atoms of 1024 bytes
+// follow each other along M (or N) (SBO 1024; LBO unused), and the 16-byte
+// chunk c of row r of an atom is stored at chunk c ^ (r mod 8).  The swizzle
+// is a function of the shared-memory address, so atoms must be 1024-byte
+// aligned; a K step within the row advances the start address (32 bytes per
+// K = 16).
+__device__ __forceinline__ uint64_t smem_desc_sw128k(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
+}
+
 // Instruction descriptor: D = F32; A, B format fmt (kind::f16: F16 = 0,
 // BF16 = 1; kind::tf32: TF32 = 2); A / B MN-major when a_mn / b_mn; shape M x N.
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, bool a_mn, bool b_mn, int M,

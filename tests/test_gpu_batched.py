@@ -116,12 +116,13 @@ def test_batched_degrid_and_graph_replay(env):
         assert rel_l2(got[offs[gi]:offs[gi + 1]], want) <= 1e-5
 
 
-@pytest.mark.parametrize("form,tol", [(2, 1e-2), (3, 1.5e-3), (5, 1e-5)])
+@pytest.mark.parametrize("form,tol", [(2, 1e-2), (3, 1.5e-3), (4, 1e-5), (5, 1e-5), (6, 1.5e-3)])
 def test_batched_tc_degrid_matches_oracle_per_grid(env, form, tol):
-    """Degridding a batched plan in the tensor-core forms (BF16 and FP16 on
-    the contraction degridder, whose windows carry each grid's base offset;
-    BF16 hi + lo on the tiled FP32 degridder): per-grid predictions against
-    the oracle at the form's bar, the empty grid included."""
+    """Degridding a batched plan in the tensor-core forms (BF16, FP16 and
+    their hi + lo splits on the contraction degridder, whose windows carry
+    each grid's base offset; TF32 on the tiled FP32 degridder): per-grid
+    predictions against the oracle at the form's bar, the empty grid
+    included."""
     torch, S = env
     wl, offs, parts = _batch(seed=4)
     ctx = S.sepw_create(S.make_params(**wl.params(), form=form))
