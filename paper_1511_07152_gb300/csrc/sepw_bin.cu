@@ -107,53 +107,67 @@ __global__ void __launch_bounds__(256) bin_scan_kernel(int32_t ntiles,
 // Pass 2 (one block of 1024 threads): exclusive scans of the tile counts
 // (-> slot cursors) and of the per-tile chunk counts (-> work items).  Full
 // chunks (`chunk` visibilities) are listed before the partial ones, so that
-// dynamically scheduled workers take the heavy items first.
+// dynamically scheduled workers take the heavy items first; within each list
+// the items are in tile order.  Warp w owns the tiles [w R, (w + 1) R) and
+// walks them 32 at a time, one tile per lane, so that its loads and its
+// cursor and item stores are coalesced: a first walk sums the range, a block
+// scan gives every warp its bases, and a second walk writes the cursors and
+// items from warp-shuffle scans of each group of 32 tiles.
 constexpr int kScanThreads = 1024;
+constexpr int kScanWarps = kScanThreads / 32;
+
+__device__ __forceinline__ void warp_scan3(int64_t &a, int32_t &b, int32_t &c, int lane)
+{
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t x = __shfl_up_sync(0xffffffffu, a, off);
+        const int32_t y = __shfl_up_sync(0xffffffffu, b, off);
+        const int32_t z = __shfl_up_sync(0xffffffffu, c, off);
+        if (lane >= off) {
+            a += x;
+            b += y;
+            c += z;
+        }
+    }
+}
 
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(
     int32_t ntiles, int32_t chunk, const int32_t *__restrict__ tile_count,
     int32_t *__restrict__ cursor, WorkItem *__restrict__ items, int32_t *nitems)
 {
-    __shared__ int64_t s_cnt[kScanThreads / 32];
+    __shared__ int64_t s_cnt[kScanWarps];
+    __shared__ int32_t s_full[kScanWarps], s_part[kScanWarps];
     __shared__ int32_t s_tot_full, s_tot_part;
-    __shared__ int32_t s_full[kScanThreads / 32];
-    __shared__ int32_t s_part[kScanThreads / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int per = (ntiles + kScanThreads - 1) / kScanThreads;
-    const int lo = min(ntiles, t * per), hi = min(ntiles, lo + per);
+    const int R = (((ntiles + kScanWarps - 1) / kScanWarps) + 31) & ~31;  // tiles per warp
+    const int lo = min(ntiles, warp * R), hi = min(ntiles, lo + R);
+    // walk 1: the range's totals (visibilities, full chunks, partial chunks)
     int64_t c = 0;
     int32_t nf = 0, np = 0;
-    // this thread's tiles, eight loads in flight at a time
-    for (int i0 = lo; i0 < hi; i0 += 8) {
-        int n[8];
+    for (int i0 = lo; i0 < hi; i0 += 32 * 4) {
+        int n[4];
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-            n[k] = i0 + k < hi ? tile_count[i0 + k] : 0;
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + 32 * k + lane;
+            n[k] = i < hi ? tile_count[i] : 0;
+        }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < 4; ++k) {
             c += n[k];
             nf += n[k] / chunk;
             np += (n[k] % chunk) != 0;
         }
     }
-    // exclusive scans over the threads: warp shuffles, then the warp totals
-    int64_t ic = c;
-    int32_t ifl = nf, ip = np;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int64_t x = __shfl_up_sync(0xffffffffu, ic, off);
-        const int32_t y = __shfl_up_sync(0xffffffffu, ifl, off);
-        const int32_t z = __shfl_up_sync(0xffffffffu, ip, off);
-        if (lane >= off) {
-            ic += x;
-            ifl += y;
-            ip += z;
-        }
+    for (int off = 16; off > 0; off >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, off);
+        nf += __shfl_xor_sync(0xffffffffu, nf, off);
+        np += __shfl_xor_sync(0xffffffffu, np, off);
     }
-    if (lane == 31) {
-        s_cnt[warp] = ic;
-        s_full[warp] = ifl;
-        s_part[warp] = ip;
+    if (lane == 0) {
+        s_cnt[warp] = c;
+        s_full[warp] = nf;
+        s_part[warp] = np;
     }
     __syncthreads();
     if (warp == 0) {
@@ -161,18 +175,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
         int32_t wf = s_full[lane], wp = s_part[lane];
         const int64_t c0 = wc;
         const int32_t f0 = wf, p0 = wp;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int64_t x = __shfl_up_sync(0xffffffffu, wc, off);
-            const int32_t y = __shfl_up_sync(0xffffffffu, wf, off);
-            const int32_t z = __shfl_up_sync(0xffffffffu, wp, off);
-            if (lane >= off) {
-                wc += x;
-                wf += y;
-                wp += z;
-            }
-        }
-        s_cnt[lane] = wc - c0;  // exclusive warp offsets
+        warp_scan3(wc, wf, wp, lane);
+        s_cnt[lane] = wc - c0;  // exclusive warp bases
         s_full[lane] = wf - f0;
         s_part[lane] = wp - p0;
         if (lane == 31) {
@@ -182,30 +186,40 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(
     }
     __syncthreads();
     const int32_t total_full = s_tot_full;
-    int64_t off_c = s_cnt[warp] + ic - c;
-    int32_t off_f = s_full[warp] + ifl - nf;
-    int32_t off_p = total_full + s_part[warp] + ip - np;
-    for (int i = lo; i < hi; ++i) {
-        const int n = tile_count[i];
-        cursor[i] = (int32_t)off_c;
-        const int nk = n / chunk;
-        for (int q = 0; q < nk; ++q) {
-            WorkItem it;
-            it.tile = i;
-            it.start = (int32_t)(off_c + (int64_t)q * chunk);
-            it.count = chunk;
-            it.pad = 0;
-            items[off_f++] = it;
+    int64_t base_c = s_cnt[warp];
+    int32_t base_f = s_full[warp], base_p = total_full + s_part[warp];
+    // walk 2: cursors and items, 32 tiles at a time
+    for (int i0 = lo; i0 < hi; i0 += 32) {
+        const int i = i0 + lane;
+        const int n = i < hi ? tile_count[i] : 0;
+        const int nk = n / chunk, part = (n % chunk) != 0;
+        int64_t ic = n;
+        int32_t ik = nk, ipt = part;
+        warp_scan3(ic, ik, ipt, lane);
+        const int64_t off_c = base_c + ic - n;  // exclusive
+        const int32_t off_f = base_f + ik - nk, off_p = base_p + ipt - part;
+        if (i < hi) {
+            cursor[i] = (int32_t)off_c;
+            for (int q = 0; q < nk; ++q) {
+                WorkItem it;
+                it.tile = i;
+                it.start = (int32_t)(off_c + (int64_t)q * chunk);
+                it.count = chunk;
+                it.pad = 0;
+                items[off_f + q] = it;
+            }
+            if (part) {
+                WorkItem it;
+                it.tile = i;
+                it.start = (int32_t)(off_c + (int64_t)nk * chunk);
+                it.count = n % chunk;
+                it.pad = 0;
+                items[off_p] = it;
+            }
         }
-        if (n % chunk) {
-            WorkItem it;
-            it.tile = i;
-            it.start = (int32_t)(off_c + (int64_t)nk * chunk);
-            it.count = n % chunk;
-            it.pad = 0;
-            items[off_p++] = it;
-        }
-        off_c += n;
+        base_c += __shfl_sync(0xffffffffu, ic, 31);
+        base_f += __shfl_sync(0xffffffffu, ik, 31);
+        base_p += __shfl_sync(0xffffffffu, ipt, 31);
     }
     if (t == 0)
         *nitems = total_full + s_tot_part;
