@@ -445,8 +445,9 @@ def test_meerkat_full_size(torch_cuda, S_, meerkat):
     """All 32,256,000 visibilities in the benchmark's launch configuration
     (tiled form, plan + grid + degrid) against the FP64 oracle on all of them
     (run over the host's cores): the grid and every prediction within the
-    FP32 bar.  Also: the plain form's grid agrees, and gridding is linear (the
-    sum of the grids of the two halves)."""
+    FP32 bar; the BF16 hi + lo tensor-core form's grid and predictions at the
+    same bar, the BF16 form's at 1e-2.  Also: the plain form's grid agrees,
+    and gridding is linear (the sum of the grids of the two halves)."""
     torch = torch_cuda
     wl = meerkat
     N = 4096
@@ -467,6 +468,19 @@ def test_meerkat_full_size(torch_cuda, S_, meerkat):
     assert rel_l2(a, want) <= TOL_FP32
     pred = _oracle_threads(p, wl, T, model=a.astype(np.complex128))
     assert rel_l2(out.cpu().numpy(), pred) <= TOL_FP32
+    # the tensor-core forms on the same full workload and model grid: BF16
+    # hi + lo at the FP32 bar, BF16 at its own (operand rounding 2^-8)
+    for form, tol in ((S_.FORM_TC_BF16X2, TOL_FP32), (S_.FORM_TC_BF16, 1e-2)):
+        ctx_c = _ctx(S_, wl, form)
+        gc = torch.zeros_like(gt)
+        S_.sepw_plan(ctx_c, d["u"], d["v"], d["w"])
+        S_.sepw_grid_planned(ctx_c, taps, d["vis"], d["weight"], gc)
+        assert rel_l2(gc.cpu().numpy(), want) <= tol, form
+        S_.sepw_degrid_planned(ctx_c, taps, gt, d["weight"], out)
+        assert S_.sepw_device_status(ctx_c) == S_.OK
+        assert rel_l2(out.cpu().numpy(), pred) <= tol, form
+        ctx_c.close()
+        del gc
     del want, pred
     gp = torch.zeros_like(gt)
     S_.sepw_grid(ctx_p, taps, d["u"], d["v"], d["w"], d["vis"], d["weight"], gp)
