@@ -96,14 +96,24 @@ def test_tc_grid_parity(env, prec, name):
 
 
 @pytest.mark.parametrize("tile", [8, 12, 16])
-@pytest.mark.parametrize("prec", ["fp16", "bf16x2", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "bf16x2", "fp16x2", "tf32"])
 def test_tc_tile_sizes(env, tile, prec):
-    """Tiles up to the 32-cell window (T + S - 1 <= 32 at S = 16)."""
+    """Tiles up to the 32-cell window (T + S - 1 <= 32 at S = 16): gridding,
+    and degridding, whose first K chunk ly / 4 ranges over 0 .. (T - 1) / 4."""
     torch, S = env
     wl = CASES["rand_S16"]()
-    want, _ = _oracle(wl)
-    got, *_ = _grid(torch, S, wl, _form(S, prec), tile=tile)
+    want, loc = _oracle(wl)
+    got, _, ctx, taps, d = _grid(torch, S, wl, _form(S, prec), tile=tile)
     assert rel_l2(got, want) <= TOL[prec]
+    p = O.params_from(wl.params())
+    N = wl.grid_size
+    rng = np.random.default_rng(tile)
+    X = (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))).astype(np.complex64)
+    want_p = O.degrid_separable(p, loc, X, wl.weight, O.taps(p))
+    out = torch.zeros(wl.nvis, dtype=torch.complex64, device="cuda")
+    S.sepw_degrid(ctx, taps, d["u"], d["v"], d["w"], torch.from_numpy(X).cuda(), d["weight"], out)
+    assert S.sepw_device_status(ctx) == S.OK
+    assert rel_l2(out.cpu().numpy(), want_p) <= TOL[prec]
 
 
 def test_tc_tile_beyond_window_rejected(env):
