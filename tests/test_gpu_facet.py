@@ -76,11 +76,17 @@ def test_facet_shift_bit_exact_uv(env):
 
 
 @pytest.mark.parametrize("S_,form", [(8, "tiled"), (10, "tiled"), (16, "tiled"),
-                                     (8, "plain"), (16, "tc_fp16x2")])
+                                     (8, "plain"), (16, "tc_fp16x2"), (16, "tc_bf16x2"),
+                                     (16, "tc_bf16")])
 def test_facet_grid_image_and_prediction(env, S_, form):
+    """Gridding, image step and prediction with the facet tables (separate u-
+    and v-tap tables, the v taps at an offset): the FP32 forms and the hi + lo
+    tensor-core forms at 1e-5, the BF16 tensor-core form at its 1e-2."""
     torch, S = env
     wl = _case(S_=S_, seed=92 + S_)
-    f = {"tiled": S.FORM_TILED, "plain": S.FORM_PLAIN, "tc_fp16x2": S.FORM_TC_FP16X2}[form]
+    f = {"tiled": S.FORM_TILED, "plain": S.FORM_PLAIN, "tc_fp16x2": S.FORM_TC_FP16X2,
+         "tc_bf16x2": S.FORM_TC_BF16X2, "tc_bf16": S.FORM_TC_BF16}[form]
+    tol = 1e-2 if form == "tc_bf16" else 1e-5
     ctx = _ctx(S, wl, f)
     taps = S.sepw_make_taps(ctx)
     d = {k: torch.from_numpy(getattr(wl, k)).cuda() for k in ("u", "v", "w", "vis", "weight")}
@@ -95,7 +101,7 @@ def test_facet_grid_image_and_prediction(env, S_, form):
     loc = O.locate(p, up, vp, wl.w)
     Tu, Tv = O.taps_facet(p, L0, M0)
     want = O.grid_separable(p, loc, visp, wl.weight, Tu, Tv=Tv)
-    assert rel_l2(grid.cpu().numpy(), want) <= 1e-5
+    assert rel_l2(grid.cpu().numpy(), want) <= tol
     # image step with n at the facet's pixels; compare with the grid
     # correction divided out (it amplifies FP32 rounding at the facet edge)
     S.sepw_image(ctx, S.GRID_TO_IMAGE, grid)
@@ -105,7 +111,7 @@ def test_facet_grid_image_and_prediction(env, S_, form):
     l = nu * p.fov
     n = np.sqrt(1 - (l[None, :] + L0) ** 2 - (l[:, None] + M0) ** 2)
     wgt = c1[None, :] * c1[:, None] / n
-    assert rel_l2(grid.cpu().numpy() * wgt, want_img * wgt) <= 1e-5
+    assert rel_l2(grid.cpu().numpy() * wgt, want_img * wgt) <= tol
     # prediction: degrid a model grid with the facet tables, rotate back
     rng = np.random.default_rng(S_)
     X = (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))).astype(np.complex64)
@@ -115,7 +121,7 @@ def test_facet_grid_image_and_prediction(env, S_, form):
     n0 = math.sqrt(1 - L0 * L0 - M0 * M0)
     ph = wl.u * L0 + wl.v * M0 + wl.w * (n0 - 1.0)
     wantv = O.degrid_separable(p, loc, X, wl.weight, Tu, Tv=Tv) * np.exp(-2j * np.pi * ph)
-    assert rel_l2(out.cpu().numpy(), wantv) <= 1e-5
+    assert rel_l2(out.cpu().numpy(), wantv) <= tol
 
 
 def test_facet_rejects(env):
