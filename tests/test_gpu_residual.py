@@ -55,11 +55,12 @@ def test_correction_table(env, oracle_tables, Sr, OSr):
     assert np.max(np.abs(g32 - got)) <= 2 ** -23 * np.max(np.abs(got)) + 1e-30
 
 
-@pytest.mark.parametrize("form", ["tiled", "tc_fp16x2"])
+@pytest.mark.parametrize("form", ["tiled", "tc_fp16x2", "tc_bf16x2"])
 def test_separable_plus_correction_is_exact_w_projection(env, oracle_tables, form):
     torch, S = env
     wl, p, K, T = oracle_tables
-    f = S.FORM_TILED if form == "tiled" else S.FORM_TC_FP16X2
+    f = {"tiled": S.FORM_TILED, "tc_fp16x2": S.FORM_TC_FP16X2,
+         "tc_bf16x2": S.FORM_TC_BF16X2}[form]
     ctx = S.sepw_create(S.make_params(**wl.params(), form=f))
     taps = S.sepw_make_taps(ctx)
     table = S.sepw_make_residual(ctx, p.S, p.OS)

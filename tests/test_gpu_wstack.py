@@ -82,11 +82,12 @@ def test_wstack_slices_and_drops(env):
     assert nd >= 3  # nan, inf and the residual beyond w_max
 
 
-@pytest.mark.parametrize("form", ["tiled", "tc_fp16x2"])
+@pytest.mark.parametrize("form", ["tiled", "tc_fp16x2", "tc_bf16x2"])
 def test_wstack_slice_grids_and_image(env, form):
     torch, S = env
     wl = _case()
-    f = S.FORM_TILED if form == "tiled" else S.FORM_TC_FP16X2
+    f = {"tiled": S.FORM_TILED, "tc_fp16x2": S.FORM_TC_FP16X2,
+         "tc_bf16x2": S.FORM_TC_BF16X2}[form]
     ctx, taps, d, _ = _plan(torch, S, wl, f)
     N, L = wl.grid_size, len(CENTRES)
     grids = torch.zeros((L, N, N), dtype=torch.complex64, device="cuda")
