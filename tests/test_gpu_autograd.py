@@ -67,7 +67,7 @@ def _oracle_grad(wl, image, target):
     return 2 * np.real(O.grid_to_image(p, G) / (1 - L * L - M * M))
 
 
-@pytest.mark.parametrize("form", [1, 3])
+@pytest.mark.parametrize("form", [1, 3, 5])
 def test_predict_gradient_matches_oracle(env, form):
     """Gradient of sum_i W_i |Predict(I)_i - V_i|^2 w.r.t. a real image."""
     torch, S, AG = env
@@ -75,7 +75,7 @@ def test_predict_gradient_matches_oracle(env, form):
     ctx, taps, d = _setup(torch, S, wl, form=form)
     rng = np.random.default_rng(3)
     image = rng.standard_normal((128, 128))
-    if form == 3:
+    if form in (3, 5):
         # FP16 degridding errs relative to the model grid, not to the
         # prediction: a white image divided by n c1^2 gives a grid 500 times
         # the prediction's rms (degridding cancels the edge-amplified part),
@@ -96,6 +96,13 @@ def test_predict_gradient_matches_oracle(env, form):
     got = I.grad.cpu().numpy()
     if form == 1:
         assert rel_l2(got, want) <= 1e-4
+    elif form == 5:
+        # BF16 hi + lo: grid and prediction errors ~4e-6, raised by the grid
+        # correction's c1(0)^2 / c1(nu)^2 <= 7.8 inside |nu| < 1/4 (see
+        # below): the FP32 bar holds there
+        nu = O.pixel_nu(128)
+        inner = np.ix_(np.abs(nu) < 0.25, np.abs(nu) < 0.25)
+        assert rel_l2(got[inner], want[inner]) <= 1e-4
     else:
         # The tensor-core form grids the backward with FP16 operands (grid
         # error ~4e-4; the FP16 forward adds ~2e-4 on this model).  That rounding noise is white in the image domain,
