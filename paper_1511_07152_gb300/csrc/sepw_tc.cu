@@ -41,21 +41,23 @@
 // Roles (work items assigned to CTAs round robin, so every role walks the
 // same items and stages without a shared counter):
 //   - eight producer warps in two groups of four, group g owning stage buffer
-//     g: it writes the CTA's stages t = g, g + 2, ... (one lane per
-//     visibility).  Owning its buffer, a group has itself filled the
+//     g: it writes the CTA's stages t = g, g + 2, ... (a lane loads the
+//     record of one slot, a quarter warp builds one slot's A row at a time).
+//     Owning its buffer, a group has itself filled the
 //     buffer's previous stage, so its wait for that stage's MMAs is never two
 //     mbarrier phases behind.  All eight build each item's window (two
 //     buffers, item n in buffer n mod 2) and wait until it is complete
 //     before they declare a stage full;
 //   - one MMA thread: per stage it waits for "full" and for the accumulator,
-//     issues the four MMAs and commits them to the stage's "done" barrier,
+//     issues the stage's MMAs (four, twelve for SPLIT) and commits them to
+//     the stage's "done" barrier,
 //     which both the producers (buffer free) and the epilogue (accumulator
 //     ready) wait on: one commit per stage;
 //   - four epilogue warps (one per tensor-memory lane quarter), one thread
 //     per visibility: it reads its accumulator row into registers, releases
 //     the accumulator, shifts the row to its column offset with a barrel
 //     shift in registers and takes the u-direction dot product with the
-//     u-taps of a second 16-bit table.
+//     u-taps of a second table (16-bit pairs, or complex64 for SPLIT).
 // Every mbarrier wait is bounded; on expiry the kernel records SEPW_ETIMEOUT
 // in the device status word, every role leaves its loop, the MMA thread waits
 // (bounded) for its own MMAs and the tensor memory is freed.
