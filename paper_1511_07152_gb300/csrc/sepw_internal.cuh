@@ -442,8 +442,9 @@ struct TcControl {
 // sepw_tc.cu: contraction-form degridder, prec 0 = BF16, 1 = FP16 (scaled
 // per item), 2 = FP16 hi + lo (scaled), 3 = BF16 hi + lo; T + S - 1 <= 32,
 // S <= 16.  tables: tc_degrid_tables_bytes(p,
-// plan.items_capacity) bytes of device workspace (per-call tap tables and
-// per-item scale exponents).
+// plan.items_capacity) bytes of device workspace for the per-call tap tables
+// (the FP16 forms' per-item window scale is found in the kernel; the item
+// count does not enter the size).
 size_t tc_degrid_tables_bytes(const DevParams &p, int64_t items_capacity);
 cudaError_t launch_degrid_tc(const DevParams &p, const Plan &plan, const float2 *grid,
                              const float *weight, const float2 *taps, void *tables, float2 *vis,
